@@ -1,0 +1,441 @@
+/*
+ * cj_oracle.c -- plain, slow, single-threaded FP64 reference of the Chebyshev-Jacobi
+ * method (CJM) for the 2-D finite-difference Poisson problem.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the product library links, loads or calls
+ * this file; only the test-suite, the smoke check and the CPU-baseline leg of the
+ * benchmark use it.  It shares no code, header or constant table with the CUDA path.
+ *
+ * What it follows (Adsuara et al., "Speeding up a few orders of magnitude the Jacobi
+ * method: high order Chebyshev-Jacobi over GPUs"):
+ *   - Sec. 2.1: CJM = weighted Jacobi with a different weight at every iteration; the
+ *     weights are precomputed from the zeros of a Chebyshev polynomial mapped onto the
+ *     eigenvalue interval [kmin, kmax] of the Jacobi iteration matrix.
+ *   - Table 3 (Cartesian row): the classical 5-point Laplacian.
+ *   - Eq. 1 / Fig. 1 (left): the 9-point, first-family, alpha = 2/3 Laplacian.
+ *   - Eq. 2 / Fig. 1 (right): the 17-point, second-family, alpha = 2/3 Laplacian.
+ *   - Eqs. for kmin^(9), kmax^(9) and kmin^(17), kmax^(17) in Sec. 2.1.
+ *   - Sec. 3.2: node indices 1 <= i <= Nx, 1 <= j <= Ny.
+ *
+ * Readings where the paper is silent (each one is listed, with its reason, in the
+ * design notes of the repository):
+ *   R1 weights: omega_j = 1/lambda_j, lambda_j = (kmax+kmin)/2 + (kmax-kmin)/2 *
+ *      cos((2j-1) pi / 2M), j = 1..M  (Chebyshev-Richardson; the paper's "transformation
+ *      of the zeros of a Chebyshev polynomial").  The sweep multiplies by w = omega/c.
+ *   R2 cycle length: M0 = ceil(acosh(1/tol) / acosh(sigma)), sigma = (kmax+kmin)/(kmax-kmin);
+ *      M = smallest power of two >= M0.
+ *   R3 order of the weights: recursive mirror pairing (1), then each index j of the
+ *      order for m is followed by its mirror 2m+1-j in the order for 2m.
+ *   R4 N in the kappa formulas is the number of intervals, Nx+1 (nodes 1..Nx, h = 1/(Nx+1)).
+ *   R5 5-point bounds: kmin = sin^2(pi/2(Nx+1)) + sin^2(pi/2(Ny+1)), kmax = 2.
+ *   R6 boundary: homogeneous Dirichlet; nodes 0 and N+1 hold 0; the 17-point stencil's
+ *      second ghost layer is the odd reflection u[-1] = -u[1], u[N+2] = -u[N].
+ *   R7 D is the constant stencil centre (-c in units of 1/h^2).
+ *   R8 stop test: relative L2 residual rho = ||b - L u||_2 / ||b||_2 <= tol, checked
+ *      before every cycle; u0 = 0 unless given.  If ||b|| = 0 the absolute norm is used.
+ *      rho cannot fall below the rounding floor of an FP64 u, about
+ *      fl = eps * S * ||u||_2 / ||b||_2 (eps = 2^-53, S = sum of |coefficients|), which is
+ *      ~5e-10 for the 9-point stencil on 4096^2; so the solve also stops, with the status
+ *      "floor", once rho <= 4 fl, or once a whole cycle fails to halve rho.
+ *   R9 evaluation order of the residual L u - b (any order is exact in real arithmetic):
+ *      horizontal pair sums p = u(i-1,.) + u(i+1,.), P = u(i-2,.) + u(i+2,.), vertical
+ *      pair sums v1 = u(i,j-1) + u(i,j+1), v2 = u(i,j-2) + u(i,j+2); axis groups
+ *      p(j) + v1, P(j) + v2; diagonal groups p(j-1) + p(j+1), P(j-2) + P(j+2); the
+ *      coefficients applied by nested fma, innermost fma(centre, u(i,j), -b).
+ *   R10 mixed precision (not in the paper; the FP32-inner / FP64-outer form): an outer
+ *      FP64 defect-correction loop r = b - L u, rt = (float) r, one FP32 CJM cycle of
+ *      length M_in on L e = rt from e = 0 with w32_n = (float)(omega_n / c), then
+ *      u <- u + (double) e.  The stop test is the FP64 residual of R8.
+ *
+ * Array convention: interior values only, row-major [Ny][Nx], value of node (i, j) at
+ * u[(j-1)*Nx + (i-1)].  Compiled with -ffp-contract=off so that every rounding is the
+ * one written here.
+ */
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define ORC_PI 3.14159265358979323846
+
+/* ---------------------------------------------------------------- stencils */
+
+/* Stencil radius: 1 for the 5- and 9-point stencils, 2 for the 17-point one. */
+int orc_radius(int st) { return st == 17 ? 2 : 1; }
+
+/* c = -(centre coefficient) of L = h^2 * Delta_h (Table 3, Eq. 1, Eq. 2). */
+double orc_centre(int st) {
+    if (st == 5) return 4.0;
+    if (st == 9) return 20.0 / 6.0;
+    return 300.0 / 72.0;
+}
+
+/* Value of node (i, j), with the homogeneous Dirichlet boundary and the odd
+ * reflection for the second ghost layer (reading R6). */
+static double at(const double *u, int Nx, int Ny, int i, int j) {
+    double s = 1.0;
+    if (i == 0 || i == Nx + 1 || j == 0 || j == Ny + 1) return 0.0;
+    if (i == -1) { i = 1; s = -s; } else if (i == Nx + 2) { i = Nx; s = -s; }
+    if (j == -1) { j = 1; s = -s; } else if (j == Ny + 2) { j = Ny; s = -s; }
+    return s * u[(size_t)(j - 1) * Nx + (i - 1)];
+}
+
+/* r = (L u)(i, j) - bk in units of 1/h^2, evaluated in the order of reading R9:
+ * horizontal pair sums p(j) = u(i-1,j) + u(i+1,j), P(j) = u(i-2,j) + u(i+2,j) and vertical
+ * pair sums v1 = u(i,j-1) + u(i,j+1), v2 = u(i,j-2) + u(i,j+2); the centre term and -bk
+ * sit in the innermost fma.  With bk = 0 it returns (L u)(i, j) exactly. */
+static double resid_at(int st, const double *u, int Nx, int Ny, int i, int j, double bk) {
+    double uC = at(u, Nx, Ny, i, j);
+    double v1 = at(u, Nx, Ny, i, j - 1) + at(u, Nx, Ny, i, j + 1);
+    double p0 = at(u, Nx, Ny, i - 1, j) + at(u, Nx, Ny, i + 1, j);
+    if (st == 5) {
+        /* Table 3, Cartesian, dx = dy = h: four neighbours with weight 1, centre -4. */
+        double a = p0 + v1;
+        return a + fma(-4.0, uC, -bk);
+    }
+    double pm = at(u, Nx, Ny, i - 1, j - 1) + at(u, Nx, Ny, i + 1, j - 1);
+    double pp = at(u, Nx, Ny, i - 1, j + 1) + at(u, Nx, Ny, i + 1, j + 1);
+    if (st == 9) {
+        /* Eq. 1: (1/6)[4 * edges + 1 * corners - 20 * centre]. */
+        double a = p0 + v1;
+        double d = pm + pp;
+        return fma(4.0 / 6.0, a, fma(1.0 / 6.0, d, fma(-20.0 / 6.0, uC, -bk)));
+    }
+    /* Eq. 2: (1/72)[64 * axis1 - 4 * axis2 + 16 * diag1 - 1 * diag2 - 300 * centre]. */
+    double v2 = at(u, Nx, Ny, i, j - 2) + at(u, Nx, Ny, i, j + 2);
+    double P0 = at(u, Nx, Ny, i - 2, j) + at(u, Nx, Ny, i + 2, j);
+    double Pm = at(u, Nx, Ny, i - 2, j - 2) + at(u, Nx, Ny, i + 2, j - 2);
+    double Pp = at(u, Nx, Ny, i - 2, j + 2) + at(u, Nx, Ny, i + 2, j + 2);
+    double a1 = p0 + v1;
+    double a2 = P0 + v2;
+    double d1 = pm + pp;
+    double d2 = Pm + Pp;
+    return fma(64.0 / 72.0, a1,
+               fma(-4.0 / 72.0, a2,
+                   fma(16.0 / 72.0, d1, fma(-1.0 / 72.0, d2, fma(-300.0 / 72.0, uC, -bk)))));
+}
+
+/* Lu = L u over the whole interior (the residual form with b = 0). */
+void orc_apply_L(int st, int Nx, int Ny, const double *u, double *Lu) {
+    for (int j = 1; j <= Ny; ++j)
+        for (int i = 1; i <= Nx; ++i)
+            Lu[(size_t)(j - 1) * Nx + (i - 1)] = resid_at(st, u, Nx, Ny, i, j, 0.0);
+}
+
+/* ---------------------------------------------------------------- plan */
+
+static double s2(double x) { double s = sin(x); return s * s; }
+
+/* Eigenvalue bounds of D^-1 A (Sec. 2.1).  Nint_x, Nint_y are the paper's N
+ * (number of intervals under reading R4; the paper-literal variant passes Nx). */
+void orc_kappa_bounds_n(int st, double Nint_x, double Nint_y, double *kmin, double *kmax) {
+    double tx = ORC_PI / (2.0 * Nint_x), ty = ORC_PI / (2.0 * Nint_y);
+    if (st == 5) {
+        /* reading R5, by the same Fourier analysis the paper applies to Eq. 1 and Eq. 2 */
+        *kmin = s2(tx) + s2(ty);
+        *kmax = 2.0;
+    } else if (st == 9) {
+        *kmin = (4.0 / 5.0) * (s2(tx) + s2(ty)) + (1.0 / 5.0) * (s2(tx + ty) + s2(tx - ty));
+        *kmax = 8.0 / 5.0;
+    } else {
+        double Tx = ORC_PI / Nint_x, Ty = ORC_PI / Nint_y;
+        *kmin = -(4.0 / 75.0) * (s2(Tx) + s2(Ty)) + (64.0 / 75.0) * (s2(tx) + s2(ty)) -
+                (1.0 / 75.0) * (s2(Tx + Ty) + s2(Tx - Ty)) +
+                (16.0 / 75.0) * (s2(tx + ty) + s2(tx - ty));
+        *kmax = 128.0 / 75.0;
+    }
+}
+
+void orc_kappa_bounds(int st, int Nx, int Ny, double *kmin, double *kmax) {
+    orc_kappa_bounds_n(st, (double)(Nx + 1), (double)(Ny + 1), kmin, kmax);
+}
+
+/* Smallest M0 with 1/T_M0(sigma) <= tol (reading R2, before rounding). */
+long orc_cycle_length_min(double kmin, double kmax, double tol) {
+    double delta = 2.0 * kmin / (kmax - kmin);               /* sigma - 1 */
+    double acosh_sigma = log1p(delta + sqrt(delta * (2.0 + delta)));
+    double need = log(1.0 / tol + sqrt(1.0 / (tol * tol) - 1.0)); /* acosh(1/tol) */
+    double m = ceil(need / acosh_sigma);
+    return m < 1.0 ? 1 : (long)m;
+}
+
+/* M = smallest power of two >= M0 (reading R2). */
+long orc_cycle_length(double kmin, double kmax, double tol) {
+    long m0 = orc_cycle_length_min(kmin, kmax, tol), m = 1;
+    while (m < m0) m *= 2;
+    return m;
+}
+
+/* Application order of the Chebyshev zeros for M = 2^p (reading R3): idx[n] in 1..M is
+ * the zero used at sweep n of a cycle.  Returns 0, or -1 if M is not a power of two. */
+int orc_order(long M, long *idx) {
+    if (M < 1 || (M & (M - 1)) != 0) return -1;
+    long *tmp = (long *)malloc(sizeof(long) * (size_t)M);
+    idx[0] = 1;
+    for (long m = 1; m < M; m *= 2) {
+        for (long k = 0; k < m; ++k) {
+            tmp[2 * k] = idx[k];
+            tmp[2 * k + 1] = 2 * m + 1 - idx[k];
+        }
+        memcpy(idx, tmp, sizeof(long) * (size_t)(2 * m));
+    }
+    free(tmp);
+    return 0;
+}
+
+/* Chebyshev-Jacobi weights omega_j for j = 1..M in natural order (reading R1). */
+void orc_weights_natural(double kmin, double kmax, long M, double *omega) {
+    double hs = 0.5 * (kmax + kmin), hd = 0.5 * (kmax - kmin);
+    for (long j = 1; j <= M; ++j) {
+        double x = cos((double)(2 * j - 1) * ORC_PI / (double)(2 * M));
+        double lam = hs + hd * x;
+        omega[j - 1] = 1.0 / lam;
+    }
+}
+
+/* Per-sweep coefficients w_n = omega_{idx[n]} / c in application order; the sweep
+ * is u <- u + w_n (L u - b).  Returns -1 if M is not a power of two. */
+int orc_sweep_coeffs(int st, double kmin, double kmax, long M, double *w) {
+    long *idx = (long *)malloc(sizeof(long) * (size_t)M);
+    if (orc_order(M, idx) != 0) { free(idx); return -1; }
+    double c = orc_centre(st);
+    double hs = 0.5 * (kmax + kmin), hd = 0.5 * (kmax - kmin);
+    for (long n = 0; n < M; ++n) {
+        long j = idx[n];
+        double x = cos((double)(2 * j - 1) * ORC_PI / (double)(2 * M));
+        double lam = hs + hd * x;
+        w[n] = 1.0 / (c * lam);
+    }
+    free(idx);
+    return 0;
+}
+
+/* ---------------------------------------------------------------- iteration */
+
+/* One weighted Jacobi sweep: u_out = u + w (L u - b)  (Sec. 2.1, with D = -c). */
+void orc_sweep(int st, int Nx, int Ny, const double *u, const double *b, double w,
+               double *u_out) {
+    for (int j = 1; j <= Ny; ++j)
+        for (int i = 1; i <= Nx; ++i) {
+            size_t k = (size_t)(j - 1) * Nx + (i - 1);
+            double r = resid_at(st, u, Nx, Ny, i, j, b[k]);
+            u_out[k] = fma(w, r, u[k]);
+        }
+}
+
+/* Sum of squares and max-abs of the residual L u - b over the interior. */
+void orc_residual(int st, int Nx, int Ny, const double *u, const double *b, double *l2sq,
+                  double *linf) {
+    double s = 0.0, m = 0.0;
+    for (int j = 1; j <= Ny; ++j)
+        for (int i = 1; i <= Nx; ++i) {
+            size_t k = (size_t)(j - 1) * Nx + (i - 1);
+            double r = resid_at(st, u, Nx, Ny, i, j, b[k]);
+            s += r * r;
+            if (fabs(r) > m) m = fabs(r);
+        }
+    *l2sq = s;
+    *linf = m;
+}
+
+/* b = h^2 f with h = 1/(Nx+1) (uniform mesh, Sec. 2.1). */
+void orc_scale_rhs(int Nx, int Ny, const double *f, double *b) {
+    double h = 1.0 / (double)(Nx + 1);
+    double h2 = h * h;
+    for (size_t k = 0; k < (size_t)Nx * (size_t)Ny; ++k) b[k] = h2 * f[k];
+}
+
+/* Sum of |coefficients| of L (S in reading R8). */
+double orc_abs_coeff_sum(int st) {
+    if (st == 5) return 8.0;
+    if (st == 9) return 40.0 / 6.0;
+    return 640.0 / 72.0;
+}
+
+/* Stop statuses of the solves (reading R8). */
+enum { ORC_CONVERGED = 0, ORC_FLOOR = 1, ORC_MAX_SWEEPS = 2, ORC_DIVERGED = 3 };
+
+/* Decide after a residual evaluation whether to stop; returns -1 to continue. */
+static int stop_rule(double rho, double floor_est, double rho_prev, long done_cycles, double tol) {
+    if (rho <= tol) return ORC_CONVERGED;
+    if (!(rho == rho) || rho > 1e300) return ORC_DIVERGED;
+    if (rho <= 4.0 * floor_est) return ORC_FLOOR;
+    if (done_cycles > 0 && rho > 0.5 * rho_prev) return ORC_FLOOR;
+    return -1;
+}
+
+/* Full CJM solve (Sec. 2.1 with readings R1-R8).  u holds the initial guess on entry
+ * and the result on exit.  The residual is tested before every cycle; a cycle is M
+ * sweeps with the weights in the order of R3.  Returns the number of sweeps done, or
+ * -1 on a bad argument.  *cycles, *rel_l2, *rel_linf describe the returned u; *status
+ * is one of ORC_CONVERGED, ORC_FLOOR, ORC_MAX_SWEEPS, ORC_DIVERGED. */
+long orc_solve(int st, int Nx, int Ny, const double *f, double tol, long max_sweeps,
+               double *u, double *rel_l2, double *rel_linf, long *cycles, int *status) {
+    if (Nx < 1 || Ny < 1 || !(tol > 0.0 && tol < 1.0)) return -1;
+    size_t n = (size_t)Nx * (size_t)Ny;
+    double kmin, kmax;
+    orc_kappa_bounds(st, Nx, Ny, &kmin, &kmax);
+    long M = orc_cycle_length(kmin, kmax, tol);
+    double *w = (double *)malloc(sizeof(double) * (size_t)M);
+    double *b = (double *)malloc(sizeof(double) * n);
+    double *v = (double *)malloc(sizeof(double) * n);
+    orc_sweep_coeffs(st, kmin, kmax, M, w);
+    orc_scale_rhs(Nx, Ny, f, b);
+    double bsq = 0.0, bmax = 0.0;
+    for (size_t k = 0; k < n; ++k) {
+        bsq += b[k] * b[k];
+        if (fabs(b[k]) > bmax) bmax = fabs(b[k]);
+    }
+    double bn = sqrt(bsq), eps = ldexp(1.0, -53), S = orc_abs_coeff_sum(st);
+    long sweeps = 0, cyc = 0;
+    int stat;
+    double rl2 = 0.0, rinf = 0.0, prev = 0.0;
+    for (;;) {
+        double sq, mx, usq = 0.0;
+        orc_residual(st, Nx, Ny, u, b, &sq, &mx);
+        for (size_t k = 0; k < n; ++k) usq += u[k] * u[k];
+        rl2 = bn > 0.0 ? sqrt(sq) / bn : sqrt(sq);
+        rinf = bmax > 0.0 ? mx / bmax : mx;
+        double fl = bn > 0.0 ? eps * S * sqrt(usq) / bn : eps * S * sqrt(usq);
+        stat = stop_rule(rl2, fl, prev, cyc, tol);
+        if (stat >= 0) break;
+        if (sweeps + M > max_sweeps) { stat = ORC_MAX_SWEEPS; break; }
+        for (long s = 0; s < M; ++s) {
+            orc_sweep(st, Nx, Ny, u, b, w[s], v);
+            memcpy(u, v, sizeof(double) * n);
+        }
+        sweeps += M;
+        cyc += 1;
+        prev = rl2;
+    }
+    free(w); free(b); free(v);
+    *rel_l2 = rl2;
+    *rel_linf = rinf;
+    *cycles = cyc;
+    *status = stat;
+    return sweeps;
+}
+
+/* ---------------------------------------------------------------- FP32 inner form */
+
+static float at32(const float *u, int Nx, int Ny, int i, int j) {
+    float s = 1.0f;
+    if (i == 0 || i == Nx + 1 || j == 0 || j == Ny + 1) return 0.0f;
+    if (i == -1) { i = 1; s = -s; } else if (i == Nx + 2) { i = Nx; s = -s; }
+    if (j == -1) { j = 1; s = -s; } else if (j == Ny + 2) { j = Ny; s = -s; }
+    return s * u[(size_t)(j - 1) * Nx + (i - 1)];
+}
+
+/* r = (L e)(i, j) - rk in FP32, same grouping as resid_at; the coefficients are the
+ * FP32 quotients (e.g. 4.0f/6.0f). */
+static float resid_at32(int st, const float *u, int Nx, int Ny, int i, int j, float rk) {
+    float uC = at32(u, Nx, Ny, i, j);
+    float v1 = at32(u, Nx, Ny, i, j - 1) + at32(u, Nx, Ny, i, j + 1);
+    float p0 = at32(u, Nx, Ny, i - 1, j) + at32(u, Nx, Ny, i + 1, j);
+    if (st == 5) {
+        float a = p0 + v1;
+        return a + fmaf(-4.0f, uC, -rk);
+    }
+    float pm = at32(u, Nx, Ny, i - 1, j - 1) + at32(u, Nx, Ny, i + 1, j - 1);
+    float pp = at32(u, Nx, Ny, i - 1, j + 1) + at32(u, Nx, Ny, i + 1, j + 1);
+    if (st == 9) {
+        float a = p0 + v1;
+        float d = pm + pp;
+        return fmaf(4.0f / 6.0f, a, fmaf(1.0f / 6.0f, d, fmaf(-20.0f / 6.0f, uC, -rk)));
+    }
+    float v2 = at32(u, Nx, Ny, i, j - 2) + at32(u, Nx, Ny, i, j + 2);
+    float P0 = at32(u, Nx, Ny, i - 2, j) + at32(u, Nx, Ny, i + 2, j);
+    float Pm = at32(u, Nx, Ny, i - 2, j - 2) + at32(u, Nx, Ny, i + 2, j - 2);
+    float Pp = at32(u, Nx, Ny, i - 2, j + 2) + at32(u, Nx, Ny, i + 2, j + 2);
+    float a1 = p0 + v1;
+    float a2 = P0 + v2;
+    float d1 = pm + pp;
+    float d2 = Pm + Pp;
+    return fmaf(64.0f / 72.0f, a1,
+                fmaf(-4.0f / 72.0f, a2,
+                     fmaf(16.0f / 72.0f, d1,
+                          fmaf(-1.0f / 72.0f, d2, fmaf(-300.0f / 72.0f, uC, -rk)))));
+}
+
+/* One FP32 weighted sweep e_out = e + w (L e - r). */
+void orc_sweep_f32(int st, int Nx, int Ny, const float *e, const float *r, float w,
+                   float *e_out) {
+    for (int j = 1; j <= Ny; ++j)
+        for (int i = 1; i <= Nx; ++i) {
+            size_t k = (size_t)(j - 1) * Nx + (i - 1);
+            float d = resid_at32(st, e, Nx, Ny, i, j, r[k]);
+            e_out[k] = fmaf(w, d, e[k]);
+        }
+}
+
+/* FP64 defect r = b - L u, its square sum and max-abs, and the FP32 copy rt. */
+void orc_defect(int st, int Nx, int Ny, const double *u, const double *b, float *rt,
+                double *l2sq, double *linf) {
+    double s = 0.0, m = 0.0;
+    for (int j = 1; j <= Ny; ++j)
+        for (int i = 1; i <= Nx; ++i) {
+            size_t k = (size_t)(j - 1) * Nx + (i - 1);
+            double r = resid_at(st, u, Nx, Ny, i, j, b[k]);
+            rt[k] = (float)(-r);
+            s += r * r;
+            if (fabs(r) > m) m = fabs(r);
+        }
+    *l2sq = s;
+    *linf = m;
+}
+
+/* Mixed-precision CJM (reading R10).  M_in is the inner cycle length (a power of two).
+ * u: initial guess in, result out.  Returns the number of FP32 sweeps, or -1 on a bad
+ * argument; *outer counts the defect-correction steps; *status as for orc_solve, with
+ * an outer step in the role of a cycle. */
+long orc_solve_mixed(int st, int Nx, int Ny, const double *f, double tol, long M_in,
+                     long max_outer, double *u, double *rel_l2, double *rel_linf,
+                     long *outer, int *status) {
+    if (Nx < 1 || Ny < 1 || !(tol > 0.0 && tol < 1.0) || M_in < 1) return -1;
+    size_t n = (size_t)Nx * (size_t)Ny;
+    double kmin, kmax;
+    orc_kappa_bounds(st, Nx, Ny, &kmin, &kmax);
+    double *w = (double *)malloc(sizeof(double) * (size_t)M_in);
+    if (orc_sweep_coeffs(st, kmin, kmax, M_in, w) != 0) { free(w); return -1; }
+    float *w32 = (float *)malloc(sizeof(float) * (size_t)M_in);
+    for (long s = 0; s < M_in; ++s) w32[s] = (float)w[s];
+    double *b = (double *)malloc(sizeof(double) * n);
+    float *rt = (float *)malloc(sizeof(float) * n);
+    float *e = (float *)malloc(sizeof(float) * n);
+    float *e2 = (float *)malloc(sizeof(float) * n);
+    orc_scale_rhs(Nx, Ny, f, b);
+    double bsq = 0.0, bmax = 0.0;
+    for (size_t k = 0; k < n; ++k) {
+        bsq += b[k] * b[k];
+        if (fabs(b[k]) > bmax) bmax = fabs(b[k]);
+    }
+    double bn = sqrt(bsq), eps = ldexp(1.0, -53), S = orc_abs_coeff_sum(st);
+    long sweeps = 0, out = 0;
+    int stat;
+    double rl2 = 0.0, rinf = 0.0, prev = 0.0;
+    for (;;) {
+        double sq, mx, usq = 0.0;
+        orc_defect(st, Nx, Ny, u, b, rt, &sq, &mx);
+        for (size_t k = 0; k < n; ++k) usq += u[k] * u[k];
+        rl2 = bn > 0.0 ? sqrt(sq) / bn : sqrt(sq);
+        rinf = bmax > 0.0 ? mx / bmax : mx;
+        double fl = bn > 0.0 ? eps * S * sqrt(usq) / bn : eps * S * sqrt(usq);
+        stat = stop_rule(rl2, fl, prev, out, tol);
+        if (stat >= 0) break;
+        if (out >= max_outer) { stat = ORC_MAX_SWEEPS; break; }
+        prev = rl2;
+        memset(e, 0, sizeof(float) * n);
+        for (long s = 0; s < M_in; ++s) {
+            orc_sweep_f32(st, Nx, Ny, e, rt, w32[s], e2);
+            memcpy(e, e2, sizeof(float) * n);
+        }
+        for (size_t k = 0; k < n; ++k) u[k] = u[k] + (double)e[k];
+        sweeps += M_in;
+        out += 1;
+    }
+    free(w); free(w32); free(b); free(rt); free(e); free(e2);
+    *rel_l2 = rl2;
+    *rel_linf = rinf;
+    *outer = out;
+    *status = stat;
+    return sweeps;
+}

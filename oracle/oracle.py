@@ -1,0 +1,227 @@
+"""ctypes front end of the plain C FP64 Chebyshev-Jacobi oracle (``cj_oracle.c``).
+
+TEST INFRASTRUCTURE ONLY: the test-suite, the smoke check and the CPU-baseline leg of
+the benchmark may use this module; the product library never imports it.
+
+Arrays follow the oracle's convention: interior values, shape ``(Ny, Nx)``, C order,
+``float64`` (``float32`` for the FP32 inner form).  Every function cites the passage of
+the paper it follows in ``cj_oracle.c``.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "cj_oracle.c")
+_LIB = os.path.join(_HERE, "_build", "libcj_oracle.so")
+
+_dp = ctypes.POINTER(ctypes.c_double)
+_fp = ctypes.POINTER(ctypes.c_float)
+_lp = ctypes.POINTER(ctypes.c_long)
+_ip = ctypes.POINTER(ctypes.c_int)
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (``-ffp-contract=off``: no silent FMA contraction)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        os.makedirs(os.path.dirname(_LIB), exist_ok=True)
+        tmp = _LIB + ".%d.tmp" % os.getpid()
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fPIC", "-shared",
+                               "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        L = ctypes.CDLL(build())
+        L.orc_radius.argtypes = [ctypes.c_int]
+        L.orc_radius.restype = ctypes.c_int
+        L.orc_centre.argtypes = [ctypes.c_int]
+        L.orc_centre.restype = ctypes.c_double
+        L.orc_apply_L.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, _dp, _dp]
+        L.orc_kappa_bounds.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, _dp, _dp]
+        L.orc_kappa_bounds_n.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double, _dp, _dp]
+        L.orc_cycle_length_min.argtypes = [ctypes.c_double, ctypes.c_double, ctypes.c_double]
+        L.orc_cycle_length_min.restype = ctypes.c_long
+        L.orc_cycle_length.argtypes = [ctypes.c_double, ctypes.c_double, ctypes.c_double]
+        L.orc_cycle_length.restype = ctypes.c_long
+        L.orc_order.argtypes = [ctypes.c_long, _lp]
+        L.orc_order.restype = ctypes.c_int
+        L.orc_weights_natural.argtypes = [ctypes.c_double, ctypes.c_double, ctypes.c_long, _dp]
+        L.orc_sweep_coeffs.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_long, _dp]
+        L.orc_sweep_coeffs.restype = ctypes.c_int
+        L.orc_sweep.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, _dp, _dp, ctypes.c_double, _dp]
+        L.orc_residual.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, _dp, _dp, _dp, _dp]
+        L.orc_scale_rhs.argtypes = [ctypes.c_int, ctypes.c_int, _dp, _dp]
+        L.orc_solve.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, _dp, ctypes.c_double,
+                                ctypes.c_long, _dp, _dp, _dp, _lp, _ip]
+        L.orc_solve.restype = ctypes.c_long
+        L.orc_abs_coeff_sum.argtypes = [ctypes.c_int]
+        L.orc_abs_coeff_sum.restype = ctypes.c_double
+        L.orc_sweep_f32.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, _fp, _fp, ctypes.c_float, _fp]
+        L.orc_defect.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, _dp, _dp, _fp, _dp, _dp]
+        L.orc_solve_mixed.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, _dp, ctypes.c_double,
+                                      ctypes.c_long, ctypes.c_long, _dp, _dp, _dp, _lp, _ip]
+        L.orc_solve_mixed.restype = ctypes.c_long
+        _lib = L
+    return _lib
+
+
+def _d(a):
+    return a.ctypes.data_as(_dp)
+
+
+def _f(a):
+    return a.ctypes.data_as(_fp)
+
+
+def _grid(a, dtype=np.float64):
+    a = np.ascontiguousarray(a, dtype=dtype)
+    assert a.ndim == 2
+    return a
+
+
+def radius(st: int) -> int:
+    return lib().orc_radius(st)
+
+
+def centre(st: int) -> float:
+    """c = -(centre coefficient of h^2 Delta_h)."""
+    return lib().orc_centre(st)
+
+
+def apply_L(st: int, u: np.ndarray) -> np.ndarray:
+    """L u = h^2 Delta_h u with the homogeneous Dirichlet / odd-reflection boundary."""
+    u = _grid(u)
+    out = np.empty_like(u)
+    lib().orc_apply_L(st, u.shape[1], u.shape[0], _d(u), _d(out))
+    return out
+
+
+def kappa_bounds(st: int, Nx: int, Ny: int, literal_n: bool = False):
+    """(kmin, kmax) of D^-1 A (Sec. 2.1); ``literal_n`` uses N = Nx instead of Nx+1."""
+    a, b = ctypes.c_double(), ctypes.c_double()
+    if literal_n:
+        lib().orc_kappa_bounds_n(st, float(Nx), float(Ny), ctypes.byref(a), ctypes.byref(b))
+    else:
+        lib().orc_kappa_bounds(st, Nx, Ny, ctypes.byref(a), ctypes.byref(b))
+    return a.value, b.value
+
+
+def cycle_length_min(kmin: float, kmax: float, tol: float) -> int:
+    return lib().orc_cycle_length_min(kmin, kmax, tol)
+
+
+def cycle_length(kmin: float, kmax: float, tol: float) -> int:
+    return lib().orc_cycle_length(kmin, kmax, tol)
+
+
+def order(M: int) -> np.ndarray:
+    idx = np.zeros(M, dtype=np.int64)
+    rc = lib().orc_order(M, idx.ctypes.data_as(_lp))
+    if rc != 0:
+        raise ValueError("M must be a power of two")
+    return idx
+
+
+def weights_natural(kmin: float, kmax: float, M: int) -> np.ndarray:
+    w = np.zeros(M)
+    lib().orc_weights_natural(kmin, kmax, M, _d(w))
+    return w
+
+
+def sweep_coeffs(st: int, kmin: float, kmax: float, M: int) -> np.ndarray:
+    """w_n = omega_n / c in application order."""
+    w = np.zeros(M)
+    if lib().orc_sweep_coeffs(st, kmin, kmax, M, _d(w)) != 0:
+        raise ValueError("M must be a power of two")
+    return w
+
+
+def sweep(st: int, u: np.ndarray, b: np.ndarray, w: float) -> np.ndarray:
+    u = _grid(u)
+    b = _grid(b)
+    out = np.empty_like(u)
+    lib().orc_sweep(st, u.shape[1], u.shape[0], _d(u), _d(b), float(w), _d(out))
+    return out
+
+
+def residual(st: int, u: np.ndarray, b: np.ndarray):
+    """(sum of squares, max-abs) of L u - b."""
+    u = _grid(u)
+    b = _grid(b)
+    s, m = ctypes.c_double(), ctypes.c_double()
+    lib().orc_residual(st, u.shape[1], u.shape[0], _d(u), _d(b), ctypes.byref(s), ctypes.byref(m))
+    return s.value, m.value
+
+
+def scale_rhs(f: np.ndarray) -> np.ndarray:
+    f = _grid(f)
+    b = np.empty_like(f)
+    lib().orc_scale_rhs(f.shape[1], f.shape[0], _d(f), _d(b))
+    return b
+
+
+STATUS = {0: "converged", 1: "floor", 2: "max_sweeps", 3: "diverged"}
+
+
+def abs_coeff_sum(st: int) -> float:
+    return lib().orc_abs_coeff_sum(st)
+
+
+def solve(st: int, f: np.ndarray, tol: float, u0: np.ndarray | None = None,
+          max_sweeps: int = 1 << 40) -> dict:
+    """Full FP64 CJM solve of Delta_h u = f; returns u and the run's counters."""
+    f = _grid(f)
+    u = np.zeros_like(f) if u0 is None else _grid(u0).copy()
+    rl2, rinf = ctypes.c_double(), ctypes.c_double()
+    cyc, stat = ctypes.c_long(), ctypes.c_int()
+    n = lib().orc_solve(st, f.shape[1], f.shape[0], _d(f), tol, max_sweeps, _d(u),
+                        ctypes.byref(rl2), ctypes.byref(rinf), ctypes.byref(cyc), ctypes.byref(stat))
+    if n < 0:
+        raise ValueError("bad argument")
+    return dict(u=u, sweeps=n, cycles=cyc.value, rel_l2=rl2.value, rel_linf=rinf.value,
+                status=STATUS[stat.value], converged=stat.value == 0)
+
+
+def sweep_f32(st: int, e: np.ndarray, r: np.ndarray, w: float) -> np.ndarray:
+    e = _grid(e, np.float32)
+    r = _grid(r, np.float32)
+    out = np.empty_like(e)
+    lib().orc_sweep_f32(st, e.shape[1], e.shape[0], _f(e), _f(r), ctypes.c_float(w), _f(out))
+    return out
+
+
+def defect(st: int, u: np.ndarray, b: np.ndarray):
+    """(rt = float32(b - L u), sum of squares, max-abs) in FP64."""
+    u = _grid(u)
+    b = _grid(b)
+    rt = np.empty(u.shape, np.float32)
+    s, m = ctypes.c_double(), ctypes.c_double()
+    lib().orc_defect(st, u.shape[1], u.shape[0], _d(u), _d(b), _f(rt), ctypes.byref(s), ctypes.byref(m))
+    return rt, s.value, m.value
+
+
+def solve_mixed(st: int, f: np.ndarray, tol: float, M_in: int, u0: np.ndarray | None = None,
+                max_outer: int = 1000) -> dict:
+    """FP32-inner / FP64-outer defect-correction CJM."""
+    f = _grid(f)
+    u = np.zeros_like(f) if u0 is None else _grid(u0).copy()
+    rl2, rinf = ctypes.c_double(), ctypes.c_double()
+    outer, stat = ctypes.c_long(), ctypes.c_int()
+    n = lib().orc_solve_mixed(st, f.shape[1], f.shape[0], _d(f), tol, M_in, max_outer, _d(u),
+                              ctypes.byref(rl2), ctypes.byref(rinf), ctypes.byref(outer),
+                              ctypes.byref(stat))
+    if n < 0:
+        raise ValueError("bad argument")
+    return dict(u=u, sweeps=n, outer=outer.value, rel_l2=rl2.value, rel_linf=rinf.value,
+                status=STATUS[stat.value], converged=stat.value == 0)

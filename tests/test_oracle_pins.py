@@ -1,0 +1,463 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix.
+
+Nothing here compares the oracle with itself: every expected value comes from the
+paper's printed coefficients and bounds (tests/golden/), from a closed form (Chebyshev
+polynomials, the stencil symbol, the discrete sine transform), from a dense linear-algebra
+routine on a small grid, or from the continuum solution of a manufactured problem.
+"""
+import os
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+from oracle import oracle as orc
+import workloads
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+STENCILS = (5, 9, 17)
+
+
+def _golden_coeffs():
+    tab = {}
+    with open(os.path.join(GOLDEN, "stencil_coefficients.txt")) as fh:
+        for line in fh:
+            line = line.split("#")[0].strip()
+            if not line:
+                continue
+            st, dx, dy, v = line.split()
+            tab.setdefault(int(st), {})[(int(dx), int(dy))] = float(Fraction(v))
+    return tab
+
+
+COEF = _golden_coeffs()
+
+
+def symbol(st, theta, phi):
+    """Fourier symbol of h^2 Delta_h built from the paper's printed coefficients."""
+    return sum(c * np.cos(dx * theta + dy * phi) for (dx, dy), c in COEF[st].items())
+
+
+def kappa_sym(st, theta, phi):
+    """Eigenvalue of D^-1 A for the mode (theta, phi), D = centre coefficient."""
+    return symbol(st, theta, phi) / COEF[st][(0, 0)]
+
+
+def dense_L(st, Nx, Ny):
+    n = Nx * Ny
+    A = np.zeros((n, n))
+    for k in range(n):
+        e = np.zeros(n)
+        e[k] = 1.0
+        A[:, k] = orc.apply_L(st, e.reshape(Ny, Nx)).ravel()
+    return A
+
+
+def sine_mode(Nx, Ny, k, l):
+    i = np.arange(1, Nx + 1)
+    j = np.arange(1, Ny + 1)
+    return np.outer(np.sin(l * np.pi * j / (Ny + 1)), np.sin(k * np.pi * i / (Nx + 1)))
+
+
+def cheb_T(M, x):
+    x = float(x)
+    if abs(x) <= 1.0:
+        return np.cos(M * np.arccos(x))
+    s = 1.0 if x > 0 or M % 2 == 0 else -1.0
+    return s * np.cosh(M * np.arccosh(abs(x)))
+
+
+# ----------------------------------------------------------------- stencils
+
+@pytest.mark.parametrize("st", STENCILS)
+def test_stencil_matches_paper_coefficients(st):
+    """A unit impulse far from the boundary returns the printed coefficients (L is
+    symmetric, so the response at offset (dx, dy) is the coefficient there)."""
+    N = 9
+    u = np.zeros((N, N))
+    u[4, 4] = 1.0
+    Lu = orc.apply_L(st, u)
+    expect = np.zeros((N, N))
+    for (dx, dy), c in COEF[st].items():
+        expect[4 + dy, 4 + dx] = c
+    np.testing.assert_allclose(Lu, expect, rtol=0, atol=1e-15)
+    assert orc.centre(st) == pytest.approx(-COEF[st][(0, 0)], rel=1e-15)
+    assert orc.radius(st) == max(max(abs(dx), abs(dy)) for dx, dy in COEF[st])
+
+
+@pytest.mark.parametrize("st", STENCILS)
+@pytest.mark.parametrize("Nx,Ny", [(7, 5), (6, 9), (11, 8)])
+def test_sine_modes_are_eigenvectors(st, Nx, Ny):
+    """With the Dirichlet / odd-reflection boundary every discrete sine mode is an exact
+    eigenvector of L with eigenvalue symbol(k pi/(Nx+1), l pi/(Ny+1))."""
+    for k, l in [(1, 1), (2, 3), (Nx, 1), (1, Ny), (Nx, Ny), (3, 2)]:
+        s = sine_mode(Nx, Ny, k, l)
+        lam = symbol(st, k * np.pi / (Nx + 1), l * np.pi / (Ny + 1))
+        np.testing.assert_allclose(orc.apply_L(st, s), lam * s, rtol=0, atol=1e-13)
+
+
+@pytest.mark.parametrize("st", STENCILS)
+def test_dense_L_symmetric(st):
+    A = dense_L(st, 6, 5)
+    np.testing.assert_allclose(A, A.T, rtol=0, atol=1e-15)
+
+
+# ----------------------------------------------------------------- kappa bounds
+
+@pytest.mark.parametrize("st", STENCILS)
+@pytest.mark.parametrize("Nx,Ny", [(4, 4), (7, 5), (10, 12), (12, 9)])
+def test_kappa_bounds_vs_dense_eigenvalues(st, Nx, Ny):
+    """kmin is the smallest eigenvalue of D^-1 A exactly; kmax bounds the largest."""
+    kmin, kmax = orc.kappa_bounds(st, Nx, Ny)
+    ev = np.linalg.eigvalsh(dense_L(st, Nx, Ny) / COEF[st][(0, 0)])
+    assert kmin == pytest.approx(ev.min(), rel=1e-12)
+    assert ev.max() <= kmax * (1 + 1e-14)
+
+
+@pytest.mark.parametrize("st", STENCILS)
+@pytest.mark.parametrize("Nx,Ny", [(16, 16), (64, 64), (1023, 1023), (4096, 4096), (8192, 8192),
+                                   (100, 37), (37, 2048)])
+def test_kappa_min_formula_equals_symbol(st, Nx, Ny):
+    """The paper's sin^2 expressions (N -> Nx+1) equal the symbol at the lowest mode (the
+    symbol summed in 40-digit arithmetic: in doubles its cosines cancel badly)."""
+    mp = pytest.importorskip("mpmath")
+    mp.mp.dps = 40
+    kmin, _ = orc.kappa_bounds(st, Nx, Ny)
+    th, ph = mp.pi / (Nx + 1), mp.pi / (Ny + 1)
+    sym = sum(mp.mpf(c) * mp.cos(dx * th + dy * ph) for (dx, dy), c in COEF[st].items())
+    ref = float(sym / mp.mpf(COEF[st][(0, 0)]))
+    assert kmin == pytest.approx(ref, rel=1e-12)
+
+
+@pytest.mark.parametrize("st", STENCILS)
+def test_kappa_max_is_symbol_supremum(st):
+    _, kmax = orc.kappa_bounds(st, 64, 64)
+    t = np.linspace(0, np.pi, 1201)
+    T, P = np.meshgrid(t, t)
+    sup = kappa_sym(st, T, P).max()
+    assert kmax == pytest.approx(sup, rel=1e-12)
+    with open(os.path.join(GOLDEN, "kappa_max.txt")) as fh:
+        for line in fh:
+            line = line.split("#")[0].strip()
+            if line and int(line.split()[0]) == st:
+                assert kmax == pytest.approx(float(Fraction(line.split()[1])), rel=1e-15)
+
+
+def test_kappa_literal_n_convention_differs():
+    """The paper-literal N = Nx variant is kept for ablation; it is not the exact bound."""
+    a, _ = orc.kappa_bounds(9, 63, 63)
+    b, _ = orc.kappa_bounds(9, 63, 63, literal_n=True)
+    ref = kappa_sym(9, np.pi / 64, np.pi / 64)
+    assert a == pytest.approx(ref, rel=1e-12)
+    assert b > a * 1.02
+
+
+# ----------------------------------------------------------------- weights / plan
+
+@pytest.mark.parametrize("M", [1, 2, 4, 8, 64, 256])
+def test_weight_product_is_scaled_chebyshev(M):
+    """prod_n (1 - omega_n lam) = T_M((kmax+kmin-2 lam)/(kmax-kmin)) / T_M(sigma)."""
+    mp = pytest.importorskip("mpmath")
+    mp.mp.dps = 50
+    st = 9
+    kmin, kmax = orc.kappa_bounds(st, 40, 30)
+    omega = orc.sweep_coeffs(st, kmin, kmax, M) * orc.centre(st)
+    sig = (kmax + kmin) / (kmax - kmin)
+    rng = np.random.default_rng(M)
+    lams = [kmin, kmax, 0.5 * (kmin + kmax), 0.5 * kmin, 1.2 * kmax] + list(rng.uniform(kmin, kmax, 6))
+    for lam in lams:
+        prod = mp.mpf(1)
+        for w in omega:
+            prod *= 1 - mp.mpf(float(w)) * mp.mpf(lam)
+        x = (mp.mpf(kmax) + kmin - 2 * mp.mpf(lam)) / (mp.mpf(kmax) - kmin)
+        ref = mp.chebyt(M, x) / mp.chebyt(M, mp.mpf(sig))
+        assert abs(prod - ref) <= 1e-8 * max(abs(ref), mp.mpf(1) / mp.chebyt(M, mp.mpf(sig)))
+
+
+def test_single_weight_is_optimal_stationary_jacobi():
+    """M = 1 reduces to weighted Jacobi with omega = 2/(kmin + kmax)."""
+    for st in STENCILS:
+        kmin, kmax = orc.kappa_bounds(st, 20, 20)
+        w = orc.sweep_coeffs(st, kmin, kmax, 1)
+        assert w[0] * orc.centre(st) == pytest.approx(2.0 / (kmin + kmax), rel=1e-15)
+
+
+@pytest.mark.parametrize("M", [1, 2, 4, 16, 512, 8192])
+def test_order_is_mirror_paired_permutation(M):
+    o = orc.order(M)
+    assert sorted(o.tolist()) == list(range(1, M + 1))
+    if M >= 2:
+        assert np.all(o[0::2] + o[1::2] == M + 1)
+
+
+def test_order_rejects_non_power_of_two():
+    with pytest.raises(ValueError):
+        orc.order(12)
+
+
+def test_order_keeps_partial_products_bounded():
+    """Rounding amplification (max partial product over the spectrum) stays modest in the
+    pairing order; in sorted order it is astronomically large."""
+    st = 5
+    kmin, kmax = orc.kappa_bounds(st, 64, 64)
+    M = 512
+    w = orc.sweep_coeffs(st, kmin, kmax, M) * orc.centre(st)
+    lam = np.concatenate([np.linspace(kmin, kmax, 3000), [kmin, kmax]])
+
+    def growth(ws):
+        p = np.ones_like(lam)
+        g = 0.0
+        for x in ws:
+            p *= 1 - x * lam
+            g = max(g, np.abs(p).max())
+        return g
+
+    # prefix products (w) and suffix products (w reversed) both stay bounded ...
+    assert growth(w) < 1e4 and growth(w[::-1]) < 1e4
+    # ... while sorted order has astronomically large suffix products
+    assert growth(np.sort(w)[::-1]) > 1e100
+
+
+@pytest.mark.parametrize("st", STENCILS)
+@pytest.mark.parametrize("N,tol", [(64, 1e-10), (4096, 1e-10), (8192, 1e-10), (300, 1e-6), (33, 1e-8)])
+def test_cycle_length_is_minimal_chebyshev_degree(st, N, tol):
+    mp = pytest.importorskip("mpmath")
+    mp.mp.dps = 40
+    kmin, kmax = orc.kappa_bounds(st, N, N)
+    sig = (mp.mpf(kmax) + kmin) / (mp.mpf(kmax) - kmin)
+    M0 = orc.cycle_length_min(kmin, kmax, tol)
+    assert 1 / mp.cosh(M0 * mp.acosh(sig)) <= tol
+    assert M0 == 1 or 1 / mp.cosh((M0 - 1) * mp.acosh(sig)) > tol
+    M = orc.cycle_length(kmin, kmax, tol)
+    assert M & (M - 1) == 0 and M >= M0 and (M == 1 or M // 2 < M0)
+
+
+def test_cycle_lengths_of_the_workloads():
+    """M of the 5-point 64^2, 9-point 4096^2 and 17-point 8192^2 problems at tol 1e-10."""
+    for st, N, M0_range, M in [(5, 64, (400, 600), 512), (9, 4096, (20000, 32768), 32768),
+                               (17, 8192, (40000, 65536), 65536)]:
+        kmin, kmax = orc.kappa_bounds(st, N, N)
+        M0 = orc.cycle_length_min(kmin, kmax, 1e-10)
+        assert M0_range[0] <= M0 <= M0_range[1]
+        assert orc.cycle_length(kmin, kmax, 1e-10) == M
+
+
+# ----------------------------------------------------------------- sweeps
+
+@pytest.mark.parametrize("st", [5, 9])
+def test_unit_weight_sweep_is_classical_jacobi(st):
+    """omega = 1 (w = 1/c) is classical Jacobi: u_i <- (b_i - sum_{j!=i} A_ij u_j) / A_ii."""
+    Nx, Ny = 7, 6
+    A = dense_L(st, Nx, Ny)
+    rng = np.random.default_rng(3)
+    u = rng.standard_normal((Ny, Nx))
+    b = rng.standard_normal((Ny, Nx))
+    d = np.diag(A)
+    ref = (b.ravel() - (A - np.diag(d)) @ u.ravel()) / d
+    out = orc.sweep(st, u, b, 1.0 / orc.centre(st))
+    np.testing.assert_allclose(out.ravel(), ref, rtol=0, atol=1e-13)
+
+
+def test_17pt_jacobi_uses_constant_centre():
+    """For the 17-point stencil the Jacobi D is the constant centre -c (reading R7), not the
+    dense diagonal that folds in the reflected ghost."""
+    st, Nx, Ny = 17, 7, 6
+    A = dense_L(st, Nx, Ny)
+    rng = np.random.default_rng(4)
+    u = rng.standard_normal((Ny, Nx))
+    b = rng.standard_normal((Ny, Nx))
+    c = -COEF[st][(0, 0)]
+    ref = (b.ravel() - (A + c * np.eye(A.shape[0])) @ u.ravel()) / (-c)
+    out = orc.sweep(st, u, b, 1.0 / orc.centre(st))
+    np.testing.assert_allclose(out.ravel(), ref, rtol=0, atol=1e-13)
+    assert not np.allclose(np.diag(A), -c)
+
+
+@pytest.mark.parametrize("st", STENCILS)
+def test_residual_norms_vs_dense(st):
+    Nx, Ny = 9, 7
+    A = dense_L(st, Nx, Ny)
+    rng = np.random.default_rng(5)
+    u = rng.standard_normal((Ny, Nx))
+    b = rng.standard_normal((Ny, Nx))
+    s, m = orc.residual(st, u, b)
+    r = A @ u.ravel() - b.ravel()
+    assert s == pytest.approx(np.sum(r * r), rel=1e-13)
+    assert m == pytest.approx(np.abs(r).max(), rel=1e-13)
+
+
+@pytest.mark.parametrize("st", STENCILS)
+def test_one_cycle_on_a_sine_mode(st):
+    """With b = 0, one cycle multiplies the mode s_kl by T_M(x_kl)/T_M(sigma) exactly."""
+    Nx, Ny, M = 20, 16, 64
+    kmin, kmax = orc.kappa_bounds(st, Nx, Ny)
+    w = orc.sweep_coeffs(st, kmin, kmax, M)
+    sig = (kmax + kmin) / (kmax - kmin)
+    for k, l in [(1, 1), (3, 5), (Nx, Ny), (7, 2)]:
+        s = sine_mode(Nx, Ny, k, l)
+        u = s.copy()
+        zero = np.zeros_like(s)
+        for wn in w:
+            u = orc.sweep(st, u, zero, wn)
+        kap = kappa_sym(st, k * np.pi / (Nx + 1), l * np.pi / (Ny + 1))
+        g = cheb_T(M, (kmax + kmin - 2 * kap) / (kmax - kmin)) / cheb_T(M, sig)
+        np.testing.assert_allclose(u, g * s, rtol=0, atol=1e-11)
+
+
+@pytest.mark.parametrize("st", STENCILS)
+def test_one_cycle_residual_bound(st):
+    Nx, Ny = 40, 33
+    f = workloads.smooth_random_rhs(Nx, Ny, seed=11, kmax=40)
+    b = orc.scale_rhs(f)
+    kmin, kmax = orc.kappa_bounds(st, Nx, Ny)
+    M = orc.cycle_length(kmin, kmax, 1e-6)
+    w = orc.sweep_coeffs(st, kmin, kmax, M)
+    u = np.zeros_like(b)
+    for wn in w:
+        u = orc.sweep(st, u, b, wn)
+    s, _ = orc.residual(st, u, b)
+    rho = np.sqrt(s) / np.linalg.norm(b)
+    sig = (kmax + kmin) / (kmax - kmin)
+    assert rho <= 1.0 / np.cosh(M * np.arccosh(sig)) * (1 + 1e-6) + 1e-13
+
+
+def test_scale_rhs_is_h_squared():
+    f = np.arange(12.0).reshape(3, 4)
+    np.testing.assert_array_equal(orc.scale_rhs(f), f * (1.0 / 5.0) ** 2)
+
+
+# ----------------------------------------------------------------- converged solutions
+
+@pytest.mark.parametrize("st", STENCILS)
+@pytest.mark.parametrize("Nx,Ny", [(1, 1), (3, 2), (7, 5), (12, 9), (16, 16)])
+def test_solve_matches_dense_lu(st, Nx, Ny):
+    rng = np.random.default_rng(Nx * 100 + Ny)
+    f = rng.standard_normal((Ny, Nx))
+    out = orc.solve(st, f, 1e-13)
+    assert out["converged"] and out["rel_l2"] <= 1e-13
+    h = 1.0 / (Nx + 1)
+    ref = np.linalg.solve(dense_L(st, Nx, Ny), (h * h * f).ravel()).reshape(Ny, Nx)
+    np.testing.assert_allclose(out["u"], ref, rtol=0, atol=1e-11 * np.abs(ref).max())
+
+
+@pytest.mark.parametrize("st", STENCILS)
+def test_solve_matches_discrete_sine_closed_form(st):
+    """u* = sum_kl h^2 a_kl / symbol(theta_k, phi_l) s_kl for f = sum_kl a_kl s_kl."""
+    Nx, Ny = 48, 40
+    k, l, a = workloads.smooth_random_modes(Nx, Ny, seed=7, kmax=30)
+    f = workloads.smooth_random_rhs(Nx, Ny, seed=7, kmax=30)
+    h = 1.0 / (Nx + 1)
+    ustar = np.zeros((Ny, Nx))
+    for kk, ll, aa in zip(k, l, a):
+        lam = symbol(st, kk * np.pi / (Nx + 1), ll * np.pi / (Ny + 1))
+        ustar += h * h * aa / lam * sine_mode(Nx, Ny, kk, ll)
+    out = orc.solve(st, f, 1e-11)
+    assert out["converged"]
+    err = np.linalg.norm(out["u"] - ustar) / np.linalg.norm(ustar)
+    assert err < 1e-9
+
+
+@pytest.mark.parametrize("st,order", [(5, 2.0), (9, 2.0), (17, 4.0)])
+def test_manufactured_solution_order(st, order):
+    """Error against sin(pi x) sin(pi y) falls at the stencil's formal order."""
+    errs = []
+    Ns = (15, 31, 63)
+    for N in Ns:
+        f = workloads.manufactured_rhs(N, N)
+        out = orc.solve(st, f, 1e-13)
+        errs.append(np.abs(out["u"] - workloads.manufactured_solution(N, N)).max())
+    rates = [np.log2(errs[i] / errs[i + 1]) for i in range(len(errs) - 1)]
+    for r in rates:
+        assert abs(r - order) < 0.25, (errs, rates)
+
+
+def _closed_form(st, Nx, Ny, seed, kmax):
+    k, l, a = workloads.smooth_random_modes(Nx, Ny, seed=seed, kmax=kmax)
+    h = 1.0 / (Nx + 1)
+    K, L = int(k.max()), int(l.max())
+    lam = symbol(st, k * np.pi / (Nx + 1), l * np.pi / (Ny + 1))
+    A = np.zeros((L, K))
+    A[l - 1, k - 1] = h * h * a / lam
+    i = np.arange(1, Nx + 1)
+    j = np.arange(1, Ny + 1)
+    Sx = np.sin(np.pi * np.outer(np.arange(1, K + 1), i) / (Nx + 1))
+    Sy = np.sin(np.pi * np.outer(j, np.arange(1, L + 1)) / (Ny + 1))
+    return Sy @ A @ Sx
+
+
+@pytest.mark.parametrize("st", STENCILS)
+def test_rounding_floor_estimate(st):
+    """The FP64-rounded exact discrete solution (closed form) has a relative residual of
+    the order of eps * S * ||u|| / ||b||: the floor the stop rule uses."""
+    N = 384
+    ustar = _closed_form(st, N, N, seed=1, kmax=64)
+    b = orc.scale_rhs(workloads.smooth_random_rhs(N, N, seed=1, kmax=64))
+    s, _ = orc.residual(st, ustar, b)
+    rho = np.sqrt(s) / np.linalg.norm(b)
+    est = 2.0 ** -53 * orc.abs_coeff_sum(st) * np.linalg.norm(ustar) / np.linalg.norm(b)
+    assert 0.1 * est < rho < 4.0 * est
+
+
+def test_solve_stops_at_rounding_floor():
+    """A tolerance below the floor ends with status 'floor', not an endless loop."""
+    f = workloads.smooth_random_rhs(48, 40, seed=7, kmax=30)
+    out = orc.solve(5, f, 1e-15)
+    assert out["status"] == "floor" and out["rel_l2"] < 1e-10
+
+
+def test_zero_rhs_converges_immediately():
+    out = orc.solve(9, np.zeros((5, 6)), 1e-10)
+    assert out["converged"] and out["sweeps"] == 0 and np.all(out["u"] == 0)
+
+
+def test_solve_rejects_bad_tolerance():
+    with pytest.raises(ValueError):
+        orc.solve(5, np.ones((4, 4)), 0.0)
+    with pytest.raises(ValueError):
+        orc.solve(5, np.ones((4, 4)), 1.0)
+
+
+# ----------------------------------------------------------------- FP32 inner form
+
+def test_fp32_sweep_exact_on_integers():
+    """5-point FP32 sweep with small-integer data and w = 1/4: all arithmetic is exact, so
+    the result equals the FP64 sweep bit for bit."""
+    rng = np.random.default_rng(9)
+    e = rng.integers(-50, 50, (11, 13)).astype(np.float32)
+    r = rng.integers(-50, 50, (11, 13)).astype(np.float32)
+    out32 = orc.sweep_f32(5, e, r, 0.25)
+    out64 = orc.sweep(5, e.astype(np.float64), r.astype(np.float64), 0.25)
+    np.testing.assert_array_equal(out32.astype(np.float64), out64)
+
+
+@pytest.mark.parametrize("st", STENCILS)
+def test_fp32_sweep_close_to_fp64(st):
+    rng = np.random.default_rng(10 + st)
+    e = rng.standard_normal((12, 15)).astype(np.float32)
+    r = rng.standard_normal((12, 15)).astype(np.float32)
+    w = 0.3
+    out32 = orc.sweep_f32(st, e, r, np.float32(w))
+    out64 = orc.sweep(st, e.astype(np.float64), r.astype(np.float64), float(np.float32(w)))
+    np.testing.assert_allclose(out32, out64, rtol=0, atol=2e-6 * np.abs(out64).max())
+
+
+@pytest.mark.parametrize("st", STENCILS)
+def test_defect_is_negated_residual(st):
+    rng = np.random.default_rng(20 + st)
+    u = rng.standard_normal((9, 10))
+    b = rng.standard_normal((9, 10))
+    rt, s, m = orc.defect(st, u, b)
+    r = b - orc.apply_L(st, u)
+    np.testing.assert_array_equal(rt, r.astype(np.float32))
+    assert s == pytest.approx(np.sum(r * r), rel=1e-13)
+
+
+@pytest.mark.parametrize("st", STENCILS)
+def test_mixed_precision_reaches_fp64_solution(st):
+    Nx, Ny = 48, 40
+    f = workloads.smooth_random_rhs(Nx, Ny, seed=3, kmax=30)
+    ref = orc.solve(st, f, 1e-11)
+    out = orc.solve_mixed(st, f, 1e-10, M_in=64)
+    assert out["converged"] and out["rel_l2"] <= 1e-10 and out["outer"] > 1
+    err = np.linalg.norm(out["u"] - ref["u"]) / np.linalg.norm(ref["u"])
+    assert err < 1e-9

@@ -1,0 +1,10 @@
+"""Seeded synthetic inputs shared by the tests, the benchmark and the oracle checks.
+
+This package holds input generation only (right-hand sides, problem-size draws, request
+streams); none of the Chebyshev-Jacobi arithmetic lives here.
+"""
+from .rhs import (grid_h, manufactured_rhs, manufactured_solution, smooth_random_modes,
+                  smooth_random_rhs, splitmix64_stream, gaussian_stream)
+
+__all__ = ["grid_h", "manufactured_rhs", "manufactured_solution", "smooth_random_modes",
+           "smooth_random_rhs", "splitmix64_stream", "gaussian_stream"]
