@@ -1,0 +1,348 @@
+"""Benchmark of the GB300 Chebyshev-Jacobi solver: one JSON line on stdout.
+
+Workload (one step): the plain FP64 CJM solve of Delta_h u = f with the 9-point alpha = 2/3
+stencil (Eq. 1) on a 4096 x 4096 interior grid, homogeneous Dirichlet boundary, relative
+residual target 1e-10; the right-hand side alternates between steps over the two of this
+workload: the manufactured f = -2 pi^2 sin(pi x) sin(pi y), and a seeded smooth random
+f (sine modes |k| <= 64, Gaussian amplitudes decaying as |k|^-2).  Inputs (three 134 MB
+FP64 grids) are larger than the 129 MB L2, so no flush is needed between steps.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+value  = interior points x sweeps of all ranks / max-over-ranks device time of the K steps
+         (Gupdates/s, grid-point updates per second), inputs resident in HBM;
+e2e    = the same metric through cj_solve_host (host arrays, one H2D copy of f and of the
+         initial guess, one D2H copy of u inside every step);
+roofline: the FP64 sweep kernel against the FP64 instruction-issue peak (it is bound by
+         FP64 arithmetic on GB300, not by HBM);
+cpu_baseline / --impl reference: the FP64 C oracle (test infrastructure) timed on the
+         host on a bounded sample of the same workload.
+N > 1 runs independent replicas, one per GPU (the solve does not shard across GPUs).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+N_GRID = 4096
+STENCIL = 9
+TOL = 1e-10
+METRIC = "CJM time-to-1e-10 residual & Gupdates/s vs plain FP64; HBM GB/s; p50/p99 latency"
+UNIT = "Gupdates/s"
+# FP64 instructions per grid-point update of the sweep (9-point tree: 4 pair/group sums,
+# 3 coefficient fmas, 1 update fma) and algorithmic bytes (read u and b, write u')
+FP64_OPS_PER_UPDATE = {5: 6, 9: 8, 17: 14}
+BYTES_PER_UPDATE_FP64 = 24
+# FP64 issue peak: 1.25 TFLOP/s nominal = 2 FP64 FMA per SM per clock x 152 SMs x 2.07 GHz
+FP64_PEAK_TOPS = 2 * 152 * 2.07e9 / 1e12
+
+
+def parse_args(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="cj", choices=["cj", "reference"])
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    return ap.parse_args(argv)
+
+
+# ----------------------------------------------------------------- distributed plumbing
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def dist_init(world, backend):
+    import torch.distributed as dist
+    if world > 1 and not dist.is_initialized():
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        dist.init_process_group(backend)
+    return dist
+
+
+def reduce_max_sum(dist, world, tmax: float, tsum: float, device=None):
+    """(max over ranks of tmax, sum over ranks of tsum)."""
+    if world == 1:
+        return tmax, tsum
+    import torch
+    a = torch.tensor([tmax], dtype=torch.float64, device=device)
+    b = torch.tensor([tsum], dtype=torch.float64, device=device)
+    dist.all_reduce(a, op=dist.ReduceOp.MAX)
+    dist.all_reduce(b, op=dist.ReduceOp.SUM)
+    return float(a.item()), float(b.item())
+
+
+def barrier(dist, world):
+    if world > 1:
+        dist.barrier()
+
+
+# ----------------------------------------------------------------- clocks
+
+class ClockSampler:
+    """nvidia-smi sampled every 200 ms during the timed region."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join("/tmp", "cj_clocks_%d_%d.csv" % (os.getpid(), index))
+
+    def start(self):
+        try:
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        sm, smax, reasons, power = [], [], set(), []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+                power.append(float(parts[3]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "power_w_max": max(power), "samples": len(sm)}
+
+
+# ----------------------------------------------------------------- traffic record
+
+def traffic_per_launch(kernel_key: str):
+    """DRAM bytes per launch of a kernel from the committed ncu summary, or None when the
+    kernel source changed since the counters were taken."""
+    path = os.path.join(ROOT, "profiles", "traffic_per_launch.txt")
+    src = os.path.join(ROOT, "paper_1705_00103_gb300", "csrc", "kernels.cu")
+    if not os.path.exists(path):
+        return None
+    digest = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    for line in open(path):
+        parts = line.split()
+        if len(parts) >= 3 and not line.startswith("#") and parts[0] == kernel_key:
+            return float(parts[1]) if parts[2] == digest else None
+    return None
+
+
+# ----------------------------------------------------------------- workload
+
+def make_rhs(which: int):
+    import workloads
+    if which == 0:
+        return workloads.manufactured_rhs(N_GRID, N_GRID)
+    return workloads.smooth_random_rhs(N_GRID, N_GRID, seed=1)
+
+
+def cpu_oracle_sample(seconds_target: float = 15.0) -> dict:
+    """The FP64 C oracle as it stands, single-threaded, timed on FP64 9-point sweeps of the
+    4096^2 grid (a bounded sample of the workload: whole sweeps until ~seconds_target)."""
+    from oracle import oracle as orc
+    f = make_rhs(1)
+    b = orc.scale_rhs(f)
+    kmin, kmax = orc.kappa_bounds(STENCIL, N_GRID, N_GRID)
+    M = orc.cycle_length(kmin, kmax, TOL)
+    w = orc.sweep_coeffs(STENCIL, kmin, kmax, M)
+    u = np.zeros_like(b)
+    t0 = time.perf_counter()
+    n = 0
+    while True:
+        u = orc.sweep(STENCIL, u, b, w[n % M])
+        n += 1
+        if time.perf_counter() - t0 >= seconds_target:
+            break
+    dt = time.perf_counter() - t0
+    return {"value": N_GRID * N_GRID * n / dt / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": "%d FP64 9-point CJM sweeps of the 4096x4096 grid (smooth random RHS), "
+                      "single-threaded C oracle, %.1f s" % (n, dt)}
+
+
+def run_cj(args):
+    import torch
+
+    import paper_1705_00103_gb300 as cj
+    rank, world, local = dist_env()
+    if world != args.gpus:
+        world = max(world, 1)
+    torch.cuda.set_device(local)
+    dist = dist_init(world, "nccl")
+    cj.build.build()
+    stream = torch.cuda.current_stream()
+
+    plan = cj.Plan(N_GRID, N_GRID, STENCIL, TOL)
+    info = plan.info()
+    rhs_host = [np.ascontiguousarray(make_rhs(0)), np.ascontiguousarray(make_rhs(1))]
+    rhs_dev = [torch.from_numpy(r).cuda() for r in rhs_host]
+    u = torch.zeros((N_GRID, N_GRID), dtype=torch.float64, device="cuda")
+
+    def step(k):
+        u.zero_()
+        return cj.cj_solve(plan.handle, rhs_dev[k % 2], u, stream)
+
+    for k in range(args.warmup):
+        step(k)
+    torch.cuda.synchronize()
+    barrier(dist, world)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    results = [step(k) for k in range(args.steps)]
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier(dist, world)
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1)
+    updates = sum(r["sweeps"] for r in results) * N_GRID * N_GRID
+    ms_max, updates_all = reduce_max_sum(dist, world, ms, float(updates), device="cuda")
+    value = updates_all / (ms_max * 1e-3) / 1e9
+
+    sweeps = sum(r["sweeps"] for r in results)
+    sweep_s = sum(r["sweep_seconds"] for r in results)
+    avg_sweep_s = sweep_s / sweeps
+    ops = FP64_OPS_PER_UPDATE[STENCIL] * N_GRID * N_GRID
+    achieved = ops / avg_sweep_s / 1e12
+    traffic = traffic_per_launch("sweep_kernel_9_f64_4096")
+    roofline = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TOPS, "unit": "TFP64op/s",
+                "frac": achieved / FP64_PEAK_TOPS, "traffic": traffic,
+                "kernel": "sweep_kernel<9,double>", "avg_launch_us": avg_sweep_s * 1e6,
+                "hbm_gbs_algorithmic": BYTES_PER_UPDATE_FP64 * N_GRID * N_GRID / avg_sweep_s / 1e9,
+                "peak_note": "FP64 issue peak derived from 1.25 TFLOP/s nominal: 2 FMA/clk/SM x 152 SMs x 2.07 GHz"}
+
+    e2e = None
+    if not args.no_e2e:
+        pinned_f = [torch.from_numpy(r).pin_memory().numpy() for r in rhs_host]
+        pinned_u = torch.zeros((N_GRID, N_GRID), dtype=torch.float64).pin_memory().numpy()
+        torch.cuda.synchronize()
+        barrier(dist, world)
+        t0 = time.perf_counter()
+        eres = []
+        for k in range(args.steps):
+            pinned_u[...] = 0.0
+            eres.append(cj.cj_solve_host(plan.handle, pinned_f[k % 2], pinned_u, stream))
+        t_e2e = time.perf_counter() - t0
+        t_max, up_all = reduce_max_sum(dist, world, t_e2e,
+                                       float(sum(r["sweeps"] for r in eres) * N_GRID * N_GRID), device="cuda")
+        e2e = {"value": up_all / t_max / 1e9, "unit": UNIT,
+               "h2d_bytes_per_step": 2 * N_GRID * N_GRID * 8, "d2h_bytes_per_step": N_GRID * N_GRID * 8,
+               "api": "cj_solve_host"}
+
+    launches = sum(r["launches"] for r in results)
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "plain CJM FP64, 9-point alpha=2/3 stencil, 4096x4096 interior, "
+                               "homogeneous Dirichlet, tol 1e-10; RHS alternating sin*sin / seeded "
+                               "smooth random (|k|<=64, |k|^-2)",
+                   "Nx": N_GRID, "Ny": N_GRID, "stencil": STENCIL, "tol": TOL, "M": info["M"],
+                   "l2_flush": "none needed: 3 resident FP64 grids of 134 MB each exceed the 129 MB L2",
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "solves": [{"status": cj.cj_status_string(r["rc"]), "sweeps": r["sweeps"], "cycles": r["cycles"],
+                    "rel_res_l2": r["rel_res_l2"], "floor_est": r["floor_est"],
+                    "time_s": r["seconds"]} for r in results[:2]],
+        "roofline": roofline, "clocks": clk, "gpu_launches": launches, "e2e": e2e,
+    }
+    if rank == 0 and not args.no_cpu:
+        out["cpu_baseline"] = cpu_oracle_sample()
+    plan.close()
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def run_reference(args):
+    """The oracle as the reference arm: each step a bounded sample (4 sweeps) of the same
+    workload, on the host cores, rank 0 only."""
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    from oracle import oracle as orc
+    f = make_rhs(1)
+    b = orc.scale_rhs(f)
+    kmin, kmax = orc.kappa_bounds(STENCIL, N_GRID, N_GRID)
+    M = orc.cycle_length(kmin, kmax, TOL)
+    w = orc.sweep_coeffs(STENCIL, kmin, kmax, M)
+    u = np.zeros_like(b)
+    per_step = 4
+
+    def step(k):
+        nonlocal u
+        for s in range(per_step):
+            u = orc.sweep(STENCIL, u, b, w[(k * per_step + s) % M])
+
+    for k in range(args.warmup):
+        step(k)
+    t0 = time.perf_counter()
+    for k in range(args.steps):
+        step(args.warmup + k)
+    dt = time.perf_counter() - t0
+    value = N_GRID * N_GRID * per_step * args.steps / dt / 1e9
+    sample = ("%d FP64 9-point CJM sweeps of the 4096x4096 grid per step, single-threaded C oracle"
+              % per_step)
+    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic",
+           "config": {"workload": "plain CJM FP64, 9-point alpha=2/3 stencil, 4096x4096 interior, "
+                                  "homogeneous Dirichlet, tol 1e-10 (bounded sample per step)",
+                      "Nx": N_GRID, "Ny": N_GRID, "stencil": STENCIL, "tol": TOL},
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main(argv=None):
+    args = parse_args(argv)
+    if args.warmup < 3:
+        raise SystemExit("--warmup must be >= 3")
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_cj(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,194 @@
+/*
+ * cj.h -- C ABI of the GB300 Chebyshev-Jacobi (CJM) solver library (libcj.so).
+ *
+ * The method (Adsuara et al., arXiv 1705.00103, Sec. 2.1): solve the finite-difference
+ * Poisson problem Delta_h u = f on the interior nodes 1 <= i <= Nx, 1 <= j <= Ny of a
+ * uniform mesh (h = 1/(Nx+1) in both directions, Sec. 3.2) by weighted Jacobi sweeps
+ *     u <- u + w_n (L u - b),   b = h^2 f,   L = h^2 Delta_h,   w_n = omega_n / c,
+ * whose weight omega_n changes at every sweep: the M weights are the zeros of the
+ * degree-M Chebyshev polynomial mapped onto the eigenvalue interval [kmin, kmax] of the
+ * Jacobi iteration matrix, whose ends the paper gives in closed form for each stencil
+ * (equations after Eq. 1 and Eq. 2).  Stencils: the classical 5-point Laplacian (Table 3,
+ * Cartesian row), the 9-point alpha = 2/3 Laplacian (Eq. 1) and the 17-point alpha = 2/3
+ * Laplacian (Eq. 2).  Boundary: homogeneous Dirichlet (u = 0 on nodes 0 and N+1); the
+ * 17-point stencil's second ghost layer is the odd reflection u[-1] = -u[1].
+ *
+ * Conventions for every entry point:
+ *   - Grids passed in or out are interior values only, row-major: node (i, j) is element
+ *     (j-1)*ld + (i-1), with ld >= Nx the row stride in elements.  "device" pointers are
+ *     CUDA device (or managed) memory of the current device; "host" pointers are host
+ *     memory (pinned memory gives the fastest copies).
+ *   - The library never frees or keeps caller memory.  Objects it creates (plans) own
+ *     their device workspace until destroyed.
+ *   - Streams are passed as `void *` holding a cudaStream_t (NULL = legacy default stream).
+ *   - No C++ exception crosses the ABI; every failure is a cj_status < 0.
+ *   - A plan is used by one host thread at a time; its workspace serialises its calls.
+ */
+#ifndef CJ_H
+#define CJ_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    CJ_OK = 0,                /* solve converged: relative residual <= tol */
+    CJ_FLOOR = 1,             /* solve stopped at the FP64 rounding floor (see cj_result) */
+    CJ_PENDING = 2,           /* reserved for asynchronous requests: not finished yet */
+    CJ_ERR_INVALID_ARG = -1,  /* a size, pointer, stencil, tolerance or option is invalid */
+    CJ_ERR_NOMEM = -2,        /* a device or host allocation failed */
+    CJ_ERR_NOT_CONVERGED = -3,/* the sweep budget ran out first */
+    CJ_ERR_DIVERGED = -4,     /* the residual became non-finite */
+    CJ_ERR_TIMEOUT = -5,      /* a bounded device wait gave up */
+    CJ_ERR_CUDA = -6,         /* a CUDA runtime call failed (message: cj_last_error) */
+    CJ_ERR_BUDGET = -7        /* reserved: a memory budget refused the request */
+} cj_status;
+
+typedef enum { CJ_ST5 = 5, CJ_ST9 = 9, CJ_ST17 = 17 } cj_stencil;
+
+typedef enum { CJ_BC_DIRICHLET0 = 0 } cj_bc;
+
+typedef enum {
+    CJ_FP64 = 0,          /* plain CJM: every sweep in FP64 */
+    CJ_FP32_INNER = 1,    /* FP32 inner CJM cycles inside an FP64 defect-correction loop */
+    CJ_FP32_INNER_DD = 2  /* FP32 inner CJM cycles inside a double-FP64 defect-correction
+                             loop: the solution is u_hi + u_lo and the defect is evaluated
+                             to about twice FP64 precision, so the relative residual can go
+                             below the FP64 floor (see cj_result.floor_est) */
+} cj_precision;
+
+/* Optional plan settings; pass NULL for the defaults (all fields 0). */
+typedef struct {
+    int precision;          /* cj_precision (default CJ_FP64) */
+    int literal_n;          /* 1: use the paper-literal N = Nx in the kappa formulas instead
+                               of the exact N = Nx + 1 (ablation only) */
+    int inner_cycle;        /* CJ_FP32_INNER: inner cycle length (a power of two); 0 = auto */
+    int reserved0;
+    long long max_sweeps;   /* sweep budget of one solve; 0 = 64 cycles */
+} cj_options;
+
+/* What one solve did.  The relative residuals are those of the returned u:
+ * rel_res_l2 = ||b - L u||_2 / ||b||_2 and rel_res_inf = max|b - L u| / max|b| (absolute
+ * when b = 0); floor_est = 2^-53 * S * ||u||_2 / ||b||_2 is the FP64 rounding floor that
+ * rel_res_l2 cannot go below (S = sum of the stencil's absolute coefficients). */
+typedef struct {
+    long long sweeps;       /* weighted sweeps applied (FP32 ones for CJ_FP32_INNER) */
+    int cycles;             /* CJM cycles (or outer defect-correction steps) */
+    int status;             /* the cj_status the solve returned */
+    double rel_res_l2;
+    double rel_res_inf;
+    double floor_est;
+    double seconds;         /* host wall time of the call */
+    double sweep_seconds;   /* device time of the sweep phases, by CUDA events recorded on
+                               the solve's stream around each cycle's sweeps */
+    long long launches;     /* kernels the call launched */
+} cj_result;
+
+typedef struct cj_plan cj_plan;
+
+/* Human-readable name of a status code (static storage). */
+const char *cj_status_string(int status);
+
+/* Last CUDA error message of the calling thread (static storage, may be ""). */
+const char *cj_last_error(void);
+
+/*
+ * cj_plan_create -- precompute everything a solve of this problem needs (Sec. 2.1:
+ * the weights are "precalculated before starting the iterative algorithm").
+ *   Nx, Ny >= 1 interior nodes; st in {5, 9, 17}; bc = CJ_BC_DIRICHLET0;
+ *   0 < tol < 1 is the relative residual target.
+ * Computes kmin, kmax, the cycle length M (smallest power of two whose Chebyshev
+ * bound reaches tol), the M weights in mirror-pairing order and the sweep table
+ * w_n = omega_n / c; allocates the device workspace on the current device (two padded
+ * solution buffers, the padded b, reduction scratch; for CJ_FP32_INNER also the FP32
+ * buffers).  On success *out owns all of it.  Errors: CJ_ERR_INVALID_ARG, CJ_ERR_NOMEM,
+ * CJ_ERR_CUDA.
+ */
+cj_status cj_plan_create(int Nx, int Ny, cj_stencil st, cj_bc bc, double tol,
+                         const cj_options *opt, cj_plan **out);
+
+/* Frees the plan and its device workspace (NULL is ignored). */
+void cj_plan_destroy(cj_plan *plan);
+
+/*
+ * cj_plan_info -- the plan's numbers (any output pointer may be NULL).
+ *   *w      host array of M per-sweep coefficients w_n = omega_n / c in application order
+ *           (owned by the plan, valid until cj_plan_destroy);
+ *   *M      cycle length; *kmin, *kmax eigenvalue bounds of D^-1 A;
+ *   *M_inner inner cycle length for CJ_FP32_INNER (0 otherwise).
+ */
+cj_status cj_plan_info(const cj_plan *plan, const double **w, long long *M, double *kmin,
+                       double *kmax, long long *M_inner);
+
+/*
+ * cj_solve -- full CJM solve on the device (Sec. 2.1 with the plan's readings).
+ *   f: device, Ny x ld_f doubles, the unscaled right-hand side f of Delta_h u = f.
+ *   u: device, Ny x ld_u doubles; in: initial guess, out: the solution.
+ * Runs the cycles on `stream`; the residual is tested on the host before each cycle,
+ * so the call blocks until the solve ends.  Stops with CJ_OK when the relative
+ * residual <= tol, CJ_FLOOR when it cannot fall further in FP64 (<= 4 x floor_est, or
+ * one plain cycle -- two consecutive CJ_FP32_INNER outer steps -- failed to halve it),
+ * CJ_ERR_NOT_CONVERGED when the sweep budget is spent,
+ * CJ_ERR_DIVERGED on a non-finite residual.  *res (may be NULL) describes the run.
+ */
+cj_status cj_solve(cj_plan *plan, const double *f, long long ld_f, double *u, long long ld_u,
+                   void *stream, cj_result *res);
+
+/*
+ * cj_solve_history -- cj_solve that also records the relative L2 residual found at every
+ * residual test (before each cycle / outer step, and the final one) into the host array
+ * history[0 .. cap-1]; *count receives the number of tests made (which may exceed cap).
+ */
+cj_status cj_solve_history(cj_plan *plan, const double *f, long long ld_f, double *u,
+                           long long ld_u, void *stream, cj_result *res, double *history,
+                           int cap, int *count);
+
+/*
+ * cj_solve_host -- cj_solve for host arrays: copies f (Ny x Nx, ld = Nx) and the initial
+ * guess u to the device in one transfer each, solves, and copies u back (Sec. 3.2:
+ * one transfer in, one out).  u_host is in/out.
+ */
+cj_status cj_solve_host(cj_plan *plan, const double *f_host, double *u_host, void *stream,
+                        cj_result *res);
+
+/*
+ * cj_sweeps -- apply `count` weighted FP64 sweeps to u in place, with the plan's weights
+ * w_{first mod M}, w_{first+1 mod M}, ... (the sweep of Sec. 2.1 alone, no stop test).
+ * f, u: device, as for cj_solve.  Asynchronous on `stream`.
+ */
+cj_status cj_sweeps(cj_plan *plan, const double *f, long long ld_f, double *u, long long ld_u,
+                    long long first, long long count, void *stream);
+
+/*
+ * cj_sweeps_f32 -- apply `count` weighted FP32 sweeps e <- e + w32_n (L e - r) in place,
+ * w32_n = (float) w_n of the plan's inner cycle (CJ_FP32_INNER plans only).
+ * r, e: device, Ny x ld floats.  Asynchronous on `stream`.
+ */
+cj_status cj_sweeps_f32(cj_plan *plan, const float *r, long long ld_r, float *e, long long ld_e,
+                        long long first, long long count, void *stream);
+
+/*
+ * cj_solution_lo -- for a CJ_FP32_INNER_DD plan, the low part u_lo of the last solve's
+ * double-FP64 solution (cj_solve returned u = u_hi, with |u_lo| <= ulp(u_hi)/2); the
+ * relative residual cj_result reported is that of u_hi + u_lo.  u_lo: device, Ny x ld
+ * doubles.  Asynchronous on `stream`.  CJ_ERR_INVALID_ARG for other plans.
+ */
+cj_status cj_solution_lo(cj_plan *plan, double *u_lo, long long ld, void *stream);
+
+/*
+ * cj_residual -- relative residual norms of u (the stop test of cj_solve, alone).
+ *   f, u: device, as for cj_solve.  Writes *rel_l2, *rel_inf, *floor_est (any may be
+ *   NULL) and blocks until they are known.
+ */
+cj_status cj_residual(cj_plan *plan, const double *f, long long ld_f, const double *u,
+                      long long ld_u, void *stream, double *rel_l2, double *rel_inf,
+                      double *floor_est);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CJ_H */

@@ -36,7 +36,9 @@
  *      rho cannot fall below the rounding floor of an FP64 u, about
  *      fl = eps * S * ||u||_2 / ||b||_2 (eps = 2^-53, S = sum of |coefficients|), which is
  *      ~5e-10 for the 9-point stencil on 4096^2; so the solve also stops, with the status
- *      "floor", once rho <= 4 fl, or once a whole cycle fails to halve rho.
+ *      "floor", once rho <= 4 fl, or once `patience` consecutive cycles each failed to
+ *      halve rho (patience 1 for plain CJM cycles; 2 for the defect-correction loop of
+ *      R10, whose residual may jump up once before contracting).
  *   R9 evaluation order of the residual L u - b (any order is exact in real arithmetic):
  *      horizontal pair sums p = u(i-1,.) + u(i+1,.), P = u(i-2,.) + u(i+2,.), vertical
  *      pair sums v1 = u(i,j-1) + u(i,j+1), v2 = u(i,j-2) + u(i,j+2); axis groups
@@ -46,6 +48,12 @@
  *      FP64 defect-correction loop r = b - L u, rt = (float) r, one FP32 CJM cycle of
  *      length M_in on L e = rt from e = 0 with w32_n = (float)(omega_n / c), then
  *      u <- u + (double) e.  The stop test is the FP64 residual of R8.
+ *   R11 double-FP64 outer (not in the paper): as R10, but the solution is the unevaluated
+ *      sum u_hi + u_lo of two FP64 arrays and the defect is evaluated to about twice FP64
+ *      precision: D (L u_hi - b), D = 1, 6 or 72 the stencil's denominator, is a sum of
+ *      terms that are exact in FP64 (power-of-two multiples of u_hi and b), added by the
+ *      error-free TwoSum cascade (Ogita, Rump and Oishi's Sum2); D L u_lo is added in plain
+ *      FP64.  The correction is added by TwoSum.  This removes the FP64 floor of R8.
  *
  * Array convention: interior values only, row-major [Ny][Nx], value of node (i, j) at
  * u[(j-1)*Nx + (i-1)].  Compiled with -ffp-contract=off so that every rounding is the
@@ -254,12 +262,17 @@ double orc_abs_coeff_sum(int st) {
 /* Stop statuses of the solves (reading R8). */
 enum { ORC_CONVERGED = 0, ORC_FLOOR = 1, ORC_MAX_SWEEPS = 2, ORC_DIVERGED = 3 };
 
-/* Decide after a residual evaluation whether to stop; returns -1 to continue. */
-static int stop_rule(double rho, double floor_est, double rho_prev, long done_cycles, double tol) {
+/* Decide after a residual evaluation whether to stop; returns -1 to continue.  *stall
+ * counts consecutive cycles that failed to halve rho. */
+static int stop_rule(double rho, double floor_est, double rho_prev, long done_cycles, double tol,
+                     int patience, int *stall) {
     if (rho <= tol) return ORC_CONVERGED;
     if (!(rho == rho) || rho > 1e300) return ORC_DIVERGED;
     if (rho <= 4.0 * floor_est) return ORC_FLOOR;
-    if (done_cycles > 0 && rho > 0.5 * rho_prev) return ORC_FLOOR;
+    if (done_cycles > 0) {
+        *stall = rho > 0.5 * rho_prev ? *stall + 1 : 0;
+        if (*stall >= patience) return ORC_FLOOR;
+    }
     return -1;
 }
 
@@ -287,7 +300,7 @@ long orc_solve(int st, int Nx, int Ny, const double *f, double tol, long max_swe
     }
     double bn = sqrt(bsq), eps = ldexp(1.0, -53), S = orc_abs_coeff_sum(st);
     long sweeps = 0, cyc = 0;
-    int stat;
+    int stat, stall = 0;
     double rl2 = 0.0, rinf = 0.0, prev = 0.0;
     for (;;) {
         double sq, mx, usq = 0.0;
@@ -296,7 +309,7 @@ long orc_solve(int st, int Nx, int Ny, const double *f, double tol, long max_swe
         rl2 = bn > 0.0 ? sqrt(sq) / bn : sqrt(sq);
         rinf = bmax > 0.0 ? mx / bmax : mx;
         double fl = bn > 0.0 ? eps * S * sqrt(usq) / bn : eps * S * sqrt(usq);
-        stat = stop_rule(rl2, fl, prev, cyc, tol);
+        stat = stop_rule(rl2, fl, prev, cyc, tol, 1, &stall);
         if (stat >= 0) break;
         if (sweeps + M > max_sweeps) { stat = ORC_MAX_SWEEPS; break; }
         for (long s = 0; s < M; ++s) {
@@ -410,7 +423,7 @@ long orc_solve_mixed(int st, int Nx, int Ny, const double *f, double tol, long M
     }
     double bn = sqrt(bsq), eps = ldexp(1.0, -53), S = orc_abs_coeff_sum(st);
     long sweeps = 0, out = 0;
-    int stat;
+    int stat, stall = 0;
     double rl2 = 0.0, rinf = 0.0, prev = 0.0;
     for (;;) {
         double sq, mx, usq = 0.0;
@@ -419,7 +432,7 @@ long orc_solve_mixed(int st, int Nx, int Ny, const double *f, double tol, long M
         rl2 = bn > 0.0 ? sqrt(sq) / bn : sqrt(sq);
         rinf = bmax > 0.0 ? mx / bmax : mx;
         double fl = bn > 0.0 ? eps * S * sqrt(usq) / bn : eps * S * sqrt(usq);
-        stat = stop_rule(rl2, fl, prev, out, tol);
+        stat = stop_rule(rl2, fl, prev, out, tol, 2, &stall);
         if (stat >= 0) break;
         if (out >= max_outer) { stat = ORC_MAX_SWEEPS; break; }
         prev = rl2;
@@ -433,6 +446,166 @@ long orc_solve_mixed(int st, int Nx, int Ny, const double *f, double tol, long M
         out += 1;
     }
     free(w); free(w32); free(b); free(rt); free(e); free(e2);
+    *rel_l2 = rl2;
+    *rel_linf = rinf;
+    *outer = out;
+    *status = stat;
+    return sweeps;
+}
+
+/* ---------------------------------------------------------------- double-FP64 outer form */
+
+/* TwoSum (Knuth): s + e = a + b exactly. */
+static void two_sum(double a, double b, double *s, double *e) {
+    double x = a + b;
+    double z = x - a;
+    *e = (a - (x - z)) + (b - z);
+    *s = x;
+}
+
+/* Sum2 accumulation of one term into (S, E). */
+static void acc(double t, double *S, double *E) {
+    double e;
+    two_sum(*S, t, S, &e);
+    *E += e;
+}
+
+/* R = (L (uh + ul))(i, j) - bk to about twice FP64 precision (reading R11), returned
+ * rounded to FP64.  The terms of D (L uh - bk) are added in this fixed order:
+ *   5-pt (D = 1) : uW, uE, uS, uN, -4 uC, -bk
+ *   9-pt (D = 6) : 4uW, 4uE, 4uS, 4uN, uSW, uSE, uNW, uNE, -16uC, -4uC, -4bk, -2bk
+ *   17-pt (D = 72): 64 x (uW, uE, uS, uN), -4 x (uWW, uEE, uSS, uNN),
+ *                   16 x (uSW, uSE, uNW, uNE), -(uSSWW, uSSEE, uNNWW, uNNEE),
+ *                   -256uC, -32uC, -8uC, -4uC, -64bk, -8bk
+ * then R = (S + (E + D * (L ul))) / D with L ul from resid_at. */
+static double resid_dd_at(int st, const double *uh, const double *ul, int Nx, int Ny, int i,
+                          int j, double bk) {
+    double S = 0.0, E = 0.0, D;
+    double uC = at(uh, Nx, Ny, i, j);
+    if (st == 5) {
+        D = 1.0;
+        acc(at(uh, Nx, Ny, i - 1, j), &S, &E);
+        acc(at(uh, Nx, Ny, i + 1, j), &S, &E);
+        acc(at(uh, Nx, Ny, i, j - 1), &S, &E);
+        acc(at(uh, Nx, Ny, i, j + 1), &S, &E);
+        acc(-4.0 * uC, &S, &E);
+        acc(-bk, &S, &E);
+    } else if (st == 9) {
+        D = 6.0;
+        acc(4.0 * at(uh, Nx, Ny, i - 1, j), &S, &E);
+        acc(4.0 * at(uh, Nx, Ny, i + 1, j), &S, &E);
+        acc(4.0 * at(uh, Nx, Ny, i, j - 1), &S, &E);
+        acc(4.0 * at(uh, Nx, Ny, i, j + 1), &S, &E);
+        acc(at(uh, Nx, Ny, i - 1, j - 1), &S, &E);
+        acc(at(uh, Nx, Ny, i + 1, j - 1), &S, &E);
+        acc(at(uh, Nx, Ny, i - 1, j + 1), &S, &E);
+        acc(at(uh, Nx, Ny, i + 1, j + 1), &S, &E);
+        acc(-16.0 * uC, &S, &E);
+        acc(-4.0 * uC, &S, &E);
+        acc(-4.0 * bk, &S, &E);
+        acc(-2.0 * bk, &S, &E);
+    } else {
+        D = 72.0;
+        acc(64.0 * at(uh, Nx, Ny, i - 1, j), &S, &E);
+        acc(64.0 * at(uh, Nx, Ny, i + 1, j), &S, &E);
+        acc(64.0 * at(uh, Nx, Ny, i, j - 1), &S, &E);
+        acc(64.0 * at(uh, Nx, Ny, i, j + 1), &S, &E);
+        acc(-4.0 * at(uh, Nx, Ny, i - 2, j), &S, &E);
+        acc(-4.0 * at(uh, Nx, Ny, i + 2, j), &S, &E);
+        acc(-4.0 * at(uh, Nx, Ny, i, j - 2), &S, &E);
+        acc(-4.0 * at(uh, Nx, Ny, i, j + 2), &S, &E);
+        acc(16.0 * at(uh, Nx, Ny, i - 1, j - 1), &S, &E);
+        acc(16.0 * at(uh, Nx, Ny, i + 1, j - 1), &S, &E);
+        acc(16.0 * at(uh, Nx, Ny, i - 1, j + 1), &S, &E);
+        acc(16.0 * at(uh, Nx, Ny, i + 1, j + 1), &S, &E);
+        acc(-at(uh, Nx, Ny, i - 2, j - 2), &S, &E);
+        acc(-at(uh, Nx, Ny, i + 2, j - 2), &S, &E);
+        acc(-at(uh, Nx, Ny, i - 2, j + 2), &S, &E);
+        acc(-at(uh, Nx, Ny, i + 2, j + 2), &S, &E);
+        acc(-256.0 * uC, &S, &E);
+        acc(-32.0 * uC, &S, &E);
+        acc(-8.0 * uC, &S, &E);
+        acc(-4.0 * uC, &S, &E);
+        acc(-64.0 * bk, &S, &E);
+        acc(-8.0 * bk, &S, &E);
+    }
+    double Llo = resid_at(st, ul, Nx, Ny, i, j, 0.0);
+    return (S + (E + D * Llo)) / D;
+}
+
+/* Residual R = L (uh + ul) - b of the double-FP64 form at every node (reading R11). */
+void orc_residual_dd(int st, int Nx, int Ny, const double *uh, const double *ul,
+                     const double *b, double *R) {
+    for (int j = 1; j <= Ny; ++j)
+        for (int i = 1; i <= Nx; ++i) {
+            size_t k = (size_t)(j - 1) * Nx + (i - 1);
+            R[k] = resid_dd_at(st, uh, ul, Nx, Ny, i, j, b[k]);
+        }
+}
+
+/* Mixed-precision CJM with the double-FP64 outer loop (reading R11).  u: initial guess in
+ * (taken as u_hi, u_lo = 0), u_hi + u_lo rounded to FP64 out; u_lo_out (may be NULL)
+ * receives u_lo.  Returns the FP32 sweeps done or -1; *outer, *status as orc_solve_mixed;
+ * the floor estimate uses 2^-106 in place of 2^-53. */
+long orc_solve_mixed_dd(int st, int Nx, int Ny, const double *f, double tol, long M_in,
+                        long max_outer, double *u, double *u_lo_out, double *rel_l2,
+                        double *rel_linf, long *outer, int *status) {
+    if (Nx < 1 || Ny < 1 || !(tol > 0.0 && tol < 1.0) || M_in < 1) return -1;
+    size_t n = (size_t)Nx * (size_t)Ny;
+    double kmin, kmax;
+    orc_kappa_bounds(st, Nx, Ny, &kmin, &kmax);
+    double *w = (double *)malloc(sizeof(double) * (size_t)M_in);
+    if (orc_sweep_coeffs(st, kmin, kmax, M_in, w) != 0) { free(w); return -1; }
+    float *w32 = (float *)malloc(sizeof(float) * (size_t)M_in);
+    for (long s = 0; s < M_in; ++s) w32[s] = (float)w[s];
+    double *b = (double *)malloc(sizeof(double) * n);
+    double *ul = (double *)calloc(n, sizeof(double));
+    double *R = (double *)malloc(sizeof(double) * n);
+    float *rt = (float *)malloc(sizeof(float) * n);
+    float *e = (float *)malloc(sizeof(float) * n);
+    float *e2 = (float *)malloc(sizeof(float) * n);
+    orc_scale_rhs(Nx, Ny, f, b);
+    double bsq = 0.0, bmax = 0.0;
+    for (size_t k = 0; k < n; ++k) {
+        bsq += b[k] * b[k];
+        if (fabs(b[k]) > bmax) bmax = fabs(b[k]);
+    }
+    double bn = sqrt(bsq), eps2 = ldexp(1.0, -106), S = orc_abs_coeff_sum(st);
+    long sweeps = 0, out = 0;
+    int stat, stall = 0;
+    double rl2 = 0.0, rinf = 0.0, prev = 0.0;
+    for (;;) {
+        double sq = 0.0, mx = 0.0, usq = 0.0;
+        orc_residual_dd(st, Nx, Ny, u, ul, b, R);
+        for (size_t k = 0; k < n; ++k) {
+            sq += R[k] * R[k];
+            if (fabs(R[k]) > mx) mx = fabs(R[k]);
+            usq += u[k] * u[k];
+            rt[k] = (float)(-R[k]);
+        }
+        rl2 = bn > 0.0 ? sqrt(sq) / bn : sqrt(sq);
+        rinf = bmax > 0.0 ? mx / bmax : mx;
+        double fl = bn > 0.0 ? eps2 * S * sqrt(usq) / bn : eps2 * S * sqrt(usq);
+        stat = stop_rule(rl2, fl, prev, out, tol, 2, &stall);
+        if (stat >= 0) break;
+        if (out >= max_outer) { stat = ORC_MAX_SWEEPS; break; }
+        prev = rl2;
+        memset(e, 0, sizeof(float) * n);
+        for (long s = 0; s < M_in; ++s) {
+            orc_sweep_f32(st, Nx, Ny, e, rt, w32[s], e2);
+            memcpy(e, e2, sizeof(float) * n);
+        }
+        for (size_t k = 0; k < n; ++k) {
+            double hi, err;
+            two_sum(u[k], (double)e[k], &hi, &err);
+            double lo = ul[k] + err;
+            two_sum(hi, lo, &u[k], &ul[k]);
+        }
+        sweeps += M_in;
+        out += 1;
+    }
+    if (u_lo_out) memcpy(u_lo_out, ul, sizeof(double) * n);
+    free(w); free(w32); free(b); free(ul); free(R); free(rt); free(e); free(e2);
     *rel_l2 = rl2;
     *rel_linf = rinf;
     *outer = out;

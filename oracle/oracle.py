@@ -72,6 +72,10 @@ def lib():
         L.orc_solve_mixed.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, _dp, ctypes.c_double,
                                       ctypes.c_long, ctypes.c_long, _dp, _dp, _dp, _lp, _ip]
         L.orc_solve_mixed.restype = ctypes.c_long
+        L.orc_residual_dd.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, _dp, _dp, _dp, _dp]
+        L.orc_solve_mixed_dd.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, _dp, ctypes.c_double,
+                                         ctypes.c_long, ctypes.c_long, _dp, _dp, _dp, _dp, _lp, _ip]
+        L.orc_solve_mixed_dd.restype = ctypes.c_long
         _lib = L
     return _lib
 
@@ -224,4 +228,30 @@ def solve_mixed(st: int, f: np.ndarray, tol: float, M_in: int, u0: np.ndarray | 
     if n < 0:
         raise ValueError("bad argument")
     return dict(u=u, sweeps=n, outer=outer.value, rel_l2=rl2.value, rel_linf=rinf.value,
+                status=STATUS[stat.value], converged=stat.value == 0)
+
+
+def residual_dd(st: int, uh: np.ndarray, ul: np.ndarray, b: np.ndarray) -> np.ndarray:
+    """R = L (uh + ul) - b evaluated to about twice FP64 precision, rounded to FP64."""
+    uh, ul, b = _grid(uh), _grid(ul), _grid(b)
+    R = np.empty_like(uh)
+    lib().orc_residual_dd(st, uh.shape[1], uh.shape[0], _d(uh), _d(ul), _d(b), _d(R))
+    return R
+
+
+def solve_mixed_dd(st: int, f: np.ndarray, tol: float, M_in: int, u0: np.ndarray | None = None,
+                   max_outer: int = 1000) -> dict:
+    """FP32-inner CJM cycles inside a double-FP64 defect-correction loop; returns
+    u = fl(u_hi + u_lo) and u_lo."""
+    f = _grid(f)
+    u = np.zeros_like(f) if u0 is None else _grid(u0).copy()
+    ulo = np.zeros_like(f)
+    rl2, rinf = ctypes.c_double(), ctypes.c_double()
+    outer, stat = ctypes.c_long(), ctypes.c_int()
+    n = lib().orc_solve_mixed_dd(st, f.shape[1], f.shape[0], _d(f), tol, M_in, max_outer, _d(u),
+                                 _d(ulo), ctypes.byref(rl2), ctypes.byref(rinf),
+                                 ctypes.byref(outer), ctypes.byref(stat))
+    if n < 0:
+        raise ValueError("bad argument")
+    return dict(u=u, u_lo=ulo, sweeps=n, outer=outer.value, rel_l2=rl2.value, rel_linf=rinf.value,
                 status=STATUS[stat.value], converged=stat.value == 0)

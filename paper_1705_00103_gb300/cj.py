@@ -1,0 +1,255 @@
+"""Python binding of libcj (the C ABI declared in include/cj.h), by ctypes.
+
+Argument marshalling only: every step of the solve runs in libcj's CUDA kernels.  Device
+grids are torch CUDA tensors (float64, or float32 for the FP32 entry points), 2-D with
+shape (Ny, Nx) and unit stride along x; their row stride is passed as ``ld``.  Streams
+default to torch's current stream.  If libcj.so has not been built, loading raises: there
+is no fallback implementation.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+CJ_OK, CJ_FLOOR, CJ_PENDING = 0, 1, 2
+CJ_ERR_INVALID_ARG, CJ_ERR_NOMEM, CJ_ERR_NOT_CONVERGED = -1, -2, -3
+CJ_ERR_DIVERGED, CJ_ERR_TIMEOUT, CJ_ERR_CUDA, CJ_ERR_BUDGET = -4, -5, -6, -7
+CJ_ST5, CJ_ST9, CJ_ST17 = 5, 9, 17
+CJ_BC_DIRICHLET0 = 0
+CJ_FP64, CJ_FP32_INNER, CJ_FP32_INNER_DD = 0, 1, 2
+
+
+class cj_options(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int), ("literal_n", ctypes.c_int),
+                ("inner_cycle", ctypes.c_int), ("reserved0", ctypes.c_int),
+                ("max_sweeps", ctypes.c_longlong)]
+
+
+class cj_result(ctypes.Structure):
+    _fields_ = [("sweeps", ctypes.c_longlong), ("cycles", ctypes.c_int), ("status", ctypes.c_int),
+                ("rel_res_l2", ctypes.c_double), ("rel_res_inf", ctypes.c_double),
+                ("floor_est", ctypes.c_double), ("seconds", ctypes.c_double),
+                ("sweep_seconds", ctypes.c_double), ("launches", ctypes.c_longlong)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class CJError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        msg = "%s: %s (%d)" % (where, cj_status_string(status), status)
+        err = _lib().cj_last_error().decode()
+        if err:
+            msg += " [%s]" % err
+        super().__init__(msg)
+        self.status = status
+
+
+_L = None
+_vp = ctypes.c_void_p
+_ll = ctypes.c_longlong
+_dp = ctypes.POINTER(ctypes.c_double)
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def _lib():
+    global _L
+    if _L is None:
+        path = _build.LIB
+        if not os.path.exists(path):
+            raise RuntimeError("libcj.so is not built (%s); run paper_1705_00103_gb300/build.py "
+                               "or __graft_entry__.build() first -- there is no CPU fallback" % path)
+        L = ctypes.CDLL(path)
+        L.cj_status_string.argtypes = [ctypes.c_int]
+        L.cj_status_string.restype = ctypes.c_char_p
+        L.cj_last_error.argtypes = []
+        L.cj_last_error.restype = ctypes.c_char_p
+        L.cj_plan_create.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                     ctypes.c_double, ctypes.POINTER(cj_options), ctypes.POINTER(_vp)]
+        L.cj_plan_create.restype = ctypes.c_int
+        L.cj_plan_destroy.argtypes = [_vp]
+        L.cj_plan_destroy.restype = None
+        L.cj_plan_info.argtypes = [_vp, ctypes.POINTER(_dp), ctypes.POINTER(_ll), _dp, _dp,
+                                   ctypes.POINTER(_ll)]
+        L.cj_plan_info.restype = ctypes.c_int
+        L.cj_solve.argtypes = [_vp, _vp, _ll, _vp, _ll, _vp, ctypes.POINTER(cj_result)]
+        L.cj_solve.restype = ctypes.c_int
+        L.cj_solve_history.argtypes = [_vp, _vp, _ll, _vp, _ll, _vp, ctypes.POINTER(cj_result),
+                                       _dp, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]
+        L.cj_solve_history.restype = ctypes.c_int
+        L.cj_solve_host.argtypes = [_vp, _vp, _vp, _vp, ctypes.POINTER(cj_result)]
+        L.cj_solve_host.restype = ctypes.c_int
+        L.cj_sweeps.argtypes = [_vp, _vp, _ll, _vp, _ll, _ll, _ll, _vp]
+        L.cj_sweeps.restype = ctypes.c_int
+        L.cj_sweeps_f32.argtypes = [_vp, _vp, _ll, _vp, _ll, _ll, _ll, _vp]
+        L.cj_sweeps_f32.restype = ctypes.c_int
+        L.cj_solution_lo.argtypes = [_vp, _vp, _ll, _vp]
+        L.cj_solution_lo.restype = ctypes.c_int
+        L.cj_residual.argtypes = [_vp, _vp, _ll, _vp, _ll, _vp, _dp, _dp, _dp]
+        L.cj_residual.restype = ctypes.c_int
+        _L = L
+    return _L
+
+
+def cj_status_string(status: int) -> str:
+    return _lib().cj_status_string(status).decode()
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def _grid(t, dtype_name: str):
+    """(pointer, ld) of a 2-D CUDA tensor with unit x-stride."""
+    if not (t.is_cuda and t.dim() == 2 and t.stride(1) == 1 and str(t.dtype) == "torch." + dtype_name):
+        raise ValueError("expected a 2-D CUDA %s tensor with unit x-stride" % dtype_name)
+    return t.data_ptr(), t.stride(0)
+
+
+def cj_plan_create(Nx: int, Ny: int, st: int, tol: float, precision: int = CJ_FP64,
+                   literal_n: int = 0, inner_cycle: int = 0, max_sweeps: int = 0,
+                   bc: int = CJ_BC_DIRICHLET0):
+    """Returns a plan handle (int); free it with cj_plan_destroy."""
+    opt = cj_options(precision, literal_n, inner_cycle, 0, max_sweeps)
+    h = _vp()
+    rc = _lib().cj_plan_create(Nx, Ny, st, bc, tol, ctypes.byref(opt), ctypes.byref(h))
+    if rc != CJ_OK:
+        raise CJError(rc, "cj_plan_create")
+    return h.value
+
+
+def cj_plan_destroy(plan) -> None:
+    _lib().cj_plan_destroy(plan)
+
+
+def cj_plan_info(plan) -> dict:
+    w = _dp()
+    M, Mi = _ll(), _ll()
+    kmin, kmax = ctypes.c_double(), ctypes.c_double()
+    rc = _lib().cj_plan_info(plan, ctypes.byref(w), ctypes.byref(M), ctypes.byref(kmin),
+                             ctypes.byref(kmax), ctypes.byref(Mi))
+    if rc != CJ_OK:
+        raise CJError(rc, "cj_plan_info")
+    return dict(w=np.ctypeslib.as_array(w, shape=(M.value,)).copy(), M=M.value, kmin=kmin.value,
+                kmax=kmax.value, M_inner=Mi.value)
+
+
+def cj_solve(plan, f, u, stream=None, check: bool = True) -> dict:
+    """Solve on device tensors; u is in/out.  Returns the cj_result fields as a dict."""
+    fp, ldf = _grid(f, "float64")
+    up, ldu = _grid(u, "float64")
+    res = cj_result()
+    rc = _lib().cj_solve(plan, fp, ldf, up, ldu, _stream(stream), ctypes.byref(res))
+    if check and rc < 0 and rc not in (CJ_ERR_NOT_CONVERGED, CJ_ERR_DIVERGED):
+        raise CJError(rc, "cj_solve")
+    d = res.as_dict()
+    d["rc"] = rc
+    return d
+
+
+def cj_solve_history(plan, f, u, stream=None, cap: int = 4096, check: bool = True) -> dict:
+    """cj_solve that also returns the relative residual at every residual test."""
+    fp, ldf = _grid(f, "float64")
+    up, ldu = _grid(u, "float64")
+    res = cj_result()
+    hist = (ctypes.c_double * cap)()
+    cnt = ctypes.c_int()
+    rc = _lib().cj_solve_history(plan, fp, ldf, up, ldu, _stream(stream), ctypes.byref(res),
+                                 hist, cap, ctypes.byref(cnt))
+    if check and rc < 0 and rc not in (CJ_ERR_NOT_CONVERGED, CJ_ERR_DIVERGED):
+        raise CJError(rc, "cj_solve_history")
+    d = res.as_dict()
+    d["rc"] = rc
+    d["history"] = list(hist[:min(cnt.value, cap)])
+    return d
+
+
+def cj_solve_host(plan, f_host: np.ndarray, u_host: np.ndarray, stream=None, check: bool = True) -> dict:
+    """Solve on host arrays (C-contiguous float64, shape (Ny, Nx)); u_host is in/out."""
+    for a in (f_host, u_host):
+        if not (isinstance(a, np.ndarray) and a.dtype == np.float64 and a.flags.c_contiguous):
+            raise ValueError("expected C-contiguous float64 numpy arrays")
+    res = cj_result()
+    rc = _lib().cj_solve_host(plan, f_host.ctypes.data, u_host.ctypes.data, _stream(stream),
+                              ctypes.byref(res))
+    if check and rc < 0 and rc not in (CJ_ERR_NOT_CONVERGED, CJ_ERR_DIVERGED):
+        raise CJError(rc, "cj_solve_host")
+    d = res.as_dict()
+    d["rc"] = rc
+    return d
+
+
+def cj_sweeps(plan, f, u, first: int, count: int, stream=None) -> None:
+    fp, ldf = _grid(f, "float64")
+    up, ldu = _grid(u, "float64")
+    rc = _lib().cj_sweeps(plan, fp, ldf, up, ldu, first, count, _stream(stream))
+    if rc != CJ_OK:
+        raise CJError(rc, "cj_sweeps")
+
+
+def cj_sweeps_f32(plan, r, e, first: int, count: int, stream=None) -> None:
+    rp, ldr = _grid(r, "float32")
+    ep, lde = _grid(e, "float32")
+    rc = _lib().cj_sweeps_f32(plan, rp, ldr, ep, lde, first, count, _stream(stream))
+    if rc != CJ_OK:
+        raise CJError(rc, "cj_sweeps_f32")
+
+
+def cj_solution_lo(plan, u_lo, stream=None) -> None:
+    """Low part of the last double-FP64 solve (CJ_FP32_INNER_DD plans)."""
+    up, ld = _grid(u_lo, "float64")
+    rc = _lib().cj_solution_lo(plan, up, ld, _stream(stream))
+    if rc != CJ_OK:
+        raise CJError(rc, "cj_solution_lo")
+
+
+def cj_residual(plan, f, u, stream=None):
+    """(relative L2 residual, relative max residual, FP64 floor estimate) of u."""
+    fp, ldf = _grid(f, "float64")
+    up, ldu = _grid(u, "float64")
+    a, b, c = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    rc = _lib().cj_residual(plan, fp, ldf, up, ldu, _stream(stream), ctypes.byref(a),
+                            ctypes.byref(b), ctypes.byref(c))
+    if rc != CJ_OK:
+        raise CJError(rc, "cj_residual")
+    return a.value, b.value, c.value
+
+
+class Plan:
+    """Owning wrapper: ``with Plan(Nx, Ny, st, tol) as p: cj_solve(p.handle, f, u)``."""
+
+    def __init__(self, Nx, Ny, st, tol, **kw):
+        self.handle = cj_plan_create(Nx, Ny, st, tol, **kw)
+        self.Nx, self.Ny, self.st, self.tol = Nx, Ny, st, tol
+
+    def info(self) -> dict:
+        return cj_plan_info(self.handle)
+
+    def close(self):
+        if self.handle:
+            cj_plan_destroy(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,96 @@
+// Internal declarations of libcj: plan object, padded grid layout, kernel launchers.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <string>
+#include <vector>
+
+#include "cj.h"
+
+// Padded device layout of one grid (FP64 or FP32).  Rows j = -1 .. Ny+2 (two ghost rows
+// each side), columns i = -1 .. Nx+2.  The interior column i = 1 starts `padl` elements
+// into the row, with padl * sizeof(T) = 128 bytes, and the row pitch is a multiple of
+// 128 bytes, so every interior row starts on a 128-byte boundary.  Nodes 0 and N+1 hold
+// the Dirichlet value 0 for the whole life of the buffer; the outer ghost layer (-1, N+2)
+// holds the odd reflection of the interior, rewritten by every kernel that writes the
+// interior (needed by the 17-point stencil only).
+struct Grid {
+    int Nx, Ny;
+    int padl;        // elements before column i = 1
+    long long pitch; // elements per row
+    __host__ __device__ long long idx(int i, int j) const {
+        return (long long)(j + 1) * pitch + (padl - 1) + i;
+    }
+    __host__ __device__ long long elems() const { return pitch * (long long)(Ny + 4); }
+};
+
+Grid make_grid(int Nx, int Ny, int elem_bytes);
+
+// Launch shape of the y-marching kernels: blocks of kBX threads, one column each, every
+// block walks `ty` consecutive rows.
+constexpr int kBX = 128;
+struct March {
+    int nbx, nby, ty;
+    int blocks() const { return nbx * nby; }
+};
+
+struct cj_plan {
+    int Nx, Ny, st, r, precision, literal_n;
+    double tol, kmin, kmax, c, S, h2;
+    long long M, M_in, max_sweeps;
+    std::vector<double> w;    // sweep coefficients w_n = omega_n / c, application order
+    std::vector<float> w32;   // FP32 inner cycle coefficients
+    int device;
+    Grid g64, g32;
+    March m64, m32;
+    double *u0 = nullptr, *u1 = nullptr, *b = nullptr;    // padded FP64
+    float *e0 = nullptr, *e1 = nullptr, *rt = nullptr;    // padded FP32 (mixed only)
+    double *partials = nullptr;                           // 3 doubles per block
+    double *red = nullptr;                                // 8 reduced doubles
+    double *h_red = nullptr;                              // pinned copy of red
+    int max_parts = 0;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;             // brackets of a cycle's sweeps
+};
+
+// ---- plan math (plan.cpp)
+double plan_centre(int st);
+double plan_abs_coeff_sum(int st);
+void plan_kappa_bounds(int st, double nint_x, double nint_y, double *kmin, double *kmax);
+long long plan_cycle_length(double kmin, double kmax, double tol);
+long long plan_inner_cycle(double kmin, double kmax, long long M);
+void plan_sweep_coeffs(int st, double kmin, double kmax, long long M, std::vector<double> &w);
+
+// ---- error reporting (solve.cpp)
+void set_cuda_error(cudaError_t e, const char *where);
+void set_error_text(const char *msg);
+
+// ---- kernel launchers (kernels.cu); every launcher returns the launch error
+March plan_march(int Nx, int Ny, int st, bool fp64);
+// caller grids -> padded b = h^2 f and u; red[3..4] = (sum b^2, max |b|)
+cudaError_t launch_import(const cj_plan *p, const double *f, long long ldf, const double *u,
+                          long long ldu, double *b_out, double *u_out, cudaStream_t s);
+cudaError_t launch_export(const cj_plan *p, const double *u_pad, double *u, long long ldu,
+                          cudaStream_t s);
+cudaError_t launch_sweep64(const cj_plan *p, const double *u, double *out, double w,
+                           cudaStream_t s);
+cudaError_t launch_sweep32(const cj_plan *p, const float *e, const float *r, float *out, float w,
+                           cudaStream_t s);
+// residual of u_pad against p->b: red[0..2] = (sum r^2, max|r|, sum u^2); with rt != NULL
+// also writes rt = (float)(b - L u) and zeroes e_zero (the defect step of the mixed solve)
+cudaError_t launch_residual(const cj_plan *p, const double *u_pad, float *rt, float *e_zero,
+                            cudaStream_t s);
+// fixed-order reduction of nparts (sum, max, sum) triples into out[0..2]
+cudaError_t launch_reduce(const double *partials, int nparts, double *out, cudaStream_t s);
+cudaError_t launch_correct(const cj_plan *p, double *u_pad, const float *e, cudaStream_t s);
+// double-FP64 outer form (dd.cu): defect R = L (uh + ul) - b to about twice FP64
+// precision -> rt = (float)(-R), e_zero = 0, red[0..2] = (sum R^2, max |R|, sum uh^2);
+// and the correction (uh, ul) += e by TwoSum
+cudaError_t launch_defect_dd(const cj_plan *p, const double *uh, const double *ul, float *rt,
+                             float *e_zero, cudaStream_t s);
+cudaError_t launch_correct_dd(const cj_plan *p, double *uh, double *ul, const float *e,
+                              cudaStream_t s);
+cudaError_t launch_import32(const cj_plan *p, const float *src, long long ld, float *dst_pad,
+                            cudaStream_t s);
+cudaError_t launch_export32(const cj_plan *p, const float *src_pad, float *dst, long long ld,
+                            cudaStream_t s);

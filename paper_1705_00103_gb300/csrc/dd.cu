@@ -1,0 +1,178 @@
+// Double-FP64 outer step of the mixed-precision Chebyshev-Jacobi solve (sm_103a).
+//
+// The solution is kept as the unevaluated sum u_hi + u_lo of two FP64 grids, and the
+// defect R = L (u_hi + u_lo) - b is evaluated to about twice FP64 precision: multiplied by
+// the stencil's denominator D (1, 6 or 72; Table 3, Eq. 1, Eq. 2), L u_hi - b becomes a sum
+// of terms that are exact in FP64 (power-of-two multiples of u_hi and b), which are added
+// by the error-free TwoSum cascade (Sum2 of Ogita, Rump and Oishi); D L u_lo is added in
+// plain FP64.  This lifts the FP64 rounding floor of the relative residual (about
+// 2^-53 S ||u|| / ||b||, 5e-10 for the 9-point stencil on 4096^2), so the FP32 inner
+// cycles can drive the residual to 1e-10 and below.  Runs once per outer step, so it is a
+// plain one-thread-per-node kernel; the term order is fixed and equals the reference's.
+#include "cj_internal.h"
+#include "grid_dev.cuh"
+
+namespace {
+
+__device__ __forceinline__ void two_sum(double a, double b, double &s, double &e) {
+    double x = a + b;
+    double z = x - a;
+    e = (a - (x - z)) + (b - z);
+    s = x;
+}
+
+struct Sum2 {
+    double S = 0.0, E = 0.0;
+    __device__ __forceinline__ void add(double t) {
+        double e;
+        two_sum(S, t, S, e);
+        E += e;
+    }
+};
+
+// Plain FP64 L u at node (i, j) in the evaluation order of the sweep kernels (b = 0).
+template <int ST>
+__device__ __forceinline__ double plain_L(const double *u, const Grid &g, int i, int j) {
+    auto U = [&](int di, int dj) { return u[g.idx(i + di, j + dj)]; };
+    const double uC = U(0, 0);
+    const double v1 = U(0, -1) + U(0, 1);
+    const double p0 = U(-1, 0) + U(1, 0);
+    if (ST == 5) return (p0 + v1) + fma(-4.0, uC, -0.0);
+    const double pm = U(-1, -1) + U(1, -1);
+    const double pp = U(-1, 1) + U(1, 1);
+    if (ST == 9)
+        return fma(4.0 / 6.0, p0 + v1, fma(1.0 / 6.0, pm + pp, fma(-20.0 / 6.0, uC, -0.0)));
+    const double v2 = U(0, -2) + U(0, 2);
+    const double P0 = U(-2, 0) + U(2, 0);
+    const double Pm = U(-2, -2) + U(2, -2);
+    const double Pp = U(-2, 2) + U(2, 2);
+    return fma(64.0 / 72.0, p0 + v1,
+               fma(-4.0 / 72.0, P0 + v2,
+                   fma(16.0 / 72.0, pm + pp, fma(-1.0 / 72.0, Pm + Pp, fma(-300.0 / 72.0, uC, -0.0)))));
+}
+
+// R = L (uh + ul) - bk at node (i, j), rounded to FP64 (term order as documented above).
+template <int ST>
+__device__ __forceinline__ double resid_dd(const double *uh, const double *ul, const Grid &g,
+                                           int i, int j, double bk) {
+    auto H = [&](int di, int dj) { return uh[g.idx(i + di, j + dj)]; };
+    const double uC = H(0, 0);
+    Sum2 s;
+    double D;
+    if (ST == 5) {
+        D = 1.0;
+        s.add(H(-1, 0));
+        s.add(H(1, 0));
+        s.add(H(0, -1));
+        s.add(H(0, 1));
+        s.add(-4.0 * uC);
+        s.add(-bk);
+    } else if (ST == 9) {
+        D = 6.0;
+        s.add(4.0 * H(-1, 0));
+        s.add(4.0 * H(1, 0));
+        s.add(4.0 * H(0, -1));
+        s.add(4.0 * H(0, 1));
+        s.add(H(-1, -1));
+        s.add(H(1, -1));
+        s.add(H(-1, 1));
+        s.add(H(1, 1));
+        s.add(-16.0 * uC);
+        s.add(-4.0 * uC);
+        s.add(-4.0 * bk);
+        s.add(-2.0 * bk);
+    } else {
+        D = 72.0;
+        s.add(64.0 * H(-1, 0));
+        s.add(64.0 * H(1, 0));
+        s.add(64.0 * H(0, -1));
+        s.add(64.0 * H(0, 1));
+        s.add(-4.0 * H(-2, 0));
+        s.add(-4.0 * H(2, 0));
+        s.add(-4.0 * H(0, -2));
+        s.add(-4.0 * H(0, 2));
+        s.add(16.0 * H(-1, -1));
+        s.add(16.0 * H(1, -1));
+        s.add(16.0 * H(-1, 1));
+        s.add(16.0 * H(1, 1));
+        s.add(-H(-2, -2));
+        s.add(-H(2, -2));
+        s.add(-H(-2, 2));
+        s.add(-H(2, 2));
+        s.add(-256.0 * uC);
+        s.add(-32.0 * uC);
+        s.add(-8.0 * uC);
+        s.add(-4.0 * uC);
+        s.add(-64.0 * bk);
+        s.add(-8.0 * bk);
+    }
+    const double Llo = plain_L<ST>(ul, g, i, j);
+    return (s.S + (s.E + D * Llo)) / D;
+}
+
+template <int ST>
+__global__ void __launch_bounds__(kBX) defect_dd_kernel(const double *__restrict__ uh,
+                                                        const double *__restrict__ ul,
+                                                        const double *__restrict__ b, Grid g,
+                                                        float *rt, float *ez, Grid g32,
+                                                        double *partials) {
+    const int i = blockIdx.x * kBX + threadIdx.x + 1;
+    double s2 = 0.0, mx = 0.0, u2 = 0.0;
+    if (i <= g.Nx) {
+        for (int j = blockIdx.y + 1; j <= g.Ny; j += gridDim.y) {
+            const double R = resid_dd<ST>(uh, ul, g, i, j, b[g.idx(i, j)]);
+            const double uc = uh[g.idx(i, j)];
+            s2 = fma(R, R, s2);
+            mx = fmax(mx, fabs(R));
+            u2 = fma(uc, uc, u2);
+            rt[g32.idx(i, j)] = (float)(-R);
+            store_node<(ST == 17 ? 2 : 1), float>(ez, g32, i, j, 0.0f);
+        }
+    }
+    block_reduce3(s2, mx, u2, partials);
+}
+
+template <int R>
+__global__ void __launch_bounds__(kBX) correct_dd_kernel(double *uh, double *ul,
+                                                         const float *__restrict__ e, Grid g,
+                                                         Grid g32) {
+    const int i = blockIdx.x * kBX + threadIdx.x + 1;
+    if (i > g.Nx) return;
+    for (int j = blockIdx.y + 1; j <= g.Ny; j += gridDim.y) {
+        const long long k = g.idx(i, j);
+        double hi, err, h2, l2;
+        two_sum(uh[k], (double)e[g32.idx(i, j)], hi, err);
+        const double lo = ul[k] + err;
+        two_sum(hi, lo, h2, l2);
+        store_node<R, double>(uh, g, i, j, h2);
+        store_node<R, double>(ul, g, i, j, l2);
+    }
+}
+
+inline dim3 node_grid(const Grid &g) {
+    return dim3((g.Nx + kBX - 1) / kBX, g.Ny < 1024 ? g.Ny : 1024);
+}
+
+}  // namespace
+
+cudaError_t launch_defect_dd(const cj_plan *p, const double *uh, const double *ul, float *rt,
+                             float *e_zero, cudaStream_t s) {
+    const dim3 grid = node_grid(p->g64);
+    switch (p->st) {
+        case 5: defect_dd_kernel<5><<<grid, kBX, 0, s>>>(uh, ul, p->b, p->g64, rt, e_zero, p->g32, p->partials); break;
+        case 9: defect_dd_kernel<9><<<grid, kBX, 0, s>>>(uh, ul, p->b, p->g64, rt, e_zero, p->g32, p->partials); break;
+        default: defect_dd_kernel<17><<<grid, kBX, 0, s>>>(uh, ul, p->b, p->g64, rt, e_zero, p->g32, p->partials); break;
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    return launch_reduce(p->partials, (int)(grid.x * grid.y), p->red, s);
+}
+
+cudaError_t launch_correct_dd(const cj_plan *p, double *uh, double *ul, const float *e,
+                              cudaStream_t s) {
+    if (p->r == 2)
+        correct_dd_kernel<2><<<node_grid(p->g64), kBX, 0, s>>>(uh, ul, e, p->g64, p->g32);
+    else
+        correct_dd_kernel<1><<<node_grid(p->g64), kBX, 0, s>>>(uh, ul, e, p->g64, p->g32);
+    return cudaGetLastError();
+}

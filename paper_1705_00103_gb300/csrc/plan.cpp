@@ -1,0 +1,101 @@
+// Plan numerics of the Chebyshev-Jacobi method (Sec. 2.1): eigenvalue bounds, cycle
+// length, Chebyshev weights and their application order.  Host FP64, compiled with
+// -ffp-contract=off so each expression rounds exactly as written.
+#include <cmath>
+#include <vector>
+
+#include "cj_internal.h"
+
+namespace {
+const double kPi = 3.14159265358979323846;
+inline double sin2(double x) {
+    double s = std::sin(x);
+    return s * s;
+}
+}  // namespace
+
+// c = -(centre coefficient of h^2 Delta_h): Table 3 (5-point), Eq. 1 (9-point: -20/6),
+// Eq. 2 (17-point: -300/72).
+double plan_centre(int st) {
+    if (st == 5) return 4.0;
+    if (st == 9) return 20.0 / 6.0;
+    return 300.0 / 72.0;
+}
+
+// Sum of the absolute coefficients of h^2 Delta_h (the FP64 rounding-floor factor S).
+double plan_abs_coeff_sum(int st) {
+    if (st == 5) return 8.0;
+    if (st == 9) return 40.0 / 6.0;
+    return 640.0 / 72.0;
+}
+
+// [kmin, kmax] of D^-1 A.  nint_x, nint_y are the paper's N: Nx + 1 intervals for the
+// exact bound, Nx for the paper-literal variant.  9- and 17-point: the closed forms
+// printed after Eq. 1 and Eq. 2; 5-point: the same Fourier analysis of Table 3's stencil.
+void plan_kappa_bounds(int st, double nint_x, double nint_y, double *kmin, double *kmax) {
+    double hx = kPi / (2.0 * nint_x), hy = kPi / (2.0 * nint_y);  // pi / 2N
+    if (st == 5) {
+        *kmin = sin2(hx) + sin2(hy);
+        *kmax = 2.0;
+        return;
+    }
+    if (st == 9) {
+        *kmin = (4.0 / 5.0) * (sin2(hx) + sin2(hy)) + (1.0 / 5.0) * (sin2(hx + hy) + sin2(hx - hy));
+        *kmax = 8.0 / 5.0;
+        return;
+    }
+    double fx = kPi / nint_x, fy = kPi / nint_y;  // pi / N
+    *kmin = -(4.0 / 75.0) * (sin2(fx) + sin2(fy)) + (64.0 / 75.0) * (sin2(hx) + sin2(hy)) -
+            (1.0 / 75.0) * (sin2(fx + fy) + sin2(fx - fy)) +
+            (16.0 / 75.0) * (sin2(hx + hy) + sin2(hx - hy));
+    *kmax = 128.0 / 75.0;
+}
+
+// Smallest power of two M with 1/T_M(sigma) <= tol, sigma = (kmax+kmin)/(kmax-kmin).
+// acosh(sigma) is taken as log1p(d + sqrt(d (2 + d))), d = sigma - 1, to keep its digits
+// when kmin << kmax.
+long long plan_cycle_length(double kmin, double kmax, double tol) {
+    double d = 2.0 * kmin / (kmax - kmin);
+    double a = std::log1p(d + std::sqrt(d * (2.0 + d)));
+    double need = std::log(1.0 / tol + std::sqrt(1.0 / (tol * tol) - 1.0));
+    double m0 = std::ceil(need / a);
+    long long m = 1;
+    while ((double)m < m0) m *= 2;
+    return m;
+}
+
+// Inner FP32 cycle length of the mixed-precision solve: the power of two nearest above
+// 7 / acosh(sigma), so that one inner cycle cuts the residual by about 2 e^-7 ~ 1e-3, at
+// most 8192 (beyond that the FP32 rounding amplified by the weight order, ~1e5 x 6e-8,
+// stops being small) and at most the FP64 cycle length M.
+long long plan_inner_cycle(double kmin, double kmax, long long M) {
+    double d = 2.0 * kmin / (kmax - kmin);
+    double a = std::log1p(d + std::sqrt(d * (2.0 + d)));
+    double want = std::ceil(7.0 / a);
+    long long m = 1;
+    while ((double)m < want && m < 8192) m *= 2;
+    return m < M ? m : M;
+}
+
+// Per-sweep coefficients w_n = 1 / (c * lambda_{o(n)}), lambda_j = (kmax+kmin)/2 +
+// (kmax-kmin)/2 * cos((2j-1) pi / 2M), applied in the mirror-pairing order o: o = (1)
+// for M = 1; going from m to 2m, every entry j of o is followed by 2m+1-j.
+void plan_sweep_coeffs(int st, double kmin, double kmax, long long M, std::vector<double> &w) {
+    std::vector<long long> o(1, 1), next;
+    for (long long m = 1; m < M; m *= 2) {
+        next.resize(2 * m);
+        for (long long k = 0; k < m; ++k) {
+            next[2 * k] = o[k];
+            next[2 * k + 1] = 2 * m + 1 - o[k];
+        }
+        o.swap(next);
+    }
+    double c = plan_centre(st);
+    double mid = 0.5 * (kmax + kmin), half = 0.5 * (kmax - kmin);
+    w.resize(M);
+    for (long long n = 0; n < M; ++n) {
+        double x = std::cos((double)(2 * o[n] - 1) * kPi / (double)(2 * M));
+        double lam = mid + half * x;
+        w[n] = 1.0 / (c * lam);
+    }
+}

@@ -1,0 +1,517 @@
+// C ABI of libcj: plan lifetime, the CJM solve drivers (Sec. 2.1: "a set of weights ...
+// precalculated before starting the iterative algorithm", then M weighted sweeps per
+// cycle), the sweep and residual entry points.  Host C++; the device work is in
+// kernels.cu.
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "cj_internal.h"
+
+namespace {
+
+thread_local char g_err[256] = "";
+
+const double kEps = 1.1102230246251565e-16;  // 2^-53
+
+bool is_pow2(long long m) { return m >= 1 && (m & (m - 1)) == 0; }
+
+void free_plan(cj_plan *p) {
+    if (!p) return;
+    cudaFree(p->u0);
+    cudaFree(p->u1);
+    cudaFree(p->b);
+    cudaFree(p->e0);
+    cudaFree(p->e1);
+    cudaFree(p->rt);
+    cudaFree(p->partials);
+    cudaFree(p->red);
+    if (p->h_red) cudaFreeHost(p->h_red);
+    if (p->ev0) cudaEventDestroy(p->ev0);
+    if (p->ev1) cudaEventDestroy(p->ev1);
+    delete p;
+}
+
+template <typename T>
+cudaError_t dev_alloc(T **ptr, size_t count) {
+    cudaError_t e = cudaMalloc((void **)ptr, count * sizeof(T));
+    if (e != cudaSuccess) return e;
+    return cudaMemset(*ptr, 0, count * sizeof(T));
+}
+
+// Stop rule applied after each residual evaluation; -1 = go on.  Converged at tol; at
+// the FP64 rounding floor when rho <= 4 fl, or when `patience` consecutive cycles each
+// failed to halve rho (*stall counts them): 1 for plain cycles, 2 for defect-correction
+// steps, whose residual may jump up once (FP32 rounding noise, high-frequency) before
+// it contracts.
+int stop_rule(double rho, double fl, double prev, long long cycles, double tol, int patience,
+              int *stall) {
+    if (rho <= tol) return CJ_OK;
+    if (!(rho == rho) || rho > 1e300) return CJ_ERR_DIVERGED;
+    if (rho <= 4.0 * fl) return CJ_FLOOR;
+    if (cycles > 0) {
+        *stall = rho > 0.5 * prev ? *stall + 1 : 0;
+        if (*stall >= patience) return CJ_FLOOR;
+    }
+    return -1;
+}
+
+// Optional convergence history of the call in progress (rho at every residual test).
+struct History {
+    double *buf = nullptr;
+    int cap = 0, n = 0;
+    void add(double v) {
+        if (n < cap) buf[n] = v;
+        ++n;
+    }
+};
+
+struct Norms {
+    double l2, inf, fl;
+};
+
+// Reads red[] (filled by the residual and import reductions) after a stream sync.  The
+// floor estimate uses unit roundoff `eps` of the solution's representation.
+cj_status fetch_norms(cj_plan *p, cudaStream_t s, Norms *n, double eps = kEps) {
+    cudaError_t e = cudaMemcpyAsync(p->h_red, p->red, 8 * sizeof(double), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) {
+        set_cuda_error(e, "residual readback");
+        return CJ_ERR_CUDA;
+    }
+    const double *r = p->h_red;
+    double bn = std::sqrt(r[3]), bmax = r[4];
+    double rn = std::sqrt(r[0]), un = std::sqrt(r[2]);
+    n->l2 = bn > 0.0 ? rn / bn : rn;
+    n->inf = bmax > 0.0 ? r[1] / bmax : r[1];
+    n->fl = bn > 0.0 ? eps * p->S * un / bn : eps * p->S * un;
+    return CJ_OK;
+}
+
+// Device time between the plan's two events (both already completed).
+double elapsed_ms(cj_plan *p) {
+    float ms = 0.0f;
+    if (cudaEventElapsedTime(&ms, p->ev0, p->ev1) != cudaSuccess) return 0.0;
+    return ms;
+}
+
+#define CJ_TRY(call, where)                 \
+    do {                                    \
+        cudaError_t e_ = (call);            \
+        if (e_ != cudaSuccess) {            \
+            set_cuda_error(e_, where);      \
+            return CJ_ERR_CUDA;             \
+        }                                   \
+    } while (0)
+
+cj_status check_grid_args(const cj_plan *p, const void *f, long long ldf, const void *u,
+                          long long ldu) {
+    if (!p || !f || !u || ldf < p->Nx || ldu < p->Nx) return CJ_ERR_INVALID_ARG;
+    return CJ_OK;
+}
+
+// The solve proper, once f and u have been imported into the plan's padded buffers.
+cj_status run_fp64(cj_plan *p, cudaStream_t s, double **cur_out, cj_result *res, History *h) {
+    double *cur = p->u0, *nxt = p->u1;
+    long long sweeps = 0, cycles = 0;
+    double prev = 0.0, sweep_ms = 0.0;
+    bool timed = false;
+    Norms n{};
+    int stat, stall = 0;
+    for (;;) {
+        CJ_TRY(launch_residual(p, cur, nullptr, nullptr, s), "residual");
+        res->launches += 2;
+        cj_status st = fetch_norms(p, s, &n);
+        if (st != CJ_OK) return st;
+        if (timed) sweep_ms += elapsed_ms(p);
+        h->add(n.l2);
+        stat = stop_rule(n.l2, n.fl, prev, cycles, p->tol, 1, &stall);
+        if (stat != -1) break;
+        if (sweeps + p->M > p->max_sweeps) {
+            stat = CJ_ERR_NOT_CONVERGED;
+            break;
+        }
+        CJ_TRY(cudaEventRecord(p->ev0, s), "event");
+        for (long long k = 0; k < p->M; ++k) {
+            CJ_TRY(launch_sweep64(p, cur, nxt, p->w[k], s), "sweep");
+            double *t = cur;
+            cur = nxt;
+            nxt = t;
+        }
+        CJ_TRY(cudaEventRecord(p->ev1, s), "event");
+        timed = true;
+        res->launches += p->M;
+        sweeps += p->M;
+        cycles += 1;
+        prev = n.l2;
+    }
+    res->sweep_seconds = 1e-3 * sweep_ms;
+    *cur_out = cur;
+    res->sweeps = sweeps;
+    res->cycles = (int)cycles;
+    res->status = stat;
+    res->rel_res_l2 = n.l2;
+    res->rel_res_inf = n.inf;
+    res->floor_est = n.fl;
+    return (cj_status)stat;
+}
+
+// Mixed precision: FP64 defect r = b - L u -> FP32 rt; one FP32 CJM cycle of length M_in
+// on L e = rt from e = 0; u += e in FP64; repeat until the FP64 stop rule ends it.
+cj_status run_mixed(cj_plan *p, cudaStream_t s, double **cur_out, cj_result *res, History *h) {
+    long long sweeps = 0, outer = 0;
+    const long long max_outer = p->max_sweeps / p->M_in;
+    double prev = 0.0, sweep_ms = 0.0;
+    bool timed = false;
+    Norms n{};
+    int stat, stall = 0;
+    for (;;) {
+        CJ_TRY(launch_residual(p, p->u0, p->rt, p->e0, s), "defect");
+        res->launches += 2;
+        cj_status st = fetch_norms(p, s, &n);
+        if (st != CJ_OK) return st;
+        if (timed) sweep_ms += elapsed_ms(p);
+        h->add(n.l2);
+        stat = stop_rule(n.l2, n.fl, prev, outer, p->tol, 2, &stall);
+        if (stat != -1) break;
+        if (outer >= max_outer) {
+            stat = CJ_ERR_NOT_CONVERGED;
+            break;
+        }
+        float *cur = p->e0, *nxt = p->e1;
+        CJ_TRY(cudaEventRecord(p->ev0, s), "event");
+        for (long long k = 0; k < p->M_in; ++k) {
+            CJ_TRY(launch_sweep32(p, cur, p->rt, nxt, p->w32[k], s), "sweep32");
+            float *t = cur;
+            cur = nxt;
+            nxt = t;
+        }
+        CJ_TRY(cudaEventRecord(p->ev1, s), "event");
+        timed = true;
+        CJ_TRY(launch_correct(p, p->u0, cur, s), "correct");
+        res->launches += p->M_in + 1;
+        sweeps += p->M_in;
+        outer += 1;
+        prev = n.l2;
+    }
+    res->sweep_seconds = 1e-3 * sweep_ms;
+    *cur_out = p->u0;
+    res->sweeps = sweeps;
+    res->cycles = (int)outer;
+    res->status = stat;
+    res->rel_res_l2 = n.l2;
+    res->rel_res_inf = n.inf;
+    res->floor_est = n.fl;
+    return (cj_status)stat;
+}
+
+// Mixed precision with the double-FP64 outer loop: the solution is u0 + u1 (hi + lo), the
+// defect is evaluated to about twice FP64 precision and the correction added by TwoSum.
+cj_status run_mixed_dd(cj_plan *p, cudaStream_t s, double **cur_out, cj_result *res, History *h) {
+    long long sweeps = 0, outer = 0;
+    const long long max_outer = p->max_sweeps / p->M_in;
+    const double eps2 = 1.2325951644078309e-32;  // 2^-106
+    double prev = 0.0, sweep_ms = 0.0;
+    bool timed = false;
+    Norms n{};
+    int stat, stall = 0;
+    CJ_TRY(cudaMemsetAsync(p->u1, 0, (size_t)p->g64.elems() * sizeof(double), s), "zero u_lo");
+    for (;;) {
+        CJ_TRY(launch_defect_dd(p, p->u0, p->u1, p->rt, p->e0, s), "defect dd");
+        res->launches += 2;
+        cj_status st = fetch_norms(p, s, &n, eps2);
+        if (st != CJ_OK) return st;
+        if (timed) sweep_ms += elapsed_ms(p);
+        h->add(n.l2);
+        stat = stop_rule(n.l2, n.fl, prev, outer, p->tol, 2, &stall);
+        if (stat != -1) break;
+        if (outer >= max_outer) {
+            stat = CJ_ERR_NOT_CONVERGED;
+            break;
+        }
+        float *cur = p->e0, *nxt = p->e1;
+        CJ_TRY(cudaEventRecord(p->ev0, s), "event");
+        for (long long k = 0; k < p->M_in; ++k) {
+            CJ_TRY(launch_sweep32(p, cur, p->rt, nxt, p->w32[k], s), "sweep32");
+            float *t = cur;
+            cur = nxt;
+            nxt = t;
+        }
+        CJ_TRY(cudaEventRecord(p->ev1, s), "event");
+        timed = true;
+        CJ_TRY(launch_correct_dd(p, p->u0, p->u1, cur, s), "correct dd");
+        res->launches += p->M_in + 1;
+        sweeps += p->M_in;
+        outer += 1;
+        prev = n.l2;
+    }
+    res->sweep_seconds = 1e-3 * sweep_ms;
+    *cur_out = p->u0;
+    res->sweeps = sweeps;
+    res->cycles = (int)outer;
+    res->status = stat;
+    res->rel_res_l2 = n.l2;
+    res->rel_res_inf = n.inf;
+    res->floor_est = n.fl;
+    return (cj_status)stat;
+}
+
+cj_status solve_core(cj_plan *p, const double *f, long long ldf, double *u, long long ldu,
+                     cudaStream_t s, cj_result *res, History *h) {
+    auto t0 = std::chrono::steady_clock::now();
+    cj_result r{};
+    CJ_TRY(launch_import(p, f, ldf, u, ldu, p->b, p->u0, s), "import");
+    r.launches = 2;
+    double *cur = nullptr;
+    cj_status st = p->precision == CJ_FP32_INNER      ? run_mixed(p, s, &cur, &r, h)
+                   : p->precision == CJ_FP32_INNER_DD ? run_mixed_dd(p, s, &cur, &r, h)
+                                                      : run_fp64(p, s, &cur, &r, h);
+    if (st < 0 && st != CJ_ERR_NOT_CONVERGED && st != CJ_ERR_DIVERGED) return st;
+    CJ_TRY(launch_export(p, cur, u, ldu, s), "export");
+    r.launches += 1;
+    CJ_TRY(cudaStreamSynchronize(s), "solve sync");
+    r.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    if (res) *res = r;
+    return st;
+}
+
+}  // namespace
+
+void set_cuda_error(cudaError_t e, const char *where) {
+    std::snprintf(g_err, sizeof(g_err), "%s: %s", where, cudaGetErrorString(e));
+}
+
+void set_error_text(const char *msg) { std::snprintf(g_err, sizeof(g_err), "%s", msg); }
+
+extern "C" {
+
+const char *cj_status_string(int status) {
+    switch (status) {
+        case CJ_OK: return "converged";
+        case CJ_FLOOR: return "stopped at the FP64 rounding floor";
+        case CJ_PENDING: return "pending";
+        case CJ_ERR_INVALID_ARG: return "invalid argument";
+        case CJ_ERR_NOMEM: return "out of memory";
+        case CJ_ERR_NOT_CONVERGED: return "sweep budget exhausted";
+        case CJ_ERR_DIVERGED: return "residual not finite";
+        case CJ_ERR_TIMEOUT: return "device wait timed out";
+        case CJ_ERR_CUDA: return "CUDA error";
+        case CJ_ERR_BUDGET: return "memory budget exceeded";
+        default: return "unknown status";
+    }
+}
+
+const char *cj_last_error(void) { return g_err; }
+
+cj_status cj_plan_create(int Nx, int Ny, cj_stencil st, cj_bc bc, double tol,
+                         const cj_options *opt, cj_plan **out) {
+    if (!out) return CJ_ERR_INVALID_ARG;
+    *out = nullptr;
+    cj_options o{};
+    if (opt) o = *opt;
+    if (Nx < 1 || Ny < 1 || Nx > (1 << 20) || Ny > (1 << 20)) return CJ_ERR_INVALID_ARG;
+    if (st != CJ_ST5 && st != CJ_ST9 && st != CJ_ST17) return CJ_ERR_INVALID_ARG;
+    if (bc != CJ_BC_DIRICHLET0) return CJ_ERR_INVALID_ARG;
+    if (!(tol > 0.0 && tol < 1.0)) return CJ_ERR_INVALID_ARG;
+    if (o.precision != CJ_FP64 && o.precision != CJ_FP32_INNER && o.precision != CJ_FP32_INNER_DD)
+        return CJ_ERR_INVALID_ARG;
+    if (o.inner_cycle != 0 && !is_pow2(o.inner_cycle)) return CJ_ERR_INVALID_ARG;
+    if (o.max_sweeps < 0) return CJ_ERR_INVALID_ARG;
+
+    cj_plan *p = new (std::nothrow) cj_plan();
+    if (!p) return CJ_ERR_NOMEM;
+    try {
+        p->Nx = Nx;
+        p->Ny = Ny;
+        p->st = st;
+        p->r = st == CJ_ST17 ? 2 : 1;
+        p->precision = o.precision;
+        p->literal_n = o.literal_n ? 1 : 0;
+        p->tol = tol;
+        plan_kappa_bounds(st, p->literal_n ? (double)Nx : (double)(Nx + 1),
+                          p->literal_n ? (double)Ny : (double)(Ny + 1), &p->kmin, &p->kmax);
+        if (!(p->kmin > 0.0 && p->kmin < p->kmax)) {
+            free_plan(p);
+            return CJ_ERR_INVALID_ARG;
+        }
+        p->c = plan_centre(st);
+        p->S = plan_abs_coeff_sum(st);
+        double h = 1.0 / (double)(Nx + 1);
+        p->h2 = h * h;
+        p->M = plan_cycle_length(p->kmin, p->kmax, tol);
+        if (p->M > (1LL << 24)) {
+            free_plan(p);
+            return CJ_ERR_INVALID_ARG;
+        }
+        plan_sweep_coeffs(st, p->kmin, p->kmax, p->M, p->w);
+        p->M_in = 0;
+        if (p->precision != CJ_FP64) {
+            p->M_in = o.inner_cycle ? o.inner_cycle : plan_inner_cycle(p->kmin, p->kmax, p->M);
+            std::vector<double> wi;
+            plan_sweep_coeffs(st, p->kmin, p->kmax, p->M_in, wi);
+            p->w32.resize(p->M_in);
+            for (long long k = 0; k < p->M_in; ++k) p->w32[k] = (float)wi[k];
+        }
+        long long unit = p->precision != CJ_FP64 ? p->M_in : p->M;
+        p->max_sweeps = o.max_sweeps ? o.max_sweeps : 64 * unit;
+    } catch (...) {
+        free_plan(p);
+        return CJ_ERR_NOMEM;
+    }
+    cudaError_t e = cudaGetDevice(&p->device);
+    if (e != cudaSuccess) {
+        set_cuda_error(e, "cudaGetDevice");
+        free_plan(p);
+        return CJ_ERR_CUDA;
+    }
+    p->g64 = make_grid(Nx, Ny, 8);
+    p->g32 = make_grid(Nx, Ny, 4);
+    p->m64 = plan_march(Nx, Ny, st, true);
+    p->m32 = plan_march(Nx, Ny, st, false);
+    long long copy_parts = (long long)((Nx + kBX - 1) / kBX) * (Ny < 1024 ? Ny : 1024);
+    long long parts = p->m64.blocks();
+    if (copy_parts > parts) parts = copy_parts;
+    p->max_parts = (int)parts;
+    const size_t n64 = (size_t)p->g64.elems(), n32 = (size_t)p->g32.elems();
+    e = dev_alloc(&p->u0, n64);
+    if (e == cudaSuccess) e = dev_alloc(&p->b, n64);
+    if (e == cudaSuccess && p->precision != CJ_FP32_INNER) e = dev_alloc(&p->u1, n64);
+    if (e == cudaSuccess && p->precision != CJ_FP64) {
+        e = dev_alloc(&p->e0, n32);
+        if (e == cudaSuccess) e = dev_alloc(&p->e1, n32);
+        if (e == cudaSuccess) e = dev_alloc(&p->rt, n32);
+    }
+    if (e == cudaSuccess) e = dev_alloc(&p->partials, (size_t)3 * parts);
+    if (e == cudaSuccess) e = dev_alloc(&p->red, 8);
+    if (e == cudaSuccess) e = cudaMallocHost((void **)&p->h_red, 8 * sizeof(double));
+    if (e == cudaSuccess) e = cudaEventCreate(&p->ev0);
+    if (e == cudaSuccess) e = cudaEventCreate(&p->ev1);
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) {
+        set_cuda_error(e, "plan allocation");
+        free_plan(p);
+        return e == cudaErrorMemoryAllocation ? CJ_ERR_NOMEM : CJ_ERR_CUDA;
+    }
+    *out = p;
+    return CJ_OK;
+}
+
+void cj_plan_destroy(cj_plan *plan) { free_plan(plan); }
+
+cj_status cj_plan_info(const cj_plan *p, const double **w, long long *M, double *kmin,
+                       double *kmax, long long *M_inner) {
+    if (!p) return CJ_ERR_INVALID_ARG;
+    if (w) *w = p->w.data();
+    if (M) *M = p->M;
+    if (kmin) *kmin = p->kmin;
+    if (kmax) *kmax = p->kmax;
+    if (M_inner) *M_inner = p->M_in;
+    return CJ_OK;
+}
+
+cj_status cj_solve(cj_plan *p, const double *f, long long ldf, double *u, long long ldu,
+                   void *stream, cj_result *res) {
+    cj_status a = check_grid_args(p, f, ldf, u, ldu);
+    if (a != CJ_OK) return a;
+    History h;
+    return solve_core(p, f, ldf, u, ldu, (cudaStream_t)stream, res, &h);
+}
+
+cj_status cj_solve_history(cj_plan *p, const double *f, long long ldf, double *u, long long ldu,
+                           void *stream, cj_result *res, double *history, int cap, int *count) {
+    cj_status a = check_grid_args(p, f, ldf, u, ldu);
+    if (a != CJ_OK) return a;
+    if (cap < 0 || (cap > 0 && !history)) return CJ_ERR_INVALID_ARG;
+    History h;
+    h.buf = history;
+    h.cap = cap;
+    cj_status st = solve_core(p, f, ldf, u, ldu, (cudaStream_t)stream, res, &h);
+    if (count) *count = h.n;
+    return st;
+}
+
+cj_status cj_solve_host(cj_plan *p, const double *f_host, double *u_host, void *stream,
+                        cj_result *res) {
+    if (!p || !f_host || !u_host) return CJ_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    auto t0 = std::chrono::steady_clock::now();
+    const Grid &g = p->g64;
+    double *b_in = p->b + g.idx(1, 1), *u_in = p->u0 + g.idx(1, 1);
+    const size_t row = (size_t)p->Nx * sizeof(double), dpitch = (size_t)g.pitch * sizeof(double);
+    CJ_TRY(cudaMemcpy2DAsync(b_in, dpitch, f_host, row, row, p->Ny, cudaMemcpyHostToDevice, s), "H2D f");
+    CJ_TRY(cudaMemcpy2DAsync(u_in, dpitch, u_host, row, row, p->Ny, cudaMemcpyHostToDevice, s), "H2D u");
+    cj_result r{};
+    History h;
+    // f and u now sit in the interiors of the plan's own buffers; the import runs in place.
+    cj_status st = solve_core(p, b_in, g.pitch, u_in, g.pitch, s, &r, &h);
+    if (st < 0 && st != CJ_ERR_NOT_CONVERGED && st != CJ_ERR_DIVERGED) return st;
+    CJ_TRY(cudaMemcpy2DAsync(u_host, row, u_in, dpitch, row, p->Ny, cudaMemcpyDeviceToHost, s), "D2H u");
+    CJ_TRY(cudaStreamSynchronize(s), "D2H sync");
+    r.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    if (res) *res = r;
+    return st;
+}
+
+cj_status cj_sweeps(cj_plan *p, const double *f, long long ldf, double *u, long long ldu,
+                    long long first, long long count, void *stream) {
+    cj_status a = check_grid_args(p, f, ldf, u, ldu);
+    if (a != CJ_OK) return a;
+    if (first < 0 || count < 0 || !p->u1) return CJ_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    CJ_TRY(launch_import(p, f, ldf, u, ldu, p->b, p->u0, s), "import");
+    double *cur = p->u0, *nxt = p->u1;
+    for (long long k = 0; k < count; ++k) {
+        CJ_TRY(launch_sweep64(p, cur, nxt, p->w[(first + k) % p->M], s), "sweep");
+        double *t = cur;
+        cur = nxt;
+        nxt = t;
+    }
+    CJ_TRY(launch_export(p, cur, u, ldu, s), "export");
+    return CJ_OK;
+}
+
+cj_status cj_sweeps_f32(cj_plan *p, const float *r, long long ldr, float *e, long long lde,
+                        long long first, long long count, void *stream) {
+    cj_status a = check_grid_args(p, r, ldr, e, lde);
+    if (a != CJ_OK) return a;
+    if (first < 0 || count < 0 || !p->e0) return CJ_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    CJ_TRY(launch_import32(p, r, ldr, p->rt, s), "import32 r");
+    CJ_TRY(launch_import32(p, e, lde, p->e0, s), "import32 e");
+    float *cur = p->e0, *nxt = p->e1;
+    for (long long k = 0; k < count; ++k) {
+        CJ_TRY(launch_sweep32(p, cur, p->rt, nxt, p->w32[(first + k) % p->M_in], s), "sweep32");
+        float *t = cur;
+        cur = nxt;
+        nxt = t;
+    }
+    CJ_TRY(launch_export32(p, cur, e, lde, s), "export32");
+    return CJ_OK;
+}
+
+cj_status cj_solution_lo(cj_plan *p, double *u_lo, long long ld, void *stream) {
+    if (!p || !u_lo || ld < p->Nx || p->precision != CJ_FP32_INNER_DD) return CJ_ERR_INVALID_ARG;
+    CJ_TRY(launch_export(p, p->u1, u_lo, ld, (cudaStream_t)stream), "export lo");
+    return CJ_OK;
+}
+
+cj_status cj_residual(cj_plan *p, const double *f, long long ldf, const double *u,
+                      long long ldu, void *stream, double *rel_l2, double *rel_inf,
+                      double *floor_est) {
+    cj_status a = check_grid_args(p, f, ldf, u, ldu);
+    if (a != CJ_OK) return a;
+    cudaStream_t s = (cudaStream_t)stream;
+    CJ_TRY(launch_import(p, f, ldf, u, ldu, p->b, p->u0, s), "import");
+    CJ_TRY(launch_residual(p, p->u0, nullptr, nullptr, s), "residual");
+    Norms n{};
+    cj_status st = fetch_norms(p, s, &n);
+    if (st != CJ_OK) return st;
+    if (rel_l2) *rel_l2 = n.l2;
+    if (rel_inf) *rel_inf = n.inf;
+    if (floor_est) *floor_est = n.fl;
+    return CJ_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,65 @@
+"""CPU checks of the C-ABI library: it builds, loads, exports every declared entry point,
+and rejects invalid arguments before touching the GPU."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared_functions():
+    src = open(os.path.join(ROOT, "include", "cj.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    names = re.findall(r"\b(cj_[a-z0-9_]+)\s*\(", src)
+    return sorted(set(names))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1705_00103_gb300 import build
+    return ctypes.CDLL(build.build())
+
+
+def test_header_declares_the_boundary():
+    names = _declared_functions()
+    for n in ("cj_plan_create", "cj_plan_destroy", "cj_plan_info", "cj_solve", "cj_solve_host",
+              "cj_solve_history", "cj_solution_lo",
+              "cj_sweeps", "cj_sweeps_f32", "cj_residual", "cj_status_string", "cj_last_error"):
+        assert n in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    missing = [n for n in _declared_functions() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_library_is_built_for_sm_103a():
+    from paper_1705_00103_gb300 import build
+    assert "arch=compute_103a,code=sm_103a" in " ".join(build.ARCH)
+
+
+def test_invalid_arguments_rejected_without_gpu():
+    import paper_1705_00103_gb300 as cj
+    bad = [dict(Nx=0, Ny=4, st=5, tol=1e-6), dict(Nx=4, Ny=-1, st=5, tol=1e-6),
+           dict(Nx=4, Ny=4, st=7, tol=1e-6), dict(Nx=4, Ny=4, st=9, tol=0.0),
+           dict(Nx=4, Ny=4, st=9, tol=1.0), dict(Nx=4, Ny=4, st=17, tol=1e-6, inner_cycle=12),
+           dict(Nx=4, Ny=4, st=17, tol=1e-6, precision=3), dict(Nx=4, Ny=4, st=5, tol=1e-6, bc=1)]
+    for kw in bad:
+        with pytest.raises(cj.CJError) as ei:
+            cj.cj_plan_create(**kw)
+        assert ei.value.status == cj.CJ_ERR_INVALID_ARG, kw
+
+
+def test_null_plan_rejected(lib):
+    lib.cj_solve.restype = ctypes.c_int
+    assert lib.cj_solve(None, None, 0, None, 0, None, None) == -1
+    lib.cj_plan_destroy(None)
+
+
+def test_status_strings(lib):
+    lib.cj_status_string.restype = ctypes.c_char_p
+    assert lib.cj_status_string(0) == b"converged"
+    assert lib.cj_status_string(1).startswith(b"stopped at")
+    assert lib.cj_status_string(-6) == b"CUDA error"

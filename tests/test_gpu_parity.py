@@ -1,0 +1,304 @@
+"""GPU parity of libcj against the FP64 CPU oracle, through the C ABI.
+
+The sweep, the FP32 inner sweep and the whole FP64 / mixed solves evaluate the same
+arithmetic in the same order on both sides, so they are compared bit for bit (integer
+counters too).  Residual norms are sums reduced in a different order on each side and are
+compared to 1e-12 relative.
+"""
+import numpy as np
+import pytest
+
+from oracle import oracle as orc
+import workloads
+
+pytestmark = pytest.mark.gpu
+
+STENCILS = (5, 9, 17)
+# sizes that span several 128-column blocks and row strips, with ragged tails
+SHAPES = [(1, 1), (1, 7), (6, 1), (3, 5), (17, 9), (130, 70), (257, 131), (300, 64)]
+
+
+@pytest.fixture(scope="module")
+def cj():
+    import paper_1705_00103_gb300 as cj
+    cj.build.build()
+    return cj
+
+
+@pytest.fixture(scope="module")
+def torch():
+    import torch
+    return torch
+
+
+def dev(torch, a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def rand_problem(Nx, Ny, seed):
+    rng = np.random.default_rng(seed)
+    return rng.standard_normal((Ny, Nx)), rng.standard_normal((Ny, Nx))
+
+
+# ----------------------------------------------------------------- plan
+
+@pytest.mark.parametrize("st", STENCILS)
+@pytest.mark.parametrize("Nx,Ny,tol", [(64, 64, 1e-10), (1, 1, 1e-6), (100, 37, 1e-8),
+                                       (4096, 4096, 1e-10), (8192, 8192, 1e-10)])
+def test_plan_matches_oracle(cj, st, Nx, Ny, tol):
+    with cj.Plan(Nx, Ny, st, tol) as p:
+        info = p.info()
+    kmin, kmax = orc.kappa_bounds(st, Nx, Ny)
+    assert info["kmin"] == kmin and info["kmax"] == kmax
+    M = orc.cycle_length(kmin, kmax, tol)
+    assert info["M"] == M
+    np.testing.assert_array_equal(info["w"], orc.sweep_coeffs(st, kmin, kmax, M))
+
+
+def test_plan_literal_n_option(cj):
+    with cj.Plan(63, 63, 9, 1e-8, literal_n=1) as p:
+        info = p.info()
+    assert info["kmin"] == orc.kappa_bounds(9, 63, 63, literal_n=True)[0]
+
+
+# ----------------------------------------------------------------- sweeps
+
+@pytest.mark.parametrize("st", STENCILS)
+@pytest.mark.parametrize("Nx,Ny", SHAPES)
+def test_fp64_sweeps_bit_exact(cj, torch, st, Nx, Ny):
+    """Each of the first sweeps of a cycle equals the oracle's bit for bit."""
+    f, u0 = rand_problem(Nx, Ny, 10 * Nx + Ny + st)
+    with cj.Plan(Nx, Ny, st, 1e-8) as p:
+        w = p.info()["w"]
+        fd = dev(torch, f)
+        ud = dev(torch, u0)
+        b = orc.scale_rhs(f)
+        ref = u0.copy()
+        nsw = min(6, len(w))
+        for k in range(nsw):
+            cj.cj_sweeps(p.handle, fd, ud, k, 1)
+            ref = orc.sweep(st, ref, b, w[k])
+            got = ud.cpu().numpy()
+            np.testing.assert_array_equal(got, ref, err_msg="sweep %d" % k)
+
+
+@pytest.mark.parametrize("st", STENCILS)
+def test_fp64_sweeps_batched_launches(cj, torch, st):
+    """Many sweeps in one call (ping-pong inside the library) equal the oracle's."""
+    Nx, Ny = 203, 77
+    f, u0 = rand_problem(Nx, Ny, st)
+    with cj.Plan(Nx, Ny, st, 1e-6) as p:
+        w = p.info()["w"]
+        fd, ud = dev(torch, f), dev(torch, u0)
+        count = min(33, len(w))
+        cj.cj_sweeps(p.handle, fd, ud, 0, count)
+        b = orc.scale_rhs(f)
+        ref = u0.copy()
+        for k in range(count):
+            ref = orc.sweep(st, ref, b, w[k])
+        np.testing.assert_array_equal(ud.cpu().numpy(), ref)
+
+
+def test_fp64_sweeps_strided_caller_arrays(cj, torch):
+    """Caller rows with ld > Nx are read and written at the right places only."""
+    Nx, Ny, ld = 45, 20, 64
+    f, u0 = rand_problem(Nx, Ny, 3)
+    fbig = np.full((Ny, ld), 7.0)
+    ubig = np.full((Ny, ld), -3.0)
+    fbig[:, :Nx] = f
+    ubig[:, :Nx] = u0
+    with cj.Plan(Nx, Ny, 17, 1e-8) as p:
+        w = p.info()["w"]
+        fd, ud = dev(torch, fbig), dev(torch, ubig)
+        cj.cj_sweeps(p.handle, fd[:, :Nx], ud[:, :Nx], 0, 3)
+        ref = u0.copy()
+        b = orc.scale_rhs(f)
+        for k in range(3):
+            ref = orc.sweep(17, ref, b, w[k])
+        got = ud.cpu().numpy()
+        np.testing.assert_array_equal(got[:, :Nx], ref)
+        assert np.all(got[:, Nx:] == -3.0)
+
+
+@pytest.mark.parametrize("st", STENCILS)
+@pytest.mark.parametrize("Nx,Ny", [(1, 1), (5, 3), (130, 70), (257, 131)])
+def test_fp32_sweeps_bit_exact(cj, torch, st, Nx, Ny):
+    rng = np.random.default_rng(Nx + Ny + st)
+    r = rng.standard_normal((Ny, Nx)).astype(np.float32)
+    e = rng.standard_normal((Ny, Nx)).astype(np.float32)
+    with cj.Plan(Nx, Ny, st, 1e-8, precision=cj.CJ_FP32_INNER, inner_cycle=16) as p:
+        kmin, kmax = orc.kappa_bounds(st, Nx, Ny)
+        w32 = orc.sweep_coeffs(st, kmin, kmax, 16).astype(np.float32)
+        rd, ed = dev(torch, r), dev(torch, e)
+        ref = e.copy()
+        for k in range(5):
+            cj.cj_sweeps_f32(p.handle, rd, ed, k, 1)
+            ref = orc.sweep_f32(st, ref, r, w32[k])
+            np.testing.assert_array_equal(ed.cpu().numpy(), ref, err_msg="sweep %d" % k)
+
+
+# ----------------------------------------------------------------- residual
+
+@pytest.mark.parametrize("st", STENCILS)
+@pytest.mark.parametrize("Nx,Ny", [(1, 1), (17, 9), (300, 64)])
+def test_residual_norms(cj, torch, st, Nx, Ny):
+    f, u = rand_problem(Nx, Ny, 5 + st)
+    with cj.Plan(Nx, Ny, st, 1e-8) as p:
+        l2, linf, fl = cj.cj_residual(p.handle, dev(torch, f), dev(torch, u))
+    b = orc.scale_rhs(f)
+    s, m = orc.residual(st, u, b)
+    assert l2 == pytest.approx(np.sqrt(s) / np.linalg.norm(b), rel=1e-12)
+    assert linf == pytest.approx(m / np.abs(b).max(), rel=1e-14)
+    assert fl == pytest.approx(2.0 ** -53 * orc.abs_coeff_sum(st) * np.linalg.norm(u) / np.linalg.norm(b),
+                               rel=1e-12)
+
+
+# ----------------------------------------------------------------- solves
+
+@pytest.mark.parametrize("st", STENCILS)
+@pytest.mark.parametrize("Nx,Ny,tol,kind", [(64, 64, 1e-10, "man"), (48, 40, 1e-10, "rnd"),
+                                            (1, 1, 1e-10, "rnd"), (97, 33, 1e-8, "rnd"),
+                                            (48, 40, 1e-15, "rnd")])
+def test_fp64_solve_matches_oracle(cj, torch, st, Nx, Ny, tol, kind):
+    f = workloads.manufactured_rhs(Nx, Ny) if kind == "man" else workloads.smooth_random_rhs(Nx, Ny, 2)
+    ref = orc.solve(st, f, tol)
+    with cj.Plan(Nx, Ny, st, tol) as p:
+        ud = torch.zeros((Ny, Nx), dtype=torch.float64, device="cuda")
+        res = cj.cj_solve(p.handle, dev(torch, f), ud)
+    assert res["sweeps"] == ref["sweeps"] and res["cycles"] == ref["cycles"]
+    assert {0: "converged", 1: "floor"}[res["status"]] == ref["status"]
+    np.testing.assert_array_equal(ud.cpu().numpy(), ref["u"])
+    assert res["rel_res_l2"] == pytest.approx(ref["rel_l2"], rel=1e-10)
+
+
+def test_fp64_solve_warm_start(cj, torch):
+    Nx, Ny, st = 70, 50, 9
+    f = workloads.smooth_random_rhs(Nx, Ny, 4)
+    u0 = np.random.default_rng(1).standard_normal((Ny, Nx)) * 1e-3
+    ref = orc.solve(st, f, 1e-9, u0=u0)
+    with cj.Plan(Nx, Ny, st, 1e-9) as p:
+        ud = dev(torch, u0)
+        res = cj.cj_solve(p.handle, dev(torch, f), ud)
+    assert res["sweeps"] == ref["sweeps"]
+    np.testing.assert_array_equal(ud.cpu().numpy(), ref["u"])
+
+
+def test_fp64_solve_host_arrays(cj, torch):
+    Nx, Ny, st = 64, 64, 5
+    f = workloads.manufactured_rhs(Nx, Ny)
+    ref = orc.solve(st, f, 1e-10)
+    with cj.Plan(Nx, Ny, st, 1e-10) as p:
+        u = np.zeros((Ny, Nx))
+        res = cj.cj_solve_host(p.handle, np.ascontiguousarray(f), u)
+    assert res["rc"] == cj.CJ_OK and res["sweeps"] == ref["sweeps"]
+    np.testing.assert_array_equal(u, ref["u"])
+
+
+def test_zero_rhs(cj, torch):
+    with cj.Plan(9, 7, 17, 1e-10) as p:
+        ud = torch.zeros((7, 9), dtype=torch.float64, device="cuda")
+        res = cj.cj_solve(p.handle, torch.zeros_like(ud), ud)
+    assert res["rc"] == cj.CJ_OK and res["sweeps"] == 0 and float(ud.abs().max()) == 0.0
+
+
+def test_sweep_budget_exhausted(cj, torch):
+    Nx, Ny = 40, 40
+    f = workloads.smooth_random_rhs(Nx, Ny, 1)
+    with cj.Plan(Nx, Ny, 5, 1e-10, max_sweeps=10) as p:
+        ud = torch.zeros((Ny, Nx), dtype=torch.float64, device="cuda")
+        res = cj.cj_solve(p.handle, dev(torch, f), ud)
+    assert res["rc"] == cj.CJ_ERR_NOT_CONVERGED and res["sweeps"] == 0
+
+
+@pytest.mark.parametrize("st", STENCILS)
+@pytest.mark.parametrize("Nx,Ny,M_in", [(48, 40, 64), (130, 70, 128), (1, 1, 1)])
+def test_mixed_solve_matches_oracle(cj, torch, st, Nx, Ny, M_in):
+    f = workloads.smooth_random_rhs(Nx, Ny, 6)
+    ref = orc.solve_mixed(st, f, 1e-10, M_in)
+    with cj.Plan(Nx, Ny, st, 1e-10, precision=cj.CJ_FP32_INNER, inner_cycle=M_in) as p:
+        ud = torch.zeros((Ny, Nx), dtype=torch.float64, device="cuda")
+        res = cj.cj_solve(p.handle, dev(torch, f), ud)
+    assert res["sweeps"] == ref["sweeps"] and res["cycles"] == ref["outer"]
+    np.testing.assert_array_equal(ud.cpu().numpy(), ref["u"])
+
+
+def test_mixed_solve_auto_inner_cycle_reaches_fp64_solution(cj, torch):
+    Nx, Ny, st = 256, 200, 9
+    f = workloads.smooth_random_rhs(Nx, Ny, 8)
+    with cj.Plan(Nx, Ny, st, 1e-10) as p:
+        u64 = torch.zeros((Ny, Nx), dtype=torch.float64, device="cuda")
+        r64 = cj.cj_solve(p.handle, dev(torch, f), u64)
+    with cj.Plan(Nx, Ny, st, 1e-10, precision=cj.CJ_FP32_INNER) as p:
+        um = torch.zeros((Ny, Nx), dtype=torch.float64, device="cuda")
+        rm = cj.cj_solve(p.handle, dev(torch, f), um)
+    assert r64["rc"] == cj.CJ_OK and rm["rc"] == cj.CJ_OK
+    err = float(torch.linalg.norm(um - u64) / torch.linalg.norm(u64))
+    assert err < 1e-9
+
+
+# ----------------------------------------------------------------- full-size cases
+
+@pytest.mark.parametrize("st,N", [(9, 4096), (17, 8192)])
+def test_full_size_sweeps_bit_exact(cj, torch, st, N):
+    """Two sweeps of the 4096^2 (9-point) and 8192^2 (17-point) problems in the launch
+    configuration the solver uses, against the oracle on the whole grid."""
+    f = workloads.smooth_random_rhs(N, N, 1)
+    u0 = np.zeros((N, N))
+    with cj.Plan(N, N, st, 1e-10) as p:
+        w = p.info()["w"]
+        fd, ud = dev(torch, f), dev(torch, u0)
+        cj.cj_sweeps(p.handle, fd, ud, 0, 2)
+        got = ud.cpu().numpy()
+    b = orc.scale_rhs(f)
+    ref = orc.sweep(st, orc.sweep(st, u0, b, w[0]), b, w[1])
+    np.testing.assert_array_equal(got, ref)
+
+
+def test_full_size_residual(cj, torch):
+    N, st = 4096, 9
+    f = workloads.smooth_random_rhs(N, N, 1)
+    u = np.random.default_rng(2).standard_normal((N, N)) * 1e-4
+    with cj.Plan(N, N, st, 1e-10) as p:
+        l2, linf, _ = cj.cj_residual(p.handle, dev(torch, f), dev(torch, u))
+    b = orc.scale_rhs(f)
+    s, m = orc.residual(st, u, b)
+    assert l2 == pytest.approx(np.sqrt(s) / np.linalg.norm(b), rel=1e-12)
+    assert linf == pytest.approx(m / np.abs(b).max(), rel=1e-14)
+
+
+# ----------------------------------------------------------------- double-FP64 outer form
+
+@pytest.mark.parametrize("st", STENCILS)
+@pytest.mark.parametrize("Nx,Ny,M_in,tol", [(48, 40, 64, 1e-12), (130, 70, 128, 1e-10), (1, 1, 1, 1e-10)])
+def test_mixed_dd_solve_matches_oracle(cj, torch, st, Nx, Ny, M_in, tol):
+    f = workloads.smooth_random_rhs(Nx, Ny, 12)
+    ref = orc.solve_mixed_dd(st, f, tol, M_in)
+    with cj.Plan(Nx, Ny, st, tol, precision=cj.CJ_FP32_INNER_DD, inner_cycle=M_in) as p:
+        ud = torch.zeros((Ny, Nx), dtype=torch.float64, device="cuda")
+        res = cj.cj_solve(p.handle, dev(torch, f), ud)
+        lo = torch.empty_like(ud)
+        cj.cj_solution_lo(p.handle, lo)
+    assert res["sweeps"] == ref["sweeps"] and res["cycles"] == ref["outer"]
+    np.testing.assert_array_equal(ud.cpu().numpy(), ref["u"])
+    np.testing.assert_array_equal(lo.cpu().numpy(), ref["u_lo"])
+    assert res["rel_res_l2"] == pytest.approx(ref["rel_l2"], rel=1e-10)
+
+
+@pytest.mark.parametrize("st", STENCILS)
+def test_mixed_dd_goes_below_fp64_floor(cj, torch, st):
+    N, tol = 160, 1e-13
+    f = workloads.smooth_random_rhs(N, N, seed=4, kmax=40)
+    with cj.Plan(N, N, st, tol, precision=cj.CJ_FP32_INNER, inner_cycle=512) as p:
+        ud = torch.zeros((N, N), dtype=torch.float64, device="cuda")
+        r32 = cj.cj_solve(p.handle, dev(torch, f), ud)
+    with cj.Plan(N, N, st, tol, precision=cj.CJ_FP32_INNER_DD, inner_cycle=512) as p:
+        ud = torch.zeros((N, N), dtype=torch.float64, device="cuda")
+        rdd = cj.cj_solve(p.handle, dev(torch, f), ud)
+    assert r32["rc"] == cj.CJ_FLOOR and r32["rel_res_l2"] > tol
+    assert rdd["rc"] == cj.CJ_OK and rdd["rel_res_l2"] <= tol
+
+
+def test_solution_lo_rejected_for_fp64_plans(cj, torch):
+    with cj.Plan(8, 8, 5, 1e-8) as p:
+        with pytest.raises(cj.CJError):
+            cj.cj_solution_lo(p.handle, torch.zeros((8, 8), dtype=torch.float64, device="cuda"))

@@ -461,3 +461,94 @@ def test_mixed_precision_reaches_fp64_solution(st):
     assert out["converged"] and out["rel_l2"] <= 1e-10 and out["outer"] > 1
     err = np.linalg.norm(out["u"] - ref["u"]) / np.linalg.norm(ref["u"])
     assert err < 1e-9
+
+
+# ----------------------------------------------------------------- double-FP64 outer form
+
+def _exact_residual(st, uh, ul, b):
+    """L (uh + ul) - b in exact rational arithmetic, from the printed coefficients and the
+    Dirichlet / odd-reflection boundary."""
+    Ny, Nx = uh.shape
+    coef = {k: Fraction(v).limit_denominator(1000) for k, v in COEF[st].items()}
+
+    def val(i, j):  # node (i, j), 1-based, with ghosts
+        s = 1
+        if i in (0, Nx + 1) or j in (0, Ny + 1):
+            return Fraction(0)
+        if i == -1:
+            i, s = 1, -s
+        elif i == Nx + 2:
+            i, s = Nx, -s
+        if j == -1:
+            j, s = 1, -s
+        elif j == Ny + 2:
+            j, s = Ny, -s
+        return s * (Fraction(float(uh[j - 1, i - 1])) + Fraction(float(ul[j - 1, i - 1])))
+
+    R = [[None] * Nx for _ in range(Ny)]
+    for j in range(1, Ny + 1):
+        for i in range(1, Nx + 1):
+            R[j - 1][i - 1] = sum(c * val(i + dx, j + dy) for (dx, dy), c in coef.items()) \
+                - Fraction(float(b[j - 1, i - 1]))
+    return R
+
+
+@pytest.mark.parametrize("st", STENCILS)
+def test_double_fp64_residual_exact(st):
+    """The double-FP64 residual equals the exact rational residual to FP64 rounding of the
+    result, even when it is 1e-12 of the terms that cancel in it."""
+    Nx, Ny = 9, 7
+    rng = np.random.default_rng(30 + st)
+    uh = rng.standard_normal((Ny, Nx))
+    ul = uh * rng.uniform(-1e-16, 1e-16, (Ny, Nx))
+    # b = L(uh + ul) + tiny perturbation, rounded: the residual is tiny relative to the terms
+    Rx = _exact_residual(st, uh, ul, np.zeros_like(uh))
+    b = np.array([[float(Rx[j][i]) for i in range(Nx)] for j in range(Ny)])
+    b = b + 1e-12 * rng.standard_normal((Ny, Nx)) * np.abs(b)
+    ex = _exact_residual(st, uh, ul, b)
+    got = orc.residual_dd(st, uh, ul, b)
+    for j in range(Ny):
+        for i in range(Nx):
+            e = ex[j][i]
+            assert abs(Fraction(float(got[j, i])) - e) <= abs(e) * Fraction(1, 2 ** 51) + Fraction(1, 10 ** 300)
+    # the plain FP64 residual of the same data is far off (that is what the form is for)
+    plain = orc.apply_L(st, uh) + orc.apply_L(st, ul) - b
+    rel = max(abs(float(plain[j, i]) - float(ex[j][i])) / abs(float(ex[j][i]))
+              for j in range(Ny) for i in range(Nx))
+    assert rel > 1e-8
+
+
+def _longdouble_residual(st, uh, ul, b):
+    """||L (uh + ul) - b||_2 in numpy long double (64-bit mantissa on x86) from the printed
+    coefficients; a check of the double-FP64 claims independent of the oracle's code."""
+    LD = np.longdouble
+    Ny, Nx = uh.shape
+    u = uh.astype(LD) + ul.astype(LD)
+    g = np.zeros((Ny + 4, Nx + 4), dtype=LD)
+    g[2:-2, 2:-2] = u
+    g[0, 2:-2] = -u[1 - 1]      # j = -1 mirrors j = 1
+    g[-1, 2:-2] = -u[Ny - 1]    # j = Ny+2 mirrors j = Ny
+    g[:, 0] = -g[:, 2]          # i = -1 mirrors i = 1 (corners pick up the second sign)
+    g[:, -1] = -g[:, -3]        # i = Nx+2 mirrors i = Nx
+    R = -b.astype(LD)
+    for (dx, dy), c in COEF[st].items():
+        fr = Fraction(c).limit_denominator(1000)
+        R = R + (LD(fr.numerator) / LD(fr.denominator)) * g[2 + dy:2 + dy + Ny, 2 + dx:2 + dx + Nx]
+    return float(np.sqrt(np.sum(R * R)))
+
+
+@pytest.mark.parametrize("st", STENCILS)
+def test_double_fp64_outer_goes_below_the_fp64_floor(st):
+    if np.finfo(np.longdouble).nmant < 63:
+        pytest.skip("needs an extended long double for the independent check")
+    N, tol = 160, 1e-13
+    f = workloads.smooth_random_rhs(N, N, seed=4, kmax=40)
+    b = orc.scale_rhs(f)
+    fp = orc.solve_mixed(st, f, tol, M_in=512)
+    dd = orc.solve_mixed_dd(st, f, tol, M_in=512)
+    assert fp["status"] == "floor" and fp["rel_l2"] > tol
+    assert dd["converged"] and dd["rel_l2"] <= tol
+    rho = _longdouble_residual(st, dd["u"], dd["u_lo"], b) / np.linalg.norm(b)
+    assert rho <= 1.5 * tol
+    # and the FP64 solution agrees with the double-FP64 one to FP64 accuracy
+    assert np.abs(fp["u"] - dd["u"]).max() <= 1e-9 * np.abs(dd["u"]).max()
