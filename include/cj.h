@@ -187,6 +187,30 @@ cj_status cj_residual(cj_plan *plan, const double *f, long long ld_f, const doub
                       long long ld_u, void *stream, double *rel_l2, double *rel_inf,
                       double *floor_est);
 
+/*
+ * cj_residual_noalloc -- the relative residual norms of cj_residual, for callers that
+ * cannot allocate device memory: for example code running under a framework whose caching
+ * allocator has already reserved the device (a cudaMalloc of its own would fail or carve
+ * up that pool), or a latency-critical loop that must not take the device-wide
+ * synchronisation cudaMalloc / cudaFree can cause.  It needs no plan and calls no
+ * cudaMalloc, cudaFree or allocating library routine.  (The paper has no counterpart: it
+ * is a deployment variant of the stop test's residual.)
+ *   Nx, Ny >= 1, st in {5, 9, 17}; f, u: device, Ny x ld_f / Ny x ld_u doubles (f unscaled,
+ *   as for cj_solve); out: device, 3 doubles, receives (rel_l2, rel_inf, floor_est) as in
+ *   cj_residual.  Asynchronous on `stream`: out is valid once the stream reaches the call.
+ * Scratch: a fixed 640 KiB array in the library's device memory, one slot per block of
+ * 128 x 64 nodes, 16384 slots; grids needing more slots (more than 134,217,728 nodes) are
+ * rejected with CJ_ERR_INVALID_ARG and a message in cj_last_error().  Every GPU that loads
+ * the library holds that array until the process exits.  The first call made on a device
+ * looks up the array's device address (cudaGetSymbolAddress) with that device current;
+ * make that first call before any stream capture.  All calls share the one array, so
+ * calls that may overlap on the GPU (different streams, no ordering between them) race
+ * and must not be issued; calls on one stream are ordered and safe.  Each call writes
+ * every slot it later reads, so nothing needs clearing between calls.
+ */
+cj_status cj_residual_noalloc(int Nx, int Ny, cj_stencil st, const double *f, long long ld_f,
+                              const double *u, long long ld_u, double *out, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

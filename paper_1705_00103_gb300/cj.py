@@ -92,6 +92,9 @@ def _lib():
         L.cj_sweeps_f32.restype = ctypes.c_int
         L.cj_solution_lo.argtypes = [_vp, _vp, _ll, _vp]
         L.cj_solution_lo.restype = ctypes.c_int
+        L.cj_residual_noalloc.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, _vp, _ll, _vp,
+                                          _ll, _vp, _vp]
+        L.cj_residual_noalloc.restype = ctypes.c_int
         L.cj_residual.argtypes = [_vp, _vp, _ll, _vp, _ll, _vp, _dp, _dp, _dp]
         L.cj_residual.restype = ctypes.c_int
         _L = L
@@ -225,6 +228,18 @@ def cj_residual(plan, f, u, stream=None):
     if rc != CJ_OK:
         raise CJError(rc, "cj_residual")
     return a.value, b.value, c.value
+
+
+def cj_residual_noalloc(Nx: int, Ny: int, st: int, f, u, out, stream=None) -> None:
+    """Allocation-free residual norms: writes (rel_l2, rel_inf, floor_est) into the device
+    tensor ``out`` (3 float64) on the stream; no plan, no device allocation."""
+    fp, ldf = _grid(f, "float64")
+    up, ldu = _grid(u, "float64")
+    if not (out.is_cuda and str(out.dtype) == "torch.float64" and out.numel() >= 3 and out.is_contiguous()):
+        raise ValueError("out must be a contiguous CUDA float64 tensor of >= 3 elements")
+    rc = _lib().cj_residual_noalloc(Nx, Ny, st, fp, ldf, up, ldu, out.data_ptr(), _stream(stream))
+    if rc != CJ_OK:
+        raise CJError(rc, "cj_residual_noalloc")
 
 
 class Plan:
