@@ -65,8 +65,9 @@ typedef struct {
     int precision;          /* cj_precision (default CJ_FP64) */
     int literal_n;          /* 1: use the paper-literal N = Nx in the kappa formulas instead
                                of the exact N = Nx + 1 (ablation only) */
-    int inner_cycle;        /* CJ_FP32_INNER: inner cycle length (a power of two); 0 = auto */
-    int reserved0;
+    int inner_cycle;        /* FP32-inner modes: inner cycle length (a power of two); 0 = auto */
+    int temporal_depth;     /* FP32-inner modes: sweeps fused per HBM round trip (temporal
+                               blocking), 1..8; 0 = auto (1) */
     long long max_sweeps;   /* sweep budget of one solve; 0 = 64 cycles */
 } cj_options;
 
@@ -164,7 +165,8 @@ cj_status cj_sweeps(cj_plan *plan, const double *f, long long ld_f, double *u, l
 
 /*
  * cj_sweeps_f32 -- apply `count` weighted FP32 sweeps e <- e + w32_n (L e - r) in place,
- * w32_n = (float) w_n of the plan's inner cycle (CJ_FP32_INNER plans only).
+ * w32_n = (float) w_n of the plan's inner cycle (FP32-inner plans only), fused
+ * temporal_depth at a time per launch as the solve does (bit-identical to one at a time).
  * r, e: device, Ny x ld floats.  Asynchronous on `stream`.
  */
 cj_status cj_sweeps_f32(cj_plan *plan, const float *r, long long ld_r, float *e, long long ld_e,

@@ -25,7 +25,7 @@ CJ_FP64, CJ_FP32_INNER, CJ_FP32_INNER_DD = 0, 1, 2
 
 class cj_options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("literal_n", ctypes.c_int),
-                ("inner_cycle", ctypes.c_int), ("reserved0", ctypes.c_int),
+                ("inner_cycle", ctypes.c_int), ("temporal_depth", ctypes.c_int),
                 ("max_sweeps", ctypes.c_longlong)]
 
 
@@ -123,9 +123,9 @@ def _grid(t, dtype_name: str):
 
 def cj_plan_create(Nx: int, Ny: int, st: int, tol: float, precision: int = CJ_FP64,
                    literal_n: int = 0, inner_cycle: int = 0, max_sweeps: int = 0,
-                   bc: int = CJ_BC_DIRICHLET0):
+                   bc: int = CJ_BC_DIRICHLET0, temporal_depth: int = 0):
     """Returns a plan handle (int); free it with cj_plan_destroy."""
-    opt = cj_options(precision, literal_n, inner_cycle, 0, max_sweeps)
+    opt = cj_options(precision, literal_n, inner_cycle, temporal_depth, max_sweeps)
     h = _vp()
     rc = _lib().cj_plan_create(Nx, Ny, st, bc, tol, ctypes.byref(opt), ctypes.byref(h))
     if rc != CJ_OK:

@@ -30,6 +30,8 @@ Grid make_grid(int Nx, int Ny, int elem_bytes);
 // Launch shape of the y-marching kernels: blocks of kBX threads, one column each, every
 // block walks `ty` consecutive rows.
 constexpr int kBX = 128;
+// Deepest temporal blocking of the FP32 inner sweep (sweeps per HBM round trip).
+constexpr int kTbMaxDepth = 8;
 struct March {
     int nbx, nby, ty;
     int blocks() const { return nbx * nby; }
@@ -39,6 +41,7 @@ struct cj_plan {
     int Nx, Ny, st, r, precision, literal_n;
     double tol, kmin, kmax, c, S, h2;
     long long M, M_in, max_sweeps;
+    int depth = 1;            // FP32 sweeps per launch (temporal blocking depth)
     std::vector<double> w;    // sweep coefficients w_n = omega_n / c, application order
     std::vector<float> w32;   // FP32 inner cycle coefficients
     int device;
@@ -90,6 +93,9 @@ cudaError_t launch_defect_dd(const cj_plan *p, const double *uh, const double *u
                              float *e_zero, cudaStream_t s);
 cudaError_t launch_correct_dd(const cj_plan *p, double *uh, double *ul, const float *e,
                               cudaStream_t s);
+// temporal-blocked FP32 sweeps (tblock.cu): `depth` sweeps with weights w[0..depth-1]
+cudaError_t launch_sweep32_tb(const cj_plan *p, const float *e, const float *r, float *out,
+                              const float *w, int depth, cudaStream_t s);
 cudaError_t launch_import32(const cj_plan *p, const float *src, long long ld, float *dst_pad,
                             cudaStream_t s);
 cudaError_t launch_export32(const cj_plan *p, const float *src_pad, float *dst, long long ld,

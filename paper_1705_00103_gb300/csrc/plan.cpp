@@ -64,17 +64,33 @@ long long plan_cycle_length(double kmin, double kmax, double tol) {
     return m;
 }
 
-// Inner FP32 cycle length of the mixed-precision solve: the power of two nearest above
-// 7 / acosh(sigma), so that one inner cycle cuts the residual by about 2 e^-7 ~ 1e-3, at
-// most 8192 (beyond that the FP32 rounding amplified by the weight order, ~1e5 x 6e-8,
-// stops being small) and at most the FP64 cycle length M.
+// Inner FP32 cycle length of the mixed-precision solve.  One outer step multiplies the
+// error by about q(M) = max(2 exp(-M theta), eps32 G(M)): the Chebyshev factor of an M-sweep
+// cycle (theta = acosh sigma) or the FP32 rounding amplified by the partial products of the
+// mirror-pairing order, G(M) ~ 10^(2.6 + 0.62 log2(M / 512)) (measured growth: 10^2.6 at
+// M = 512, 10^5.1 at 8192, 10^6.9 at 65536).  The rule takes the power of two that
+// minimises sweeps per decade, M / log10(1/q(M)), and at most the FP64 cycle length M.
+// On the 9-point 4096^2 problem it gives 4096, the measured best (53k FP32 sweeps to
+// 1e-10 against 131k at 8192 and 51k-55k at 2048).
 long long plan_inner_cycle(double kmin, double kmax, long long M) {
-    double d = 2.0 * kmin / (kmax - kmin);
-    double a = std::log1p(d + std::sqrt(d * (2.0 + d)));
-    double want = std::ceil(7.0 / a);
-    long long m = 1;
-    while ((double)m < want && m < 8192) m *= 2;
-    return m < M ? m : M;
+    const double d = 2.0 * kmin / (kmax - kmin);
+    const double theta = std::log1p(d + std::sqrt(d * (2.0 + d)));
+    const double eps32 = 5.9604644775390625e-08;  // 2^-24
+    long long best = 1;
+    double best_cost = 1e300;
+    for (long long m = 2; m <= 65536 && m <= M; m *= 2) {
+        const double cheb = 2.0 * std::exp(-(double)m * theta);
+        const double growth = std::pow(10.0, 2.6 + 0.62 * std::log2((double)m / 512.0));
+        const double q = std::fmax(cheb, eps32 * growth);
+        if (q >= 0.5) continue;
+        const double cost = (double)m / std::log10(1.0 / q);
+        if (cost < best_cost) {
+            best_cost = cost;
+            best = m;
+        }
+    }
+    if (best_cost == 1e300) best = M < 2 ? M : 2;
+    return best;
 }
 
 // Per-sweep coefficients w_n = 1 / (c * lambda_{o(n)}), lambda_j = (kmax+kmin)/2 +

@@ -158,6 +158,31 @@ cj_status run_fp64(cj_plan *p, cudaStream_t s, double **cur_out, cj_result *res,
     return (cj_status)stat;
 }
 
+// One inner cycle of FP32 sweeps with weights w32[first .. first+count-1], `depth` per
+// launch; *cur holds the input on entry and the result on exit (ping-pong with *nxt).
+cudaError_t fp32_sweeps(cj_plan *p, float **cur, float **nxt, const float *r, long long first,
+                        long long count, cudaStream_t s, long long *launches) {
+    long long n = 0;
+    while (n < count) {
+        const long long k = p->depth < count - n ? p->depth : count - n;
+        cudaError_t e;
+        if (k == 1) {
+            e = launch_sweep32(p, *cur, r, *nxt, p->w32[(first + n) % p->M_in], s);
+        } else {
+            float w[kTbMaxDepth];
+            for (long long q = 0; q < k; ++q) w[q] = p->w32[(first + n + q) % p->M_in];
+            e = launch_sweep32_tb(p, *cur, r, *nxt, w, (int)k, s);
+        }
+        if (e != cudaSuccess) return e;
+        float *t = *cur;
+        *cur = *nxt;
+        *nxt = t;
+        n += k;
+        ++*launches;
+    }
+    return cudaSuccess;
+}
+
 // Mixed precision: FP64 defect r = b - L u -> FP32 rt; one FP32 CJM cycle of length M_in
 // on L e = rt from e = 0; u += e in FP64; repeat until the FP64 stop rule ends it.
 cj_status run_mixed(cj_plan *p, cudaStream_t s, double **cur_out, cj_result *res, History *h) {
@@ -182,16 +207,11 @@ cj_status run_mixed(cj_plan *p, cudaStream_t s, double **cur_out, cj_result *res
         }
         float *cur = p->e0, *nxt = p->e1;
         CJ_TRY(cudaEventRecord(p->ev0, s), "event");
-        for (long long k = 0; k < p->M_in; ++k) {
-            CJ_TRY(launch_sweep32(p, cur, p->rt, nxt, p->w32[k], s), "sweep32");
-            float *t = cur;
-            cur = nxt;
-            nxt = t;
-        }
+        CJ_TRY(fp32_sweeps(p, &cur, &nxt, p->rt, 0, p->M_in, s, &res->launches), "sweep32");
         CJ_TRY(cudaEventRecord(p->ev1, s), "event");
         timed = true;
         CJ_TRY(launch_correct(p, p->u0, cur, s), "correct");
-        res->launches += p->M_in + 1;
+        res->launches += 1;
         sweeps += p->M_in;
         outer += 1;
         prev = n.l2;
@@ -233,16 +253,11 @@ cj_status run_mixed_dd(cj_plan *p, cudaStream_t s, double **cur_out, cj_result *
         }
         float *cur = p->e0, *nxt = p->e1;
         CJ_TRY(cudaEventRecord(p->ev0, s), "event");
-        for (long long k = 0; k < p->M_in; ++k) {
-            CJ_TRY(launch_sweep32(p, cur, p->rt, nxt, p->w32[k], s), "sweep32");
-            float *t = cur;
-            cur = nxt;
-            nxt = t;
-        }
+        CJ_TRY(fp32_sweeps(p, &cur, &nxt, p->rt, 0, p->M_in, s, &res->launches), "sweep32");
         CJ_TRY(cudaEventRecord(p->ev1, s), "event");
         timed = true;
         CJ_TRY(launch_correct_dd(p, p->u0, p->u1, cur, s), "correct dd");
-        res->launches += p->M_in + 1;
+        res->launches += 1;
         sweeps += p->M_in;
         outer += 1;
         prev = n.l2;
@@ -319,6 +334,7 @@ cj_status cj_plan_create(int Nx, int Ny, cj_stencil st, cj_bc bc, double tol,
         return CJ_ERR_INVALID_ARG;
     if (o.inner_cycle != 0 && !is_pow2(o.inner_cycle)) return CJ_ERR_INVALID_ARG;
     if (o.max_sweeps < 0) return CJ_ERR_INVALID_ARG;
+    if (o.temporal_depth < 0 || o.temporal_depth > kTbMaxDepth) return CJ_ERR_INVALID_ARG;
 
     cj_plan *p = new (std::nothrow) cj_plan();
     if (!p) return CJ_ERR_NOMEM;
@@ -354,6 +370,8 @@ cj_status cj_plan_create(int Nx, int Ny, cj_stencil st, cj_bc bc, double tol,
             p->w32.resize(p->M_in);
             for (long long k = 0; k < p->M_in; ++k) p->w32[k] = (float)wi[k];
         }
+        // temporal blocking is opt-in until its kernel beats the one-sweep kernel
+        p->depth = o.temporal_depth ? o.temporal_depth : 1;
         long long unit = p->precision != CJ_FP64 ? p->M_in : p->M;
         p->max_sweeps = o.max_sweeps ? o.max_sweeps : 64 * unit;
     } catch (...) {
@@ -481,12 +499,8 @@ cj_status cj_sweeps_f32(cj_plan *p, const float *r, long long ldr, float *e, lon
     CJ_TRY(launch_import32(p, r, ldr, p->rt, s), "import32 r");
     CJ_TRY(launch_import32(p, e, lde, p->e0, s), "import32 e");
     float *cur = p->e0, *nxt = p->e1;
-    for (long long k = 0; k < count; ++k) {
-        CJ_TRY(launch_sweep32(p, cur, p->rt, nxt, p->w32[(first + k) % p->M_in], s), "sweep32");
-        float *t = cur;
-        cur = nxt;
-        nxt = t;
-    }
+    long long launches = 0;
+    CJ_TRY(fp32_sweeps(p, &cur, &nxt, p->rt, first, count, s, &launches), "sweep32");
     CJ_TRY(launch_export32(p, cur, e, lde, s), "export32");
     return CJ_OK;
 }

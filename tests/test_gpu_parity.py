@@ -302,3 +302,40 @@ def test_solution_lo_rejected_for_fp64_plans(cj, torch):
     with cj.Plan(8, 8, 5, 1e-8) as p:
         with pytest.raises(cj.CJError):
             cj.cj_solution_lo(p.handle, torch.zeros((8, 8), dtype=torch.float64, device="cuda"))
+
+
+# ----------------------------------------------------------------- temporal blocking
+
+@pytest.mark.parametrize("st", STENCILS)
+@pytest.mark.parametrize("depth", [2, 3, 4, 8])
+@pytest.mark.parametrize("Nx,Ny", [(1, 1), (5, 3), (2, 40), (130, 70), (257, 33), (300, 97)])
+def test_fp32_temporal_blocking_bit_exact(cj, torch, st, depth, Nx, Ny):
+    """depth sweeps per launch equal one sweep per launch bit for bit, over counts that are
+    not multiples of the depth and tiles cut by the grid's edges."""
+    rng = np.random.default_rng(7 * Nx + Ny + st + depth)
+    r = rng.standard_normal((Ny, Nx)).astype(np.float32)
+    e = rng.standard_normal((Ny, Nx)).astype(np.float32)
+    count = 2 * depth + 1
+    with cj.Plan(Nx, Ny, st, 1e-8, precision=cj.CJ_FP32_INNER, inner_cycle=32,
+                 temporal_depth=depth) as p:
+        kmin, kmax = orc.kappa_bounds(st, Nx, Ny)
+        w32 = orc.sweep_coeffs(st, kmin, kmax, 32).astype(np.float32)
+        rd, ed = dev(torch, r), dev(torch, e)
+        cj.cj_sweeps_f32(p.handle, rd, ed, 3, count)
+    ref = e.copy()
+    for k in range(count):
+        ref = orc.sweep_f32(st, ref, r, w32[(3 + k) % 32])
+    np.testing.assert_array_equal(ed.cpu().numpy(), ref)
+
+
+@pytest.mark.parametrize("st", STENCILS)
+def test_mixed_solve_with_temporal_blocking_matches_oracle(cj, torch, st):
+    Nx, Ny, M_in = 200, 150, 128
+    f = workloads.smooth_random_rhs(Nx, Ny, 13)
+    ref = orc.solve_mixed_dd(st, f, 1e-11, M_in)
+    with cj.Plan(Nx, Ny, st, 1e-11, precision=cj.CJ_FP32_INNER_DD, inner_cycle=M_in,
+                 temporal_depth=4) as p:
+        ud = torch.zeros((Ny, Nx), dtype=torch.float64, device="cuda")
+        res = cj.cj_solve(p.handle, dev(torch, f), ud)
+    assert res["sweeps"] == ref["sweeps"] and res["cycles"] == ref["outer"]
+    np.testing.assert_array_equal(ud.cpu().numpy(), ref["u"])
