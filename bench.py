@@ -57,6 +57,11 @@ def parse_args(argv=None):
     ap.add_argument("--impl", default="cj", choices=["cj", "reference"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-mixed", action="store_true")
+    ap.add_argument("--workload", default="solve", choices=["solve", "batch", "serve"],
+                    help="solve: the plain FP64 9-point 4096^2 solve (default); batch: the 512-problem "
+                         "batched workload; serve: a bounded sample of the request stream")
+    ap.add_argument("--serve-requests", type=int, default=48)
     return ap.parse_args(argv)
 
 
@@ -268,6 +273,9 @@ def run_cj(args):
                "h2d_bytes_per_step": 2 * N_GRID * N_GRID * 8, "d2h_bytes_per_step": N_GRID * N_GRID * 8,
                "api": "cj_solve_host"}
 
+    mixed = None
+    if not args.no_mixed:
+        mixed = mixed_paths(cj, rhs_dev[1], stream, results[1])
     launches = sum(r["launches"] for r in results)
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -283,6 +291,7 @@ def run_cj(args):
                     "rel_res_l2": r["rel_res_l2"], "floor_est": r["floor_est"],
                     "time_s": r["seconds"]} for r in results[:2]],
         "roofline": roofline, "clocks": clk, "gpu_launches": launches, "e2e": e2e,
+        "vs_plain_fp64": mixed,
     }
     if rank == 0 and not args.no_cpu:
         out["cpu_baseline"] = cpu_oracle_sample()
@@ -291,6 +300,124 @@ def run_cj(args):
         print(json.dumps(out), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+def mixed_paths(cj, f, stream, plain):
+    """The same smooth-RHS problem by the FP32-inner paths (FP64 and double-FP64 outer
+    steps), each solved once after the timed region: time to stop, residual reached, and
+    the speed-up over the plain FP64 solve's time (which stops at its rounding floor)."""
+    import torch
+    out = {"plain_fp64": {"time_s": plain["seconds"], "rel_res_l2": plain["rel_res_l2"],
+                          "status": cj.cj_status_string(plain["rc"]), "sweeps": plain["sweeps"]}}
+    for name, prec in (("fp32_inner_fp64_outer", cj.CJ_FP32_INNER), ("fp32_inner_dd_outer", cj.CJ_FP32_INNER_DD)):
+        with cj.Plan(N_GRID, N_GRID, STENCIL, TOL, precision=prec) as p:
+            u = torch.zeros((N_GRID, N_GRID), dtype=torch.float64, device="cuda")
+            r = cj.cj_solve(p.handle, f, u, stream)
+            M_in = p.info()["M_inner"]
+        out[name] = {"time_s": r["seconds"], "rel_res_l2": r["rel_res_l2"], "status": cj.cj_status_string(r["rc"]),
+                     "fp32_sweeps": r["sweeps"], "outer_steps": r["cycles"], "inner_cycle": M_in,
+                     "fp32_gupdates_s": N_GRID * N_GRID * r["sweeps"] / r["sweep_seconds"] / 1e9,
+                     "speedup_vs_plain_fp64_time": plain["seconds"] / r["seconds"]}
+    return out
+
+
+def run_batch(args):
+    """The batched workload (512 problems, sides log-uniform in [64, 2048], 5/9-point,
+    tol 1e-8, FP32-inner / FP64-outer) through cj_solve_batch; each step one batch."""
+    import torch
+
+    import paper_1705_00103_gb300 as cj
+    import workloads
+    torch.cuda.set_device(0)
+    cj.build.build()
+    specs = workloads.batch_problems()
+    fs = [torch.from_numpy(workloads.smooth_random_rhs(p["Nx"], p["Ny"], p["rhs_seed"])).cuda() for p in specs]
+    us = [torch.zeros_like(f) for f in fs]
+    probs = [dict(Nx=p["Nx"], Ny=p["Ny"], st=p["st"], tol=p["tol"], precision=cj.CJ_FP32_INNER, f=f, u=u)
+             for p, f, u in zip(specs, fs, us)]
+    stream = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        for u in us:
+            u.zero_()
+        cj.cj_solve_batch(probs, stream)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    clocks = ClockSampler(0)
+    clocks.start()
+    e0.record(stream)
+    res = []
+    for _ in range(args.steps):
+        for u in us:
+            u.zero_()
+        res = cj.cj_solve_batch(probs, stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1)
+    updates = sum(r["sweeps"] * p["Nx"] * p["Ny"] for r, p in zip(res, specs))
+    stat = {}
+    for r in res:
+        k = cj.cj_status_string(r["rc"])
+        stat[k] = stat.get(k, 0) + 1
+    out = {"metric": METRIC, "value": updates * args.steps / (ms * 1e-3) / 1e9, "unit": UNIT, "n_gpus": 1,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
+           "data": "synthetic",
+           "config": {"workload": "batched: 512 Dirichlet problems, Nx, Ny log-uniform in [64, 2048], "
+                                  "5/9-point, tol 1e-8, FP32-inner / FP64-outer, one engine per batch",
+                      "points": sum(p["Nx"] * p["Ny"] for p in specs)},
+           "time_to_all_converged_s": ms / args.steps * 1e-3, "statuses": stat,
+           "max_rel_res_l2": max(r["rel_res_l2"] for r in res), "clocks": clk,
+           "gpu_launches": res[0]["launches"] if res else 0}
+    print(json.dumps(out), flush=True)
+
+
+def run_serve(args):
+    """A bounded sample of the served workload: the first --serve-requests requests of the
+    seeded Poisson stream (lambda = 2000/s, sides log-uniform in [32, 8192], 5/9/17-point,
+    tol 1e-6 or 1e-10) submitted at their arrival times to one server with a 150 GB budget;
+    latency = submit to result ready."""
+    import torch
+
+    import paper_1705_00103_gb300 as cj
+    import workloads
+    torch.cuda.set_device(0)
+    cj.build.build()
+    reqs = workloads.request_stream()[:args.serve_requests]
+    fs = [workloads.smooth_random_rhs(r["Nx"], r["Ny"], r["rhs_seed"]) for r in reqs]
+    lat, svc, upd = [], [], 0
+    clocks = ClockSampler(0)
+    with cj.Server(150 * 10 ** 9, 64) as srv:
+        clocks.start()
+        t0 = time.perf_counter()
+        tickets = {}
+        k = 0
+        while k < len(reqs) or tickets:
+            now = time.perf_counter() - t0
+            while k < len(reqs) and reqs[k]["t_arrival"] <= now:
+                tickets[srv.submit(fs[k], reqs[k]["st"], reqs[k]["tol"])] = k
+                k += 1
+            for t, j in list(tickets.items()):
+                got = srv.poll(t, fs[j].shape)
+                if got is not None:
+                    lat.append(got[1]["seconds"])
+                    upd += got[1]["sweeps"] * reqs[j]["Nx"] * reqs[j]["Ny"]
+                    del tickets[t]
+            time.sleep(0.0005)
+        wall = time.perf_counter() - t0
+        stats = srv.stats()
+    clk = clocks.stop()
+    out = {"metric": METRIC, "value": upd / wall / 1e9, "unit": UNIT, "n_gpus": 1, "steps": 1, "warmup": 0,
+           "ms_per_step": wall * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+           "dtype": "f32+f64", "data": "synthetic",
+           "config": {"workload": "served: first %d requests of the seeded Poisson stream (2000/s), sides "
+                                  "log-uniform in [32, 8192], 5/9/17-point, tol 1e-6 / 1e-10, budget 150 GB"
+                                  % len(reqs)},
+           "latency_s": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
+                         "max": float(max(lat))},
+           "offered_window_s": reqs[-1]["t_arrival"], "wall_s": wall, "server": stats, "clocks": clk}
+    print(json.dumps(out), flush=True)
 
 
 def run_reference(args):
@@ -340,6 +467,10 @@ def main(argv=None):
         raise SystemExit("--warmup must be >= 3")
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "batch":
+        run_batch(args)
+    elif args.workload == "serve":
+        run_serve(args)
     else:
         run_cj(args)
 

@@ -189,6 +189,79 @@ cj_status cj_residual(cj_plan *plan, const double *f, long long ld_f, const doub
                       long long ld_u, void *stream, double *rel_l2, double *rel_inf,
                       double *floor_est);
 
+/* ------------------------------------------------------------------ batched solves */
+
+/* One problem of a batch (device grids, as for cj_solve). */
+typedef struct {
+    int Nx, Ny;
+    cj_stencil st;
+    int precision;          /* CJ_FP32_INNER or CJ_FP32_INNER_DD; 0 = CJ_FP32_INNER unless the
+                               FP64 floor (about 2^-53 S / (c kmin)) is within 4x of tol */
+    double tol;
+    int inner_cycle;        /* 0 = the planner's choice */
+    int temporal_depth;     /* FP32 sweeps per engine step, 1..8; 0 = 1 */
+    long long max_sweeps;   /* 0 = 64 inner cycles */
+    const double *f;        /* device, Ny x ld_f, unscaled right-hand side */
+    long long ld_f;
+    double *u;              /* device, Ny x ld_u: initial guess in, solution out */
+    long long ld_u;
+} cj_problem;
+
+/*
+ * cj_solve_batch -- solve n independent problems (any sizes, stencils, tolerances) together
+ * with the mixed-precision CJM: FP32 inner cycles inside FP64 or double-FP64 defect
+ * correction, every problem's residual test and stop rule evaluated on the device.  The
+ * problems run as slots of one engine whose step (correct, defect, decide, sweep, export,
+ * advance: six launches over persistent grids that read a device tile list) is captured
+ * once in a CUDA graph and replayed until every slot has finished; a problem's arithmetic
+ * does not depend on its batch-mates.  results[k] receives problem k's outcome (status per
+ * problem; seconds and launches are those of the whole batch).  Orders itself after the
+ * work already on `stream` and makes `stream` wait for it; blocks until done.  Returns
+ * CJ_OK, or CJ_ERR_TIMEOUT if a problem did not finish within its sweep budget's steps.
+ */
+cj_status cj_solve_batch(const cj_problem *problems, int n, void *stream, cj_result *results);
+
+/* ------------------------------------------------------------------ request server */
+
+typedef struct cj_server cj_server;
+
+typedef struct {
+    long long queued, active, admitted, completed, steps, peak_active;
+    size_t bytes_in_use, peak_bytes, budget_bytes;
+} cj_server_stats_t;
+
+/*
+ * cj_server_create -- a request loop with continuous batching on the current device: a
+ * worker thread admits submitted problems, in arrival order, into free engine slots while
+ * their device footprint (FP64 u, b [, u_lo], FP32 e, e', r, weights; 28-36 bytes per
+ * node) fits in hbm_budget_bytes; admitted problems join the running engine between graph
+ * replays and leave it as each one finishes, so requests arriving while others run overlap
+ * with them on the device.
+ */
+cj_status cj_server_create(size_t hbm_budget_bytes, int max_slots, cj_server **out);
+
+/*
+ * cj_submit -- queue one solve: f_host (Ny x Nx, copied before return), tolerance tol; the
+ * precision follows cj_problem.precision = 0.  *ticket identifies it for cj_poll.
+ * CJ_ERR_INVALID_ARG for bad sizes; a problem larger than the whole budget completes with
+ * CJ_ERR_BUDGET.
+ */
+cj_status cj_submit(cj_server *server, int Nx, int Ny, cj_stencil st, double tol, const double *f_host,
+                    uint64_t *ticket);
+
+/*
+ * cj_poll -- CJ_PENDING while the request is queued or running; otherwise its final status,
+ * with the solution copied to u_host (Ny x Nx, may be NULL) and *res filled (res->seconds =
+ * latency from submit to result ready).  A finished ticket can be polled once.
+ */
+cj_status cj_poll(cj_server *server, uint64_t ticket, double *u_host, cj_result *res);
+
+/* Counters of the server (queue, active slots, admitted, completed, engine steps, memory). */
+cj_status cj_server_stats(cj_server *server, cj_server_stats_t *out);
+
+/* Stops the worker (requests still queued or running are dropped) and frees the server. */
+void cj_server_destroy(cj_server *server);
+
 /*
  * cj_residual_noalloc -- the relative residual norms of cj_residual, for callers that
  * cannot allocate device memory: for example code running under a framework whose caching

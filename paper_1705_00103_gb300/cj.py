@@ -39,6 +39,22 @@ class cj_result(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class cj_problem(ctypes.Structure):
+    _fields_ = [("Nx", ctypes.c_int), ("Ny", ctypes.c_int), ("st", ctypes.c_int),
+                ("precision", ctypes.c_int), ("tol", ctypes.c_double),
+                ("inner_cycle", ctypes.c_int), ("temporal_depth", ctypes.c_int),
+                ("max_sweeps", ctypes.c_longlong), ("f", ctypes.c_void_p), ("ld_f", ctypes.c_longlong),
+                ("u", ctypes.c_void_p), ("ld_u", ctypes.c_longlong)]
+
+
+class cj_server_stats_t(ctypes.Structure):
+    _fields_ = [("queued", ctypes.c_longlong), ("active", ctypes.c_longlong),
+                ("admitted", ctypes.c_longlong), ("completed", ctypes.c_longlong),
+                ("steps", ctypes.c_longlong), ("peak_active", ctypes.c_longlong),
+                ("bytes_in_use", ctypes.c_size_t), ("peak_bytes", ctypes.c_size_t),
+                ("budget_bytes", ctypes.c_size_t)]
+
+
 class CJError(RuntimeError):
     def __init__(self, status: int, where: str):
         msg = "%s: %s (%d)" % (where, cj_status_string(status), status)
@@ -95,6 +111,20 @@ def _lib():
         L.cj_residual_noalloc.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, _vp, _ll, _vp,
                                           _ll, _vp, _vp]
         L.cj_residual_noalloc.restype = ctypes.c_int
+        L.cj_solve_batch.argtypes = [ctypes.POINTER(cj_problem), ctypes.c_int, _vp,
+                                     ctypes.POINTER(cj_result)]
+        L.cj_solve_batch.restype = ctypes.c_int
+        L.cj_server_create.argtypes = [ctypes.c_size_t, ctypes.c_int, ctypes.POINTER(_vp)]
+        L.cj_server_create.restype = ctypes.c_int
+        L.cj_submit.argtypes = [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double, _vp,
+                                ctypes.POINTER(ctypes.c_uint64)]
+        L.cj_submit.restype = ctypes.c_int
+        L.cj_poll.argtypes = [_vp, ctypes.c_uint64, _vp, ctypes.POINTER(cj_result)]
+        L.cj_poll.restype = ctypes.c_int
+        L.cj_server_stats.argtypes = [_vp, ctypes.POINTER(cj_server_stats_t)]
+        L.cj_server_stats.restype = ctypes.c_int
+        L.cj_server_destroy.argtypes = [_vp]
+        L.cj_server_destroy.restype = None
         L.cj_residual.argtypes = [_vp, _vp, _ll, _vp, _ll, _vp, _dp, _dp, _dp]
         L.cj_residual.restype = ctypes.c_int
         _L = L
@@ -240,6 +270,79 @@ def cj_residual_noalloc(Nx: int, Ny: int, st: int, f, u, out, stream=None) -> No
     rc = _lib().cj_residual_noalloc(Nx, Ny, st, fp, ldf, up, ldu, out.data_ptr(), _stream(stream))
     if rc != CJ_OK:
         raise CJError(rc, "cj_residual_noalloc")
+
+
+def cj_solve_batch(problems, stream=None) -> list:
+    """Solve independent problems together.  Each problem is a dict with keys Nx, Ny, st,
+    tol, f (CUDA float64 tensor), u (in/out CUDA float64 tensor) and optionally precision,
+    inner_cycle, temporal_depth, max_sweeps.  Returns one result dict per problem."""
+    n = len(problems)
+    arr = (cj_problem * n)()
+    for k, pr in enumerate(problems):
+        fp, ldf = _grid(pr["f"], "float64")
+        up, ldu = _grid(pr["u"], "float64")
+        arr[k] = cj_problem(pr["Nx"], pr["Ny"], pr["st"], pr.get("precision", 0), pr["tol"],
+                            pr.get("inner_cycle", 0), pr.get("temporal_depth", 0),
+                            pr.get("max_sweeps", 0), fp, ldf, up, ldu)
+    res = (cj_result * n)()
+    rc = _lib().cj_solve_batch(arr, n, _stream(stream), res)
+    if rc not in (CJ_OK, CJ_ERR_TIMEOUT):
+        raise CJError(rc, "cj_solve_batch")
+    out = []
+    for k in range(n):
+        d = res[k].as_dict()
+        d["rc"] = res[k].status
+        out.append(d)
+    return out
+
+
+class Server:
+    """Request server with continuous batching (cj_server_create / cj_submit / cj_poll)."""
+
+    def __init__(self, hbm_budget_bytes: int, max_slots: int):
+        h = _vp()
+        rc = _lib().cj_server_create(hbm_budget_bytes, max_slots, ctypes.byref(h))
+        if rc != CJ_OK:
+            raise CJError(rc, "cj_server_create")
+        self.handle = h.value
+
+    def submit(self, f_host: np.ndarray, st: int, tol: float) -> int:
+        f_host = np.ascontiguousarray(f_host, dtype=np.float64)
+        Ny, Nx = f_host.shape
+        t = ctypes.c_uint64()
+        rc = _lib().cj_submit(self.handle, Nx, Ny, st, tol, f_host.ctypes.data, ctypes.byref(t))
+        if rc != CJ_OK:
+            raise CJError(rc, "cj_submit")
+        return t.value
+
+    def poll(self, ticket: int, shape):
+        """None while pending, else (u, result dict)."""
+        u = np.empty(shape, dtype=np.float64)
+        res = cj_result()
+        rc = _lib().cj_poll(self.handle, ticket, u.ctypes.data, ctypes.byref(res))
+        if rc == CJ_PENDING:
+            return None
+        d = res.as_dict()
+        d["rc"] = rc
+        return u, d
+
+    def stats(self) -> dict:
+        s = cj_server_stats_t()
+        rc = _lib().cj_server_stats(self.handle, ctypes.byref(s))
+        if rc != CJ_OK:
+            raise CJError(rc, "cj_server_stats")
+        return {k: getattr(s, k) for k, _ in s._fields_}
+
+    def close(self):
+        if self.handle:
+            _lib().cj_server_destroy(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
 
 
 class Plan:

@@ -1,0 +1,684 @@
+// Host side of the batched / served CJM engine: slot admission (plan math, device memory,
+// import), the captured CUDA graph of engine steps, completion polling, and the C ABI of
+// cj_solve_batch and of the request server (cj_server_* / cj_submit / cj_poll).
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <condition_variable>
+#include <cstddef>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <mutex>
+#include <new>
+#include <thread>
+#include <vector>
+
+#include "engine.cuh"
+
+namespace {
+
+using Clock = std::chrono::steady_clock;
+
+#define ENG_TRY(call, where)                \
+    do {                                    \
+        cudaError_t e_ = (call);            \
+        if (e_ != cudaSuccess) {            \
+            set_cuda_error(e_, where);      \
+            return CJ_ERR_CUDA;             \
+        }                                   \
+    } while (0)
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+// What a slot needs besides its device state: the allocation behind it.
+struct SlotMem {
+    char *base = nullptr;
+    size_t bytes = 0;
+};
+
+struct Spec {
+    int Nx, Ny, st, mode, inner_cycle, depth;
+    double tol;
+    long long max_sweeps;
+};
+
+// Device bytes a problem occupies in the engine (FP64 u, b [, u_lo], FP32 e0, e1, rt,
+// weights, partials).
+size_t slot_bytes(const Spec &sp, long long M_in) {
+    const Grid g64 = make_grid(sp.Nx, sp.Ny, 8), g32 = make_grid(sp.Nx, sp.Ny, 4);
+    const long long ntiles = (long long)((sp.Nx + kEngTX - 1) / kEngTX) * ((sp.Ny + kEngTY - 1) / kEngTY);
+    size_t n = 0;
+    n += align256(g64.elems() * 8) * (sp.mode == CJ_FP32_INNER_DD ? 3 : 2);
+    n += align256(g32.elems() * 4) * 3;
+    n += align256((size_t)M_in * 4);
+    n += align256((size_t)ntiles * 3 * 8);
+    return n;
+}
+
+class Engine {
+  public:
+    ~Engine() { destroy(); }
+
+    cj_status init(int max_slots, int max_depth) {
+        if (max_slots < 1 || max_depth < 1 || max_depth > kTbMaxDepth) return CJ_ERR_INVALID_ARG;
+        max_slots_ = max_slots;
+        max_depth_ = max_depth;
+        ENG_TRY(cudaGetDevice(&dev_), "cudaGetDevice");
+        ENG_TRY(cudaStreamCreateWithFlags(&s_, cudaStreamNonBlocking), "engine stream");
+        int sms = 152;
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev_);
+        grid_tiles_ = sms * 8;
+        grid_slots_ = std::min(max_slots, sms * 4);
+        smem_ = eng_sweep_smem(max_depth);
+        ENG_TRY(eng_prepare(smem_), "engine smem attribute");
+        host_.assign(max_slots, SlotDev{});
+        mem_.assign(max_slots, SlotMem{});
+        used_.assign(max_slots, 0);
+        ENG_TRY(cudaMalloc(&d_.slots, sizeof(SlotDev) * max_slots), "engine slots");
+        ENG_TRY(cudaMemset(d_.slots, 0, sizeof(SlotDev) * max_slots), "engine slots");
+        ENG_TRY(cudaMalloc(&d_.status, sizeof(SlotStatus) * max_slots), "engine status");
+        ENG_TRY(cudaMemset(d_.status, 0, sizeof(SlotStatus) * max_slots), "engine status");
+        ENG_TRY(cudaMalloc(&d_.ntiles, sizeof(int)), "engine tile count");
+        ENG_TRY(cudaMemset(d_.ntiles, 0, sizeof(int)), "engine tile count");
+        tile_cap_ = 0;
+        d_.tiles = nullptr;
+        d_.max_slots = max_slots;
+        ENG_TRY(cudaMallocHost(&h_status_, sizeof(SlotStatus) * max_slots), "engine status (host)");
+        ENG_TRY(cudaMallocHost(&h_ntiles_, sizeof(int)), "engine tile count (host)");
+        return ensure_tile_capacity(1024);
+    }
+
+    void destroy() {
+        if (!s_) return;
+        cudaStreamSynchronize(s_);
+        for (int q = 0; q < max_slots_; ++q)
+            if (mem_[q].base) cudaFree(mem_[q].base);
+        if (gexec_) cudaGraphExecDestroy(gexec_);
+        cudaFree(d_.slots);
+        cudaFree(d_.status);
+        cudaFree(d_.ntiles);
+        cudaFree(d_.tiles);
+        if (h_status_) cudaFreeHost(h_status_);
+        if (h_ntiles_) cudaFreeHost(h_ntiles_);
+        cudaStreamDestroy(s_);
+        s_ = nullptr;
+    }
+
+    cudaStream_t stream() const { return s_; }
+    int free_slots() const { return (int)std::count(used_.begin(), used_.end(), 0); }
+
+    // Plan numbers of a problem: (kmin, kmax, M_in), with the FP64 cycle length as the cap.
+    static cj_status plan(const Spec &sp, double *kmin, double *kmax, long long *M_in) {
+        plan_kappa_bounds(sp.st, sp.Nx + 1.0, sp.Ny + 1.0, kmin, kmax);
+        if (!(*kmin > 0.0 && *kmin < *kmax)) return CJ_ERR_INVALID_ARG;
+        const long long M = plan_cycle_length(*kmin, *kmax, sp.tol);
+        *M_in = sp.inner_cycle ? sp.inner_cycle : plan_inner_cycle(*kmin, *kmax, M);
+        return CJ_OK;
+    }
+
+    // Admit a problem into a free slot: f, u0 device grids (u0 may be NULL = zero), out:
+    // caller grid for the result.  Enqueued on the engine stream; takes effect at the next
+    // run().
+    // With out_to_b the result is exported into the interior of the slot's own b buffer
+    // (no longer needed once the slot is done), for callers without a device output grid.
+    cj_status admit(const Spec &sp, const double *f, long long ldf, const double *u0, long long ldu,
+                    double *out, long long ld_out, int *slot_out, bool out_to_b = false) {
+        int q = -1;
+        for (int k = 0; k < max_slots_; ++k)
+            if (!used_[k]) {
+                q = k;
+                break;
+            }
+        if (q < 0) return CJ_ERR_BUDGET;
+        double kmin, kmax;
+        long long M_in;
+        cj_status st = plan(sp, &kmin, &kmax, &M_in);
+        if (st != CJ_OK) return st;
+        const size_t bytes = slot_bytes(sp, M_in);
+        char *base = nullptr;
+        ENG_TRY(cudaMallocAsync((void **)&base, bytes, s_), "slot memory");
+        ENG_TRY(cudaMemsetAsync(base, 0, bytes, s_), "slot memory");
+        SlotDev S{};
+        S.Nx = sp.Nx;
+        S.Ny = sp.Ny;
+        S.st = sp.st;
+        S.mode = sp.mode;
+        S.depth = sp.depth;
+        S.ntx = (sp.Nx + kEngTX - 1) / kEngTX;
+        S.ntiles = S.ntx * ((sp.Ny + kEngTY - 1) / kEngTY);
+        S.M_in = M_in;
+        const long long max_sweeps = sp.max_sweeps ? sp.max_sweeps : 64 * M_in;
+        S.max_outer = max_sweeps / M_in;
+        S.tol = sp.tol;
+        S.S = plan_abs_coeff_sum(sp.st);
+        const double h = 1.0 / (double)(sp.Nx + 1);
+        S.h2 = h * h;
+        S.g64 = make_grid(sp.Nx, sp.Ny, 8);
+        S.g32 = make_grid(sp.Nx, sp.Ny, 4);
+        char *p = base;
+        const size_t b64 = align256(S.g64.elems() * 8), b32 = align256(S.g32.elems() * 4);
+        S.u = (double *)p;
+        p += b64;
+        S.b = (double *)p;
+        p += b64;
+        if (sp.mode == CJ_FP32_INNER_DD) {
+            S.ulo = (double *)p;
+            p += b64;
+        }
+        S.e0 = (float *)p;
+        p += b32;
+        S.e1 = (float *)p;
+        p += b32;
+        S.rt = (float *)p;
+        p += b32;
+        float *w32 = (float *)p;
+        p += align256((size_t)M_in * 4);
+        S.part = (double *)p;
+        if (out_to_b) {
+            S.out = S.b + S.g64.idx(1, 1);
+            S.ld_out = S.g64.pitch;
+        } else {
+            S.out = out;
+            S.ld_out = ld_out;
+        }
+        std::vector<double> w;
+        plan_sweep_coeffs(sp.st, kmin, kmax, M_in, w);
+        wstage_.assign(w.size(), 0.0f);
+        for (size_t k = 0; k < w.size(); ++k) wstage_[k] = (float)w[k];
+        S.w32 = w32;
+        host_[q] = S;
+        ENG_TRY(cudaMemcpyAsync(w32, wstage_.data(), wstage_.size() * 4, cudaMemcpyHostToDevice, s_), "weights");
+        ENG_TRY(cudaMemcpyAsync(d_.slots + q, &host_[q], sizeof(SlotDev), cudaMemcpyHostToDevice, s_), "slot upload");
+        ENG_TRY(cudaStreamSynchronize(s_), "admit sync");  // host staging buffers reused next time
+        const double *u0p = u0;
+        if (!u0p) {
+            // zero initial guess: the slot's u is already zero; import reads it in place
+            u0p = S.u + S.g64.idx(1, 1);
+            ldu = S.g64.pitch;
+        }
+        ENG_TRY(eng_launch_import(d_, q, S.ntiles, f, ldf, u0p, ldu, s_), "import");
+        mem_[q].base = base;
+        mem_[q].bytes = bytes;
+        used_[q] = 1;
+        tiles_dirty_ = true;
+        *slot_out = q;
+        return CJ_OK;
+    }
+
+    // Device pointer to the interior of slot q's b buffer and its pitch (elements).
+    void b_interior(int q, double **ptr, long long *pitch) const {
+        *ptr = host_[q].b + host_[q].g64.idx(1, 1);
+        *pitch = host_[q].g64.pitch;
+    }
+
+    size_t slot_mem(int q) const { return mem_[q].bytes; }
+
+    // Frees slot q (after its result has been read).
+    cj_status release(int q) {
+        if (q < 0 || q >= max_slots_ || !used_[q]) return CJ_ERR_INVALID_ARG;
+        const int free_phase = PHASE_FREE;
+        ENG_TRY(cudaMemcpyAsync((char *)(d_.slots + q) + offsetof(SlotDev, phase), &free_phase,
+                                sizeof(int), cudaMemcpyHostToDevice, s_), "slot release");
+        ENG_TRY(cudaFreeAsync(mem_[q].base, s_), "slot free");
+        ENG_TRY(cudaStreamSynchronize(s_), "release sync");
+        mem_[q] = SlotMem{};
+        used_[q] = 0;
+        tiles_dirty_ = true;
+        return CJ_OK;
+    }
+
+    // Runs `replays` graph replays of the engine steps, then refreshes the host status.
+    cj_status run(int replays) {
+        if (tiles_dirty_) {
+            cj_status st = upload_tiles();
+            if (st != CJ_OK) return st;
+        }
+        if (!gexec_) {
+            cj_status st = capture();
+            if (st != CJ_OK) return st;
+        }
+        for (int k = 0; k < replays; ++k) ENG_TRY(cudaGraphLaunch(gexec_, s_), "graph launch");
+        launches_ += (long long)replays * steps_per_graph_ * 6;
+        ENG_TRY(cudaMemcpyAsync(h_status_, d_.status, sizeof(SlotStatus) * max_slots_,
+                                cudaMemcpyDeviceToHost, s_), "status readback");
+        ENG_TRY(cudaStreamSynchronize(s_), "step sync");
+        return CJ_OK;
+    }
+
+    const SlotStatus &status(int q) const { return h_status_[q]; }
+    bool used(int q) const { return used_[q] != 0; }
+    long long launches() const { return launches_; }
+    int steps_per_graph() const { return steps_per_graph_; }
+
+  private:
+    cj_status ensure_tile_capacity(int n) {
+        if (n <= tile_cap_) return CJ_OK;
+        int cap = std::max(n, 2 * tile_cap_);
+        int2 *t = nullptr;
+        ENG_TRY(cudaMalloc(&t, sizeof(int2) * cap), "tile table");
+        cudaFree(d_.tiles);
+        d_.tiles = t;
+        tile_cap_ = cap;
+        if (gexec_) {  // the graph bakes the table pointer in: capture again
+            cudaGraphExecDestroy(gexec_);
+            gexec_ = nullptr;
+        }
+        return CJ_OK;
+    }
+
+    cj_status upload_tiles() {
+        tiles_.clear();
+        for (int q = 0; q < max_slots_; ++q)
+            if (used_[q])
+                for (int t = 0; t < host_[q].ntiles; ++t) tiles_.push_back(make_int2(q, t));
+        cj_status st = ensure_tile_capacity((int)tiles_.size() + 1);
+        if (st != CJ_OK) return st;
+        *h_ntiles_ = (int)tiles_.size();
+        if (!tiles_.empty())
+            ENG_TRY(cudaMemcpyAsync(d_.tiles, tiles_.data(), sizeof(int2) * tiles_.size(),
+                                    cudaMemcpyHostToDevice, s_), "tile upload");
+        ENG_TRY(cudaMemcpyAsync(d_.ntiles, h_ntiles_, sizeof(int), cudaMemcpyHostToDevice, s_), "tile count");
+        ENG_TRY(cudaStreamSynchronize(s_), "tile sync");
+        tiles_dirty_ = false;
+        return CJ_OK;
+    }
+
+    cj_status capture() {
+        cudaGraph_t g = nullptr;
+        ENG_TRY(cudaStreamBeginCapture(s_, cudaStreamCaptureModeThreadLocal), "begin capture");
+        cudaError_t err = cudaSuccess;
+        for (int k = 0; k < steps_per_graph_ && err == cudaSuccess; ++k)
+            err = eng_launch_step(d_, grid_tiles_, grid_slots_, smem_, s_);
+        cudaError_t e2 = cudaStreamEndCapture(s_, &g);
+        if (err == cudaSuccess) err = e2;
+        if (err == cudaSuccess) err = cudaGraphInstantiate(&gexec_, g, 0);
+        if (g) cudaGraphDestroy(g);
+        ENG_TRY(err, "graph capture");
+        return CJ_OK;
+    }
+
+    int dev_ = 0, max_slots_ = 0, max_depth_ = 1, grid_tiles_ = 0, grid_slots_ = 0;
+    int steps_per_graph_ = 32;
+    size_t smem_ = 0;
+    cudaStream_t s_ = nullptr;
+    EngineDev d_{};
+    std::vector<SlotDev> host_;
+    std::vector<SlotMem> mem_;
+    std::vector<char> used_;
+    std::vector<int2> tiles_;
+    std::vector<float> wstage_;
+    int tile_cap_ = 0;
+    bool tiles_dirty_ = true;
+    SlotStatus *h_status_ = nullptr;
+    int *h_ntiles_ = nullptr;
+    cudaGraphExec_t gexec_ = nullptr;
+    long long launches_ = 0;
+};
+
+// Precision a request gets when it does not name one: FP64 outer steps unless the FP64
+// rounding floor of the relative residual (about 2^-53 S / (c kmin)) comes within 4x of
+// the tolerance, then double-FP64.
+int auto_mode(int st, int Nx, int Ny, double tol) {
+    double kmin, kmax;
+    plan_kappa_bounds(st, Nx + 1.0, Ny + 1.0, &kmin, &kmax);
+    const double fl = 1.1102230246251565e-16 * plan_abs_coeff_sum(st) / (plan_centre(st) * kmin);
+    return 4.0 * fl > tol ? CJ_FP32_INNER_DD : CJ_FP32_INNER;
+}
+
+cj_status check_problem(const cj_problem &pr) {
+    if (pr.Nx < 1 || pr.Ny < 1 || pr.Nx > (1 << 20) || pr.Ny > (1 << 20)) return CJ_ERR_INVALID_ARG;
+    if (pr.st != CJ_ST5 && pr.st != CJ_ST9 && pr.st != CJ_ST17) return CJ_ERR_INVALID_ARG;
+    if (!(pr.tol > 0.0 && pr.tol < 1.0)) return CJ_ERR_INVALID_ARG;
+    if (pr.precision != 0 && pr.precision != CJ_FP32_INNER && pr.precision != CJ_FP32_INNER_DD)
+        return CJ_ERR_INVALID_ARG;
+    if (pr.inner_cycle < 0 || (pr.inner_cycle & (pr.inner_cycle - 1)) != 0) return CJ_ERR_INVALID_ARG;
+    if (pr.temporal_depth < 0 || pr.temporal_depth > kTbMaxDepth) return CJ_ERR_INVALID_ARG;
+    if (!pr.f || !pr.u || pr.ld_f < pr.Nx || pr.ld_u < pr.Nx) return CJ_ERR_INVALID_ARG;
+    return CJ_OK;
+}
+
+Spec spec_of(const cj_problem &pr) {
+    Spec sp;
+    sp.Nx = pr.Nx;
+    sp.Ny = pr.Ny;
+    sp.st = pr.st;
+    sp.tol = pr.tol;
+    sp.mode = pr.precision ? pr.precision : auto_mode(pr.st, pr.Nx, pr.Ny, pr.tol);
+    sp.inner_cycle = pr.inner_cycle;
+    sp.depth = pr.temporal_depth ? pr.temporal_depth : 1;
+    sp.max_sweeps = pr.max_sweeps;
+    return sp;
+}
+
+void fill_result(const SlotStatus &st, cj_result *r) {
+    r->sweeps = st.sweeps;
+    r->cycles = (int)st.outer;
+    r->status = st.status;
+    r->rel_res_l2 = st.rho;
+    r->rel_res_inf = st.rinf;
+    r->floor_est = st.fl;
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ request server
+
+struct cj_server {
+    struct Request {
+        uint64_t ticket;
+        Spec sp;
+        std::vector<double> f;     // host copy of the right-hand side
+        std::vector<double> u;     // host result
+        int slot = -1;
+        size_t bytes = 0;
+        int state = 0;             // 0 queued, 1 running, 2 done
+        cj_status rc = CJ_PENDING;
+        cj_result res{};
+        Clock::time_point t_submit, t_admit, t_done;
+    };
+
+    Engine eng;
+    size_t budget = 0, in_use = 0;
+    int max_slots = 0;
+    std::mutex mu;
+    std::condition_variable cv;
+    std::deque<uint64_t> queue;
+    std::map<uint64_t, Request> reqs;
+    std::map<int, uint64_t> by_slot;
+    uint64_t next_ticket = 1;
+    bool stop = false;
+    cj_status fatal = CJ_OK;
+    std::thread worker;
+    int device = 0;
+    long long steps = 0, admitted = 0, completed = 0, peak_active = 0;
+    size_t peak_bytes = 0;
+
+    void loop() {
+        cudaSetDevice(device);
+        for (;;) {
+            std::vector<uint64_t> admit_now;
+            {
+                std::unique_lock<std::mutex> lk(mu);
+                cv.wait(lk, [&] { return stop || !queue.empty() || !by_slot.empty(); });
+                if (stop) return;
+                // admission by footprint and free slots, in arrival order
+                while (!queue.empty()) {
+                    Request &r = reqs[queue.front()];
+                    double kmin, kmax;
+                    long long M_in;
+                    if (Engine::plan(r.sp, &kmin, &kmax, &M_in) != CJ_OK) {
+                        r.state = 2;
+                        r.rc = CJ_ERR_INVALID_ARG;
+                        queue.pop_front();
+                        continue;
+                    }
+                    const size_t need = slot_bytes(r.sp, M_in);
+                    if (need > budget) {
+                        r.state = 2;
+                        r.rc = CJ_ERR_BUDGET;
+                        queue.pop_front();
+                        continue;
+                    }
+                    if (in_use + need > budget || (int)(by_slot.size() + admit_now.size()) >= max_slots)
+                        break;
+                    r.bytes = need;
+                    in_use += need;
+                    admit_now.push_back(queue.front());
+                    queue.pop_front();
+                }
+            }
+            for (uint64_t t : admit_now) {
+                Request *r;
+                {
+                    std::lock_guard<std::mutex> lk(mu);
+                    r = &reqs[t];
+                }
+                cj_status st = admit(*r);
+                std::lock_guard<std::mutex> lk(mu);
+                if (st != CJ_OK) {
+                    r->state = 2;
+                    r->rc = st;
+                    in_use -= r->bytes;
+                    if (st == CJ_ERR_CUDA) fatal = st;
+                } else {
+                    r->state = 1;
+                    r->t_admit = Clock::now();
+                    by_slot[r->slot] = t;
+                    ++admitted;
+                    peak_active = std::max<long long>(peak_active, (long long)by_slot.size());
+                    peak_bytes = std::max(peak_bytes, in_use);
+                }
+            }
+            bool active;
+            {
+                std::lock_guard<std::mutex> lk(mu);
+                active = !by_slot.empty();
+            }
+            if (!active) continue;
+            if (eng.run(1) != CJ_OK) {
+                std::lock_guard<std::mutex> lk(mu);
+                fatal = CJ_ERR_CUDA;
+                for (auto &kv : by_slot) {
+                    reqs[kv.second].state = 2;
+                    reqs[kv.second].rc = CJ_ERR_CUDA;
+                }
+                by_slot.clear();
+                cv.notify_all();
+                return;
+            }
+            steps += eng.steps_per_graph();
+            // release finished problems
+            std::vector<std::pair<int, uint64_t>> done;
+            {
+                std::lock_guard<std::mutex> lk(mu);
+                for (auto &kv : by_slot)
+                    if (eng.status(kv.first).phase == PHASE_RETIRED) done.push_back(kv);
+            }
+            for (auto &d : done) {
+                Request *r;
+                {
+                    std::lock_guard<std::mutex> lk(mu);
+                    r = &reqs[d.second];
+                }
+                const SlotStatus &ss = eng.status(d.first);
+                double *bin;
+                long long pitch;
+                eng.b_interior(d.first, &bin, &pitch);
+                r->u.assign((size_t)r->sp.Nx * r->sp.Ny, 0.0);
+                cudaError_t e = cudaMemcpy2DAsync(r->u.data(), (size_t)r->sp.Nx * 8, bin, (size_t)pitch * 8,
+                                                  (size_t)r->sp.Nx * 8, r->sp.Ny, cudaMemcpyDeviceToHost,
+                                                  eng.stream());
+                if (e == cudaSuccess) e = cudaStreamSynchronize(eng.stream());
+                fill_result(ss, &r->res);
+                eng.release(d.first);
+                std::lock_guard<std::mutex> lk(mu);
+                r->t_done = Clock::now();
+                r->res.seconds = std::chrono::duration<double>(r->t_done - r->t_submit).count();
+                r->rc = e != cudaSuccess ? CJ_ERR_CUDA : (cj_status)ss.status;
+                r->state = 2;
+                in_use -= r->bytes;
+                by_slot.erase(d.first);
+                ++completed;
+                cv.notify_all();
+            }
+        }
+    }
+
+    // Stages f on the device, admits the request, and points its result at the slot's own b
+    // interior (read back by the worker when the slot retires).
+    cj_status admit(Request &r) {
+        double *fd = nullptr;
+        const size_t fbytes = (size_t)r.sp.Nx * r.sp.Ny * 8;
+        ENG_TRY(cudaMallocAsync((void **)&fd, fbytes, eng.stream()), "request f");
+        ENG_TRY(cudaMemcpyAsync(fd, r.f.data(), fbytes, cudaMemcpyHostToDevice, eng.stream()), "request H2D");
+        int slot = -1;
+        cj_status st = eng.admit(r.sp, fd, r.sp.Nx, nullptr, 0, nullptr, 0, &slot, true);
+        cudaError_t e = cudaFreeAsync(fd, eng.stream());
+        if (st == CJ_OK && e != cudaSuccess) {
+            set_cuda_error(e, "request f free");
+            st = CJ_ERR_CUDA;
+        }
+        r.slot = slot;
+        std::vector<double>().swap(r.f);
+        return st;
+    }
+};
+
+// ------------------------------------------------------------------ C ABI
+
+extern "C" {
+
+cj_status cj_solve_batch(const cj_problem *problems, int n, void *stream, cj_result *results) {
+    if (!problems || n < 1 || !results) return CJ_ERR_INVALID_ARG;
+    int max_depth = 1;
+    for (int k = 0; k < n; ++k) {
+        cj_status st = check_problem(problems[k]);
+        if (st != CJ_OK) return st;
+        max_depth = std::max(max_depth, problems[k].temporal_depth);
+    }
+    auto t0 = Clock::now();
+    Engine eng;
+    cj_status st = eng.init(n, max_depth);
+    if (st != CJ_OK) return st;
+    cudaEvent_t ev;
+    ENG_TRY(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming), "event");
+    ENG_TRY(cudaEventRecord(ev, (cudaStream_t)stream), "event");
+    ENG_TRY(cudaStreamWaitEvent(eng.stream(), ev, 0), "event wait");
+    std::vector<int> slot(n, -1);
+    long long max_steps = 0;
+    for (int k = 0; k < n; ++k) {
+        const cj_problem &pr = problems[k];
+        const Spec sp = spec_of(pr);
+        st = eng.admit(sp, pr.f, pr.ld_f, pr.u, pr.ld_u, pr.u, pr.ld_u, &slot[k]);
+        if (st != CJ_OK) {
+            cudaEventDestroy(ev);
+            return st;
+        }
+        double kmin, kmax;
+        long long M_in = 1;
+        Engine::plan(sp, &kmin, &kmax, &M_in);
+        const long long max_sweeps = sp.max_sweeps ? sp.max_sweeps : 64 * M_in;
+        const long long outer = max_sweeps / M_in + 1;
+        max_steps = std::max(max_steps, outer * (M_in / sp.depth + 2) + 4);
+    }
+    // every slot retires within max_steps engine steps (its outer-step budget)
+    const long long max_replays = max_steps / eng.steps_per_graph() + 2;
+    bool all = false;
+    for (long long rep = 0; rep < max_replays && !all; ++rep) {
+        st = eng.run(1);
+        if (st != CJ_OK) {
+            cudaEventDestroy(ev);
+            return st;
+        }
+        all = true;
+        for (int k = 0; k < n; ++k)
+            if (eng.status(slot[k]).phase != PHASE_RETIRED) all = false;
+    }
+    const double secs = std::chrono::duration<double>(Clock::now() - t0).count();
+    for (int k = 0; k < n; ++k) {
+        cj_result r{};
+        fill_result(eng.status(slot[k]), &r);
+        if (!all && eng.status(slot[k]).phase != PHASE_RETIRED) r.status = CJ_ERR_TIMEOUT;
+        r.seconds = secs;
+        r.launches = eng.launches();
+        results[k] = r;
+    }
+    ENG_TRY(cudaEventRecord(ev, eng.stream()), "event");
+    ENG_TRY(cudaStreamWaitEvent((cudaStream_t)stream, ev, 0), "event wait");
+    ENG_TRY(cudaStreamSynchronize(eng.stream()), "batch sync");
+    cudaEventDestroy(ev);
+    return all ? CJ_OK : CJ_ERR_TIMEOUT;
+}
+
+cj_status cj_server_create(size_t hbm_budget_bytes, int max_slots, cj_server **out) {
+    if (!out || hbm_budget_bytes == 0 || max_slots < 1) return CJ_ERR_INVALID_ARG;
+    *out = nullptr;
+    cj_server *sv = new (std::nothrow) cj_server();
+    if (!sv) return CJ_ERR_NOMEM;
+    sv->budget = hbm_budget_bytes;
+    sv->max_slots = max_slots;
+    cudaGetDevice(&sv->device);
+    cj_status st = sv->eng.init(max_slots, 1);
+    if (st != CJ_OK) {
+        delete sv;
+        return st;
+    }
+    try {
+        sv->worker = std::thread([sv] { sv->loop(); });
+    } catch (...) {
+        delete sv;
+        return CJ_ERR_NOMEM;
+    }
+    *out = sv;
+    return CJ_OK;
+}
+
+cj_status cj_submit(cj_server *sv, int Nx, int Ny, cj_stencil st, double tol, const double *f_host,
+                    uint64_t *ticket) {
+    if (!sv || !f_host || !ticket) return CJ_ERR_INVALID_ARG;
+    cj_problem pr{};
+    pr.Nx = Nx;
+    pr.Ny = Ny;
+    pr.st = st;
+    pr.tol = tol;
+    pr.f = f_host;
+    pr.u = (double *)f_host;
+    pr.ld_f = pr.ld_u = Nx;
+    cj_status c = check_problem(pr);
+    if (c != CJ_OK) return c;
+    std::lock_guard<std::mutex> lk(sv->mu);
+    if (sv->fatal != CJ_OK) return sv->fatal;
+    const uint64_t t = sv->next_ticket++;
+    cj_server::Request &r = sv->reqs[t];
+    r.ticket = t;
+    r.sp = spec_of(pr);
+    r.f.assign(f_host, f_host + (size_t)Nx * Ny);
+    r.t_submit = Clock::now();
+    sv->queue.push_back(t);
+    *ticket = t;
+    sv->cv.notify_all();
+    return CJ_OK;
+}
+
+cj_status cj_poll(cj_server *sv, uint64_t ticket, double *u_host, cj_result *res) {
+    if (!sv) return CJ_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lk(sv->mu);
+    auto it = sv->reqs.find(ticket);
+    if (it == sv->reqs.end()) return CJ_ERR_INVALID_ARG;
+    cj_server::Request &r = it->second;
+    if (r.state != 2) return CJ_PENDING;
+    if (u_host && !r.u.empty()) std::memcpy(u_host, r.u.data(), r.u.size() * sizeof(double));
+    if (res) *res = r.res;
+    const cj_status rc = r.rc;
+    sv->reqs.erase(it);
+    return rc;
+}
+
+cj_status cj_server_stats(cj_server *sv, cj_server_stats_t *out) {
+    if (!sv || !out) return CJ_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lk(sv->mu);
+    out->queued = (long long)sv->queue.size();
+    out->active = (long long)sv->by_slot.size();
+    out->admitted = sv->admitted;
+    out->completed = sv->completed;
+    out->steps = sv->steps;
+    out->peak_active = sv->peak_active;
+    out->bytes_in_use = sv->in_use;
+    out->peak_bytes = sv->peak_bytes;
+    out->budget_bytes = sv->budget;
+    return CJ_OK;
+}
+
+void cj_server_destroy(cj_server *sv) {
+    if (!sv) return;
+    {
+        std::lock_guard<std::mutex> lk(sv->mu);
+        sv->stop = true;
+        sv->cv.notify_all();
+    }
+    if (sv->worker.joinable()) sv->worker.join();
+    delete sv;
+}
+
+}  // extern "C"

@@ -11,104 +11,9 @@
 // plain one-thread-per-node kernel; the term order is fixed and equals the reference's.
 #include "cj_internal.h"
 #include "grid_dev.cuh"
+#include "stencil_dev.cuh"
 
 namespace {
-
-__device__ __forceinline__ void two_sum(double a, double b, double &s, double &e) {
-    double x = a + b;
-    double z = x - a;
-    e = (a - (x - z)) + (b - z);
-    s = x;
-}
-
-struct Sum2 {
-    double S = 0.0, E = 0.0;
-    __device__ __forceinline__ void add(double t) {
-        double e;
-        two_sum(S, t, S, e);
-        E += e;
-    }
-};
-
-// Plain FP64 L u at node (i, j) in the evaluation order of the sweep kernels (b = 0).
-template <int ST>
-__device__ __forceinline__ double plain_L(const double *u, const Grid &g, int i, int j) {
-    auto U = [&](int di, int dj) { return u[g.idx(i + di, j + dj)]; };
-    const double uC = U(0, 0);
-    const double v1 = U(0, -1) + U(0, 1);
-    const double p0 = U(-1, 0) + U(1, 0);
-    if (ST == 5) return (p0 + v1) + fma(-4.0, uC, -0.0);
-    const double pm = U(-1, -1) + U(1, -1);
-    const double pp = U(-1, 1) + U(1, 1);
-    if (ST == 9)
-        return fma(4.0 / 6.0, p0 + v1, fma(1.0 / 6.0, pm + pp, fma(-20.0 / 6.0, uC, -0.0)));
-    const double v2 = U(0, -2) + U(0, 2);
-    const double P0 = U(-2, 0) + U(2, 0);
-    const double Pm = U(-2, -2) + U(2, -2);
-    const double Pp = U(-2, 2) + U(2, 2);
-    return fma(64.0 / 72.0, p0 + v1,
-               fma(-4.0 / 72.0, P0 + v2,
-                   fma(16.0 / 72.0, pm + pp, fma(-1.0 / 72.0, Pm + Pp, fma(-300.0 / 72.0, uC, -0.0)))));
-}
-
-// R = L (uh + ul) - bk at node (i, j), rounded to FP64 (term order as documented above).
-template <int ST>
-__device__ __forceinline__ double resid_dd(const double *uh, const double *ul, const Grid &g,
-                                           int i, int j, double bk) {
-    auto H = [&](int di, int dj) { return uh[g.idx(i + di, j + dj)]; };
-    const double uC = H(0, 0);
-    Sum2 s;
-    double D;
-    if (ST == 5) {
-        D = 1.0;
-        s.add(H(-1, 0));
-        s.add(H(1, 0));
-        s.add(H(0, -1));
-        s.add(H(0, 1));
-        s.add(-4.0 * uC);
-        s.add(-bk);
-    } else if (ST == 9) {
-        D = 6.0;
-        s.add(4.0 * H(-1, 0));
-        s.add(4.0 * H(1, 0));
-        s.add(4.0 * H(0, -1));
-        s.add(4.0 * H(0, 1));
-        s.add(H(-1, -1));
-        s.add(H(1, -1));
-        s.add(H(-1, 1));
-        s.add(H(1, 1));
-        s.add(-16.0 * uC);
-        s.add(-4.0 * uC);
-        s.add(-4.0 * bk);
-        s.add(-2.0 * bk);
-    } else {
-        D = 72.0;
-        s.add(64.0 * H(-1, 0));
-        s.add(64.0 * H(1, 0));
-        s.add(64.0 * H(0, -1));
-        s.add(64.0 * H(0, 1));
-        s.add(-4.0 * H(-2, 0));
-        s.add(-4.0 * H(2, 0));
-        s.add(-4.0 * H(0, -2));
-        s.add(-4.0 * H(0, 2));
-        s.add(16.0 * H(-1, -1));
-        s.add(16.0 * H(1, -1));
-        s.add(16.0 * H(-1, 1));
-        s.add(16.0 * H(1, 1));
-        s.add(-H(-2, -2));
-        s.add(-H(2, -2));
-        s.add(-H(-2, 2));
-        s.add(-H(2, 2));
-        s.add(-256.0 * uC);
-        s.add(-32.0 * uC);
-        s.add(-8.0 * uC);
-        s.add(-4.0 * uC);
-        s.add(-64.0 * bk);
-        s.add(-8.0 * bk);
-    }
-    const double Llo = plain_L<ST>(ul, g, i, j);
-    return (s.S + (s.E + D * Llo)) / D;
-}
 
 template <int ST>
 __global__ void __launch_bounds__(kBX) defect_dd_kernel(const double *__restrict__ uh,

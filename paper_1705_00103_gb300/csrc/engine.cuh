@@ -1,0 +1,60 @@
+// Device-resident state of the batched / served CJM engine (shared by engine.cu and
+// batch.cpp).  Each admitted problem occupies one slot; every kernel of an engine step
+// reads the slots' phases from device memory, so one captured CUDA graph of steps serves
+// whatever set of problems is admitted when it is replayed.
+#pragma once
+
+#include "cj_internal.h"
+
+// Engine tile: the unit of work of every engine kernel (columns x rows of nodes).
+constexpr int kEngTX = 128, kEngTY = 32;
+
+enum SlotPhase : int {
+    PHASE_FREE = 0,     // unused
+    PHASE_OUTER = 1,    // next step: correction (after the first cycle) + defect + stop test
+    PHASE_SWEEP = 2,    // inner FP32 cycle in progress
+    PHASE_DONE = 3,     // stopped; the next step copies u to the caller's buffer
+    PHASE_RETIRED = 4   // result delivered; the host may release the slot
+};
+
+struct SlotDev {
+    // set at admission
+    int Nx, Ny, st, mode;          // mode: CJ_FP32_INNER or CJ_FP32_INNER_DD
+    int depth, ntx, ntiles, pad0;
+    long long M_in, max_outer;
+    double tol, S, h2;
+    Grid g64, g32;
+    double *u, *ulo, *b;           // padded FP64 (ulo: CJ_FP32_INNER_DD only)
+    float *e0, *e1, *rt;           // padded FP32
+    const float *w32;              // inner-cycle weights, M_in of them
+    double *part;                  // 3 doubles per tile
+    double *out;                   // caller's device grid for the result
+    long long ld_out;
+    // evolving
+    int phase, status, cur, stall;
+    long long counter, outer, sweeps;
+    double prev, rho, rinf, fl, bsq, bmax;
+};
+
+// Compact per-slot record the host polls after each replay.
+struct SlotStatus {
+    int phase, status;
+    long long sweeps, outer;
+    double rho, rinf, fl;
+};
+
+struct EngineDev {
+    SlotDev *slots;        // max_slots entries
+    int max_slots;
+    int2 *tiles;           // (slot, tile index within the slot)
+    int *ntiles;           // device counter of valid entries in tiles
+    SlotStatus *status;    // max_slots entries, refreshed by the advance kernel
+};
+
+// launchers (engine.cu)
+cudaError_t eng_launch_step(const EngineDev &e, int grid_tiles, int grid_slots, size_t sweep_smem,
+                            cudaStream_t s);
+cudaError_t eng_launch_import(const EngineDev &e, int slot, int ntiles, const double *f,
+                              long long ldf, const double *u0, long long ldu, cudaStream_t s);
+size_t eng_sweep_smem(int max_depth);
+cudaError_t eng_prepare(size_t sweep_smem);

@@ -24,143 +24,9 @@
 
 #include "cj_internal.h"
 #include "grid_dev.cuh"
+#include "stencil_dev.cuh"
 
 namespace {
-
-template <typename T>
-struct Ar;
-template <>
-struct Ar<double> {
-    static __device__ __forceinline__ double add(double a, double b, double one) {
-        return fma(a, one, b);
-    }
-    static __device__ __forceinline__ double fm(double a, double b, double c) { return fma(a, b, c); }
-};
-template <>
-struct Ar<float> {
-    static __device__ __forceinline__ float add(float a, float b, float) { return a + b; }
-    static __device__ __forceinline__ float fm(float a, float b, float c) { return fmaf(a, b, c); }
-};
-
-// Stencil coefficients of h^2 Delta_h (Table 3; Eq. 1 and Fig. 1 left; Eq. 2 and Fig. 1
-// right), rounded once to the working type.
-template <typename T>
-struct Co;
-template <>
-struct Co<double> {
-    static __device__ __forceinline__ double c5() { return -4.0; }
-    static __device__ __forceinline__ double ax9() { return 4.0 / 6.0; }
-    static __device__ __forceinline__ double dg9() { return 1.0 / 6.0; }
-    static __device__ __forceinline__ double cc9() { return -20.0 / 6.0; }
-    static __device__ __forceinline__ double a1() { return 64.0 / 72.0; }
-    static __device__ __forceinline__ double a2() { return -4.0 / 72.0; }
-    static __device__ __forceinline__ double d1() { return 16.0 / 72.0; }
-    static __device__ __forceinline__ double d2() { return -1.0 / 72.0; }
-    static __device__ __forceinline__ double cc17() { return -300.0 / 72.0; }
-};
-template <>
-struct Co<float> {
-    static __device__ __forceinline__ float c5() { return -4.0f; }
-    static __device__ __forceinline__ float ax9() { return 4.0f / 6.0f; }
-    static __device__ __forceinline__ float dg9() { return 1.0f / 6.0f; }
-    static __device__ __forceinline__ float cc9() { return -20.0f / 6.0f; }
-    static __device__ __forceinline__ float a1() { return 64.0f / 72.0f; }
-    static __device__ __forceinline__ float a2() { return -4.0f / 72.0f; }
-    static __device__ __forceinline__ float d1() { return 16.0f / 72.0f; }
-    static __device__ __forceinline__ float d2() { return -1.0f / 72.0f; }
-    static __device__ __forceinline__ float cc17() { return -300.0f / 72.0f; }
-};
-
-template <typename T>
-__device__ __forceinline__ T ld(const T *p) {
-    return __ldg(p);
-}
-
-// Walks rows j0..j1 of column i and calls op(j, r, u(i,j)) with r = (L u - b)(i, j).
-template <int ST, typename T, class Op>
-__device__ __forceinline__ void march(const T *__restrict__ u, const T *__restrict__ b,
-                                      const Grid &g, int i, int j0, int j1, T one, Op &op) {
-    using A = Ar<T>;
-    using C = Co<T>;
-    const long long P = g.pitch;
-    const T *col = u + g.idx(i, 0);  // node (i, 0); row k at col + k * P
-    const T *bcol = b + g.idx(i, 0);
-    if (ST == 5) {
-        T um = ld(col + (long long)(j0 - 1) * P);
-        T uc = ld(col + (long long)j0 * P);
-        for (int j = j0; j <= j1; ++j) {
-            const T *row = col + (long long)j * P;
-            T up = ld(row + P);
-            T p0 = A::add(ld(row - 1), ld(row + 1), one);
-            T v1 = A::add(um, up, one);
-            T bk = ld(bcol + (long long)j * P);
-            T a = A::add(p0, v1, one);
-            T r = A::add(a, A::fm(C::c5(), uc, -bk), one);
-            op(j, r, uc);
-            um = uc;
-            uc = up;
-        }
-    } else if (ST == 9) {
-        const T *row = col + (long long)(j0 - 1) * P;
-        T um = ld(row);
-        T pm = A::add(ld(row - 1), ld(row + 1), one);
-        row += P;
-        T uc = ld(row);
-        T pc = A::add(ld(row - 1), ld(row + 1), one);
-        for (int j = j0; j <= j1; ++j) {
-            row = col + (long long)(j + 1) * P;
-            T up = ld(row);
-            T pp = A::add(ld(row - 1), ld(row + 1), one);
-            T bk = ld(bcol + (long long)j * P);
-            T v1 = A::add(um, up, one);
-            T a = A::add(pc, v1, one);
-            T d = A::add(pm, pp, one);
-            T r = A::fm(C::ax9(), a, A::fm(C::dg9(), d, A::fm(C::cc9(), uc, -bk)));
-            op(j, r, uc);
-            um = uc;
-            uc = up;
-            pm = pc;
-            pc = pp;
-        }
-    } else {
-        // rows j-2 .. j+1 in registers on entry to each iteration; row j+2 loaded in it
-        T u_[4], p_[4], Q_[4];
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            const T *row = col + (long long)(j0 - 2 + k) * P;
-            u_[k] = ld(row);
-            p_[k] = A::add(ld(row - 1), ld(row + 1), one);
-            Q_[k] = A::add(ld(row - 2), ld(row + 2), one);
-        }
-        for (int j = j0; j <= j1; ++j) {
-            const T *row = col + (long long)(j + 2) * P;
-            T u4 = ld(row);
-            T p4 = A::add(ld(row - 1), ld(row + 1), one);
-            T Q4 = A::add(ld(row - 2), ld(row + 2), one);
-            T bk = ld(bcol + (long long)j * P);
-            // u_[0..3] = rows j-2, j-1, j, j+1; u4 = row j+2
-            T v1 = A::add(u_[1], u_[3], one);
-            T v2 = A::add(u_[0], u4, one);
-            T a1 = A::add(p_[2], v1, one);
-            T a2 = A::add(Q_[2], v2, one);
-            T d1 = A::add(p_[1], p_[3], one);
-            T d2 = A::add(Q_[0], Q4, one);
-            T r = A::fm(C::a1(), a1,
-                        A::fm(C::a2(), a2,
-                              A::fm(C::d1(), d1, A::fm(C::d2(), d2, A::fm(C::cc17(), u_[2], -bk)))));
-            op(j, r, u_[2]);
-#pragma unroll
-            for (int k = 0; k < 3; ++k) {
-                u_[k] = u_[k + 1];
-                p_[k] = p_[k + 1];
-                Q_[k] = Q_[k + 1];
-            }
-            u_[3] = u4;
-            p_[3] = p4;
-            Q_[3] = Q4;
-        }
-    }
-}
 
 template <int ST, typename T>
 struct SweepOp {
