@@ -154,14 +154,24 @@ class ClockSampler:
 
 # ----------------------------------------------------------------- traffic record
 
+KERNEL_SOURCES = ("kernels.cu", "stencil_dev.cuh", "grid_dev.cuh")
+
+
+def kernel_digest() -> str:
+    """Digest of the sources the sweep kernel is compiled from."""
+    h = hashlib.sha256()
+    for name in KERNEL_SOURCES:
+        h.update(open(os.path.join(ROOT, "paper_1705_00103_gb300", "csrc", name), "rb").read())
+    return h.hexdigest()[:16]
+
+
 def traffic_per_launch(kernel_key: str):
     """DRAM bytes per launch of a kernel from the committed ncu summary, or None when the
-    kernel source changed since the counters were taken."""
+    kernel's sources changed since the counters were taken."""
     path = os.path.join(ROOT, "profiles", "traffic_per_launch.txt")
-    src = os.path.join(ROOT, "paper_1705_00103_gb300", "csrc", "kernels.cu")
     if not os.path.exists(path):
         return None
-    digest = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    digest = kernel_digest()
     for line in open(path):
         parts = line.split()
         if len(parts) >= 3 and not line.startswith("#") and parts[0] == kernel_key:

@@ -96,6 +96,10 @@ cudaError_t launch_correct_dd(const cj_plan *p, double *uh, double *ul, const fl
 // temporal-blocked FP32 sweeps (tblock.cu): `depth` sweeps with weights w[0..depth-1]
 cudaError_t launch_sweep32_tb(const cj_plan *p, const float *e, const float *r, float *out,
                               const float *w, int depth, cudaStream_t s);
+// wavefront temporal-blocked FP32 sweeps (wave.cu): k in {2, 4, 8} sweeps per launch
+int wave_depth_supported(int k);
+cudaError_t launch_sweep32_wave(const cj_plan *p, const float *e, const float *r, float *out,
+                                const float *w, int k, cudaStream_t s);
 cudaError_t launch_import32(const cj_plan *p, const float *src, long long ld, float *dst_pad,
                             cudaStream_t s);
 cudaError_t launch_export32(const cj_plan *p, const float *src_pad, float *dst, long long ld,

@@ -164,14 +164,16 @@ cudaError_t fp32_sweeps(cj_plan *p, float **cur, float **nxt, const float *r, lo
                         long long count, cudaStream_t s, long long *launches) {
     long long n = 0;
     while (n < count) {
-        const long long k = p->depth < count - n ? p->depth : count - n;
+        long long k = p->depth < count - n ? p->depth : count - n;
+        // the wavefront kernel exists for depths 2, 4 and 8: use the largest that fits
+        while (k > 1 && !wave_depth_supported((int)k)) --k;
         cudaError_t e;
         if (k == 1) {
             e = launch_sweep32(p, *cur, r, *nxt, p->w32[(first + n) % p->M_in], s);
         } else {
             float w[kTbMaxDepth];
             for (long long q = 0; q < k; ++q) w[q] = p->w32[(first + n + q) % p->M_in];
-            e = launch_sweep32_tb(p, *cur, r, *nxt, w, (int)k, s);
+            e = launch_sweep32_wave(p, *cur, r, *nxt, w, (int)k, s);
         }
         if (e != cudaSuccess) return e;
         float *t = *cur;

@@ -1,0 +1,217 @@
+// Wavefront temporal blocking of the FP32 inner sweep (sm_103a): K consecutive weighted
+// sweeps e <- e + w_n (L e - r) per HBM round trip, each with its own weight.
+//
+// A block of 256 threads owns a strip of 256 staged columns (one per thread: 256 - 2H output
+// columns plus an x-halo of H = r K on each side, r = stencil radius) and streams down a
+// block of rows.  Every iteration loads one new input row and pushes the K stages one row
+// further: stage s computes row y_in - r s from the rows y_in - r s - r .. y_in - r s + r of
+// stage s-1.  Each thread keeps its own column's values and horizontal pair sums of those
+// rows in registers, so only the newest row of each stage goes through shared memory (one
+// row buffer per stage, read by the next stage for the horizontal neighbours); the output
+// of stage K is written back.
+// There is no halo in y (rows are streamed, not tiled), so each block redoes only the H
+// columns on each side and the 2H warm-up rows of its row block.
+//
+// Boundaries: the grid is extended by the odd reflection the homogeneous Dirichlet boundary
+// implies (u and r odd about nodes 0 and N+1, which stay 0).  Every operation of the sweep
+// is an odd function of its inputs under round-to-nearest (sums, fma with constant
+// coefficients and weights), so the values computed on reflected rows and columns are the
+// exact negatives of their mirrors, and interior values equal those of one-sweep launches
+// bit for bit -- with no per-stage ghost refresh.
+//
+// Per node and stage: 2 (9-point) or 4 (17-point) shared-memory loads for the horizontal
+// pair sums, which each thread keeps, with its own column's values, in register windows
+// down the rows.  HBM traffic per update: about (4 e + 4 r + 4 e') / K bytes plus the halo.
+#include "cj_internal.h"
+#include "grid_dev.cuh"
+#include "stencil_dev.cuh"
+
+namespace {
+
+constexpr int kWaveW = 256;   // threads = staged columns per block
+constexpr int kWaveRows = 128; // output rows per block
+
+struct WaveWeights {
+    float w[kTbMaxDepth];
+};
+
+// Index and sign of node k of the odd extension of 1..N (nodes 0 and N+1 are zero: sign 0).
+__device__ __forceinline__ int fold(int k, int N, float &sign) {
+    if (k >= 1 && k <= N) {
+        sign = 1.0f;
+        return k;
+    }
+    const int P = 2 * (N + 1);
+    int m = k % P;
+    if (m < 0) m += P;
+    if (m == 0 || m == N + 1) {
+        sign = 0.0f;
+        return 1;
+    }
+    if (m <= N) {
+        sign = 1.0f;
+        return m;
+    }
+    sign = -1.0f;
+    return P - m;
+}
+
+// Value of e or r at node (ci, row y) of the odd extension (0 on the boundary rows/columns).
+__device__ __forceinline__ float load_ext(const float *__restrict__ a, const Grid &g, int ci, float csign,
+                                          int y) {
+    float rs;
+    const int ry = fold(y, g.Ny, rs);
+    const float s = rs * csign;
+    return s == 0.0f ? 0.0f : s * __ldg(a + g.idx(ci, ry));
+}
+
+template <int ST, int K>
+__global__ void __launch_bounds__(kWaveW) sweep_wave_kernel(const float *__restrict__ e,
+                                                            const float *__restrict__ r,
+                                                            float *__restrict__ out, Grid g,
+                                                            WaveWeights wt) {
+    constexpr int R = ST == 17 ? 2 : 1;
+    constexpr int H = R * K;
+    constexpr int TX = kWaveW - 2 * H;  // output columns per block
+    constexpr int RING = 2 * R + 1;     // rows in a register window
+    constexpr int RW = kWaveW + 2 * R;  // row buffer width (R pad columns each side)
+    constexpr int D = 4;                // rows of e and r loaded ahead
+    constexpr int RQ = H + 1;           // r of rows yin .. yin - H
+    __shared__ float ring[K][RW];
+
+    const int tid = threadIdx.x;
+    const int gi = (int)blockIdx.x * TX + 1 - H + tid;  // this thread's column
+    const int y0 = (int)blockIdx.y * kWaveRows + 1;      // first output row
+    const int Nx = g.Nx, Ny = g.Ny;
+    float csign;
+    const int ci = fold(gi, Nx, csign);  // column of the original grid this one mirrors
+    const bool col_bc = csign == 0.0f;
+
+    for (int k = tid; k < K * RW; k += kWaveW) (&ring[0][0])[k] = 0.0f;
+
+    // register windows of each stage's input (stage s reads stage s-1): own-column values
+    // and horizontal pair sums of the last 2R+1 rows (index 2R = newest)
+    float uw[K][RING], pw[K][RING], Pw[K][RING];
+#pragma unroll
+    for (int s = 0; s < K; ++s)
+#pragma unroll
+        for (int q = 0; q < RING; ++q) uw[s][q] = pw[s][q] = Pw[s][q] = 0.0f;
+    // loads in flight: eq[d], rq_in[d] hold rows yin + d; rl[j] holds r of row yin - j
+    float eq[D], rqi[D], rl[RQ];
+    const int ystart = y0 - H;
+#pragma unroll
+    for (int d = 0; d < D; ++d) {
+        eq[d] = load_ext(e, g, ci, csign, ystart + d);
+        rqi[d] = load_ext(r, g, ci, csign, ystart + d);
+    }
+#pragma unroll
+    for (int j = 0; j < RQ; ++j) rl[j] = 0.0f;
+
+    __syncthreads();
+    const int T = kWaveRows + 2 * H;
+    int tend = T;
+    if (ystart + tend - 1 > Ny + 1 + H) tend = Ny + 1 + H - ystart + 1;  // rows past the reflection
+    for (int t = 0; t < tend; ++t) {
+        const int yin = ystart + t;
+        // take this row's e and r from the queues and issue the loads of row yin + D
+        float v = eq[0];
+#pragma unroll
+        for (int j = RQ - 1; j > 0; --j) rl[j] = rl[j - 1];
+        rl[0] = rqi[0];
+#pragma unroll
+        for (int d = 0; d < D - 1; ++d) {
+            eq[d] = eq[d + 1];
+            rqi[d] = rqi[d + 1];
+        }
+        eq[D - 1] = load_ext(e, g, ci, csign, yin + D);
+        rqi[D - 1] = load_ext(r, g, ci, csign, yin + D);
+        if (col_bc) v = 0.0f;
+        ring[0][tid + R] = v;
+        __syncthreads();
+#pragma unroll
+        for (int s = 1; s <= K; ++s) {
+            // push stage s-1's newest row (row yin - R (s-1)) into stage s's window
+            const float *row = &ring[s - 1][tid + R];
+#pragma unroll
+            for (int q = 0; q < RING - 1; ++q) {
+                uw[s - 1][q] = uw[s - 1][q + 1];
+                pw[s - 1][q] = pw[s - 1][q + 1];
+                Pw[s - 1][q] = Pw[s - 1][q + 1];
+            }
+            uw[s - 1][RING - 1] = v;
+            pw[s - 1][RING - 1] = row[-1] + row[1];
+            if (R == 2) Pw[s - 1][RING - 1] = row[-2] + row[2];
+            // stage s: row y = yin - R s, window rows y-R .. y+R; r(y) = rl[R s]
+            const int y = yin - R * s;
+            float rsg;
+            fold(y, Ny, rsg);
+            float nv = 0.0f;
+            if (rsg != 0.0f && !col_bc) {
+                const float rk = rl[R * s];
+                const float *U = uw[s - 1], *p = pw[s - 1], *Q = Pw[s - 1];
+                const float uc = U[R];
+                float res;
+                if (ST == 5) {
+                    res = (p[1] + (U[0] + U[2])) + fmaf(-4.0f, uc, -rk);
+                } else if (ST == 9) {
+                    res = fmaf(4.0f / 6.0f, p[1] + (U[0] + U[2]),
+                               fmaf(1.0f / 6.0f, p[0] + p[2], fmaf(-20.0f / 6.0f, uc, -rk)));
+                } else {
+                    res = fmaf(64.0f / 72.0f, p[2] + (U[1] + U[3]),
+                               fmaf(-4.0f / 72.0f, Q[2] + (U[0] + U[4]),
+                                    fmaf(16.0f / 72.0f, p[1] + p[3],
+                                         fmaf(-1.0f / 72.0f, Q[0] + Q[4], fmaf(-300.0f / 72.0f, uc, -rk)))));
+                }
+                nv = fmaf(wt.w[s - 1], res, uc);
+            }
+            v = nv;
+            if (s < K) {
+                // the next stage reads this row; the row it replaces was last read before
+                // the barrier that followed this iteration's input load
+                ring[s][tid + R] = v;
+                __syncthreads();
+            }
+        }
+        // stage K produced row yin - H
+        const int yo = yin - H;
+        if (yo >= y0 && yo < y0 + kWaveRows && yo <= Ny && tid >= H && tid < kWaveW - H && gi >= 1 &&
+            gi <= Nx)
+            store_node<R, float>(out, g, gi, yo, v);
+    }
+}
+
+template <int ST, int K>
+cudaError_t launch_wave_k(const Grid &g, const float *e, const float *r, float *out,
+                          const float *w, cudaStream_t s) {
+    constexpr int R = ST == 17 ? 2 : 1;
+    constexpr int TX = kWaveW - 2 * R * K;
+    WaveWeights wt{};
+    for (int k = 0; k < K; ++k) wt.w[k] = w[k];
+    const dim3 grid((g.Nx + TX - 1) / TX, (g.Ny + kWaveRows - 1) / kWaveRows);
+    sweep_wave_kernel<ST, K><<<grid, kWaveW, 0, s>>>(e, r, out, g, wt);
+    return cudaGetLastError();
+}
+
+template <int ST>
+cudaError_t launch_wave_st(const Grid &g, const float *e, const float *r, float *out,
+                           const float *w, int k, cudaStream_t s) {
+    switch (k) {
+        case 2: return launch_wave_k<ST, 2>(g, e, r, out, w, s);
+        case 4: return launch_wave_k<ST, 4>(g, e, r, out, w, s);
+        case 8: return launch_wave_k<ST, 8>(g, e, r, out, w, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace
+
+int wave_depth_supported(int k) { return k == 2 || k == 4 || k == 8; }
+
+cudaError_t launch_sweep32_wave(const cj_plan *p, const float *e, const float *r, float *out,
+                                const float *w, int k, cudaStream_t s) {
+    switch (p->st) {
+        case 5: return launch_wave_st<5>(p->g32, e, r, out, w, k, s);
+        case 9: return launch_wave_st<9>(p->g32, e, r, out, w, k, s);
+        default: return launch_wave_st<17>(p->g32, e, r, out, w, k, s);
+    }
+}

@@ -1,6 +1,7 @@
 """Runs a fixed number of CJM sweeps through the C ABI, for kernel profiling (ncu).
 
     python -m paper_1705_00103_gb300.profile_sweeps --stencil 9 --n 4096 --precision fp64 --count 3
+    python -m paper_1705_00103_gb300.profile_sweeps --stencil 9 --precision fp32 --depth 8 --count 16
 
 Inputs are zero grids of the given size (the sweep's cost does not depend on the values);
 three FP64 grids of 4096^2 (400 MB) exceed the 129 MB L2.
@@ -20,6 +21,7 @@ def main(argv=None):
     ap.add_argument("--n", type=int, default=4096)
     ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32"])
     ap.add_argument("--count", type=int, default=3)
+    ap.add_argument("--depth", type=int, default=1, help="FP32 sweeps per launch (temporal blocking)")
     a = ap.parse_args(argv)
     build.build()
     if a.precision == "fp64":
@@ -28,7 +30,7 @@ def main(argv=None):
             u = torch.zeros_like(f)
             cj.cj_sweeps(p.handle, f, u, 0, a.count)
     else:
-        with cj.Plan(a.n, a.n, a.stencil, 1e-10, precision=cj.CJ_FP32_INNER) as p:
+        with cj.Plan(a.n, a.n, a.stencil, 1e-10, precision=cj.CJ_FP32_INNER, temporal_depth=a.depth) as p:
             r = torch.zeros((a.n, a.n), dtype=torch.float32, device="cuda")
             e = torch.zeros_like(r)
             cj.cj_sweeps_f32(p.handle, r, e, 0, a.count)
