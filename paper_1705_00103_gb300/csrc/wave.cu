@@ -29,7 +29,6 @@
 namespace {
 
 constexpr int kWaveW = 256;   // threads = staged columns per block
-constexpr int kWaveRows = 128; // output rows per block
 
 struct WaveWeights {
     float w[kTbMaxDepth];
@@ -56,6 +55,14 @@ __device__ __forceinline__ int fold(int k, int N, float &sign) {
     return P - m;
 }
 
+// True when row y of the odd extension is a Dirichlet row (a node 0 or N+1 image).
+__device__ __forceinline__ bool boundary_row(int y, int N) {
+    if (y >= 1 && y <= N) return false;
+    float sg;
+    fold(y, N, sg);
+    return sg == 0.0f;
+}
+
 // Value of e or r at node (ci, row y) of the odd extension (0 on the boundary rows/columns).
 __device__ __forceinline__ float load_ext(const float *__restrict__ a, const Grid &g, int ci, float csign,
                                           int y) {
@@ -69,25 +76,27 @@ template <int ST, int K>
 __global__ void __launch_bounds__(kWaveW) sweep_wave_kernel(const float *__restrict__ e,
                                                             const float *__restrict__ r,
                                                             float *__restrict__ out, Grid g,
-                                                            WaveWeights wt) {
+                                                            WaveWeights wt, int rows) {
     constexpr int R = ST == 17 ? 2 : 1;
     constexpr int H = R * K;
     constexpr int TX = kWaveW - 2 * H;  // output columns per block
     constexpr int RING = 2 * R + 1;     // rows in a register window
     constexpr int RW = kWaveW + 2 * R;  // row buffer width (R pad columns each side)
-    constexpr int D = 4;                // rows of e and r loaded ahead
-    constexpr int RQ = H + 1;           // r of rows yin .. yin - H
+    constexpr int D = RING;             // rows of e and r loaded ahead
+    constexpr int RQ = H + 1;           // r of rows yin .. yin - H, one slot per row
     __shared__ float ring[K][RW];
+    __shared__ float rline[RQ][kWaveW];
 
     const int tid = threadIdx.x;
     const int gi = (int)blockIdx.x * TX + 1 - H + tid;  // this thread's column
-    const int y0 = (int)blockIdx.y * kWaveRows + 1;      // first output row
+    const int y0 = (int)blockIdx.y * rows + 1;           // first output row
     const int Nx = g.Nx, Ny = g.Ny;
     float csign;
     const int ci = fold(gi, Nx, csign);  // column of the original grid this one mirrors
     const bool col_bc = csign == 0.0f;
 
     for (int k = tid; k < K * RW; k += kWaveW) (&ring[0][0])[k] = 0.0f;
+    for (int k = 0; k < RQ; ++k) rline[k][tid] = 0.0f;
 
     // register windows of each stage's input (stage s reads stage s-1): own-column values
     // and horizontal pair sums of the last 2R+1 rows (index 2R = newest)
@@ -96,36 +105,32 @@ __global__ void __launch_bounds__(kWaveW) sweep_wave_kernel(const float *__restr
     for (int s = 0; s < K; ++s)
 #pragma unroll
         for (int q = 0; q < RING; ++q) uw[s][q] = pw[s][q] = Pw[s][q] = 0.0f;
-    // loads in flight: eq[d], rq_in[d] hold rows yin + d; rl[j] holds r of row yin - j
-    float eq[D], rqi[D], rl[RQ];
+    // loads in flight: eq[d], rq[d] hold rows yin + d
+    float eq[D], rq[D];
     const int ystart = y0 - H;
 #pragma unroll
     for (int d = 0; d < D; ++d) {
         eq[d] = load_ext(e, g, ci, csign, ystart + d);
-        rqi[d] = load_ext(r, g, ci, csign, ystart + d);
+        rq[d] = load_ext(r, g, ci, csign, ystart + d);
     }
-#pragma unroll
-    for (int j = 0; j < RQ; ++j) rl[j] = 0.0f;
 
     __syncthreads();
-    const int T = kWaveRows + 2 * H;
-    int tend = T;
-    if (ystart + tend - 1 > Ny + 1 + H) tend = Ny + 1 + H - ystart + 1;  // rows past the reflection
+    int tend = rows + 2 * H;
+    if (ystart + tend - 1 > Ny + H) tend = Ny + H - ystart + 1;  // rows past the last output's needs
+    int slot = 0;                                                // rline slot of row yin
+    // unrolled by the window length, so the window shifts become register renames
+#pragma unroll RING
     for (int t = 0; t < tend; ++t) {
         const int yin = ystart + t;
-        // take this row's e and r from the queues and issue the loads of row yin + D
-        float v = eq[0];
-#pragma unroll
-        for (int j = RQ - 1; j > 0; --j) rl[j] = rl[j - 1];
-        rl[0] = rqi[0];
+        float v = col_bc ? 0.0f : eq[0];
+        rline[slot][tid] = rq[0];
 #pragma unroll
         for (int d = 0; d < D - 1; ++d) {
             eq[d] = eq[d + 1];
-            rqi[d] = rqi[d + 1];
+            rq[d] = rq[d + 1];
         }
         eq[D - 1] = load_ext(e, g, ci, csign, yin + D);
-        rqi[D - 1] = load_ext(r, g, ci, csign, yin + D);
-        if (col_bc) v = 0.0f;
+        rq[D - 1] = load_ext(r, g, ci, csign, yin + D);
         ring[0][tid + R] = v;
         __syncthreads();
 #pragma unroll
@@ -141,13 +146,14 @@ __global__ void __launch_bounds__(kWaveW) sweep_wave_kernel(const float *__restr
             uw[s - 1][RING - 1] = v;
             pw[s - 1][RING - 1] = row[-1] + row[1];
             if (R == 2) Pw[s - 1][RING - 1] = row[-2] + row[2];
-            // stage s: row y = yin - R s, window rows y-R .. y+R; r(y) = rl[R s]
+            // stage s: row y = yin - R s, window rows y-R .. y+R; r(y) from the r line
             const int y = yin - R * s;
-            float rsg;
-            fold(y, Ny, rsg);
+            const bool bc_row = boundary_row(y, Ny);
             float nv = 0.0f;
-            if (rsg != 0.0f && !col_bc) {
-                const float rk = rl[R * s];
+            if (!bc_row && !col_bc) {
+                int rs = slot - R * s;
+                if (rs < 0) rs += RQ;
+                const float rk = rline[rs][tid];
                 const float *U = uw[s - 1], *p = pw[s - 1], *Q = Pw[s - 1];
                 const float uc = U[R];
                 float res;
@@ -174,10 +180,34 @@ __global__ void __launch_bounds__(kWaveW) sweep_wave_kernel(const float *__restr
         }
         // stage K produced row yin - H
         const int yo = yin - H;
-        if (yo >= y0 && yo < y0 + kWaveRows && yo <= Ny && tid >= H && tid < kWaveW - H && gi >= 1 &&
+        if (yo >= y0 && yo < y0 + rows && yo <= Ny && tid >= H && tid < kWaveW - H && gi >= 1 &&
             gi <= Nx)
             store_node<R, float>(out, g, gi, yo, v);
+        slot = slot + 1 == RQ ? 0 : slot + 1;
     }
+}
+
+// Rows per block so that the grid is one wave of resident blocks (at least 2H + 1, so the
+// warm-up rows stay a minority).
+template <int ST, int K>
+int wave_rows(const Grid &g, int nstrips) {
+    static int resident = 0;
+    if (resident == 0) {
+        int dev = 0, sms = 152, per_sm = 1;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sweep_wave_kernel<ST, K>, kWaveW, 0) !=
+                cudaSuccess ||
+            per_sm < 1)
+            per_sm = 1;
+        resident = sms * per_sm;
+    }
+    constexpr int H = (ST == 17 ? 2 : 1) * K;
+    int nby = resident / nstrips;
+    if (nby < 1) nby = 1;
+    int rows = (g.Ny + nby - 1) / nby;
+    if (rows < 2 * H + 1) rows = 2 * H + 1;
+    return rows;
 }
 
 template <int ST, int K>
@@ -187,8 +217,10 @@ cudaError_t launch_wave_k(const Grid &g, const float *e, const float *r, float *
     constexpr int TX = kWaveW - 2 * R * K;
     WaveWeights wt{};
     for (int k = 0; k < K; ++k) wt.w[k] = w[k];
-    const dim3 grid((g.Nx + TX - 1) / TX, (g.Ny + kWaveRows - 1) / kWaveRows);
-    sweep_wave_kernel<ST, K><<<grid, kWaveW, 0, s>>>(e, r, out, g, wt);
+    const int nstrips = (g.Nx + TX - 1) / TX;
+    const int rows = wave_rows<ST, K>(g, nstrips);
+    const dim3 grid(nstrips, (g.Ny + rows - 1) / rows);
+    sweep_wave_kernel<ST, K><<<grid, kWaveW, 0, s>>>(e, r, out, g, wt, rows);
     return cudaGetLastError();
 }
 

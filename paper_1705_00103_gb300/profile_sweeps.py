@@ -22,19 +22,40 @@ def main(argv=None):
     ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32"])
     ap.add_argument("--count", type=int, default=3)
     ap.add_argument("--depth", type=int, default=1, help="FP32 sweeps per launch (temporal blocking)")
+    ap.add_argument("--time", type=int, default=0,
+                    help="also time this many sweeps with CUDA events and print us per sweep")
     a = ap.parse_args(argv)
     build.build()
+
+    def run(fn):
+        fn(a.count)
+        torch.cuda.synchronize()
+        if a.time > 0:
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            fn(a.time)
+            e1.record()
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1)
+            e0.record()
+            fn(0)
+            e1.record()
+            torch.cuda.synchronize()
+            per = (ms - e0.elapsed_time(e1)) / a.time
+            print("stencil %d %s depth %d %dx%d: %.2f us per sweep, %.1f Gupdates/s"
+                  % (a.stencil, a.precision, a.depth, a.n, a.n, per * 1e3, a.n * a.n / per / 1e6))
+
     if a.precision == "fp64":
         with cj.Plan(a.n, a.n, a.stencil, 1e-10) as p:
             f = torch.zeros((a.n, a.n), dtype=torch.float64, device="cuda")
             u = torch.zeros_like(f)
-            cj.cj_sweeps(p.handle, f, u, 0, a.count)
+            run(lambda c: cj.cj_sweeps(p.handle, f, u, 0, c))
     else:
         with cj.Plan(a.n, a.n, a.stencil, 1e-10, precision=cj.CJ_FP32_INNER, temporal_depth=a.depth) as p:
             r = torch.zeros((a.n, a.n), dtype=torch.float32, device="cuda")
             e = torch.zeros_like(r)
-            cj.cj_sweeps_f32(p.handle, r, e, 0, a.count)
-    torch.cuda.synchronize()
+            run(lambda c: cj.cj_sweeps_f32(p.handle, r, e, 0, c))
     print("ok")
 
 
