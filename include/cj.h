@@ -174,6 +174,17 @@ cj_status cj_sweeps_f32(cj_plan *plan, const float *r, long long ld_r, float *e,
                         long long first, long long count, void *stream);
 
 /*
+ * cj_autotune_depth -- measure the FP32 sweep at temporal depths 1, 2, 4 and 8 on an Nx x Ny
+ * grid (`sweeps` >= 8 sweeps each, CUDA events on `stream`), and record the fastest for the
+ * stencil and size class (grids whose node counts are within a factor 4 share a class) in a
+ * per-process table; FP32-inner plans created afterwards with temporal_depth = 0 use it.
+ * *best_depth (may be NULL) receives the winner, gupd[4] (may be NULL) the measured
+ * grid-point updates per second (1e9) at depths 1, 2, 4, 8.  Allocates a temporary plan.
+ */
+cj_status cj_autotune_depth(int Nx, int Ny, cj_stencil st, int sweeps, void *stream, int *best_depth,
+                            double *gupd);
+
+/*
  * cj_solution_lo -- for a CJ_FP32_INNER_DD plan, the low part u_lo of the last solve's
  * double-FP64 solution (cj_solve returned u = u_hi, with |u_lo| <= ulp(u_hi)/2); the
  * relative residual cj_result reported is that of u_hi + u_lo.  u_lo: device, Ny x ld

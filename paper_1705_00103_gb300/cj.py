@@ -106,6 +106,9 @@ def _lib():
         L.cj_sweeps.restype = ctypes.c_int
         L.cj_sweeps_f32.argtypes = [_vp, _vp, _ll, _vp, _ll, _ll, _ll, _vp]
         L.cj_sweeps_f32.restype = ctypes.c_int
+        L.cj_autotune_depth.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, _vp,
+                                        ctypes.POINTER(ctypes.c_int), _dp]
+        L.cj_autotune_depth.restype = ctypes.c_int
         L.cj_solution_lo.argtypes = [_vp, _vp, _ll, _vp]
         L.cj_solution_lo.restype = ctypes.c_int
         L.cj_residual_noalloc.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, _vp, _ll, _vp,
@@ -238,6 +241,17 @@ def cj_sweeps_f32(plan, r, e, first: int, count: int, stream=None) -> None:
     rc = _lib().cj_sweeps_f32(plan, rp, ldr, ep, lde, first, count, _stream(stream))
     if rc != CJ_OK:
         raise CJError(rc, "cj_sweeps_f32")
+
+
+def cj_autotune_depth(Nx: int, Ny: int, st: int, sweeps: int = 64, stream=None) -> dict:
+    """Time FP32 sweeps at temporal depths 1, 2, 4, 8 and record the fastest for this
+    stencil and size class; returns {"best": depth, "gupd": {depth: rate}}."""
+    best = ctypes.c_int()
+    rates = (ctypes.c_double * 4)()
+    rc = _lib().cj_autotune_depth(Nx, Ny, st, sweeps, _stream(stream), ctypes.byref(best), rates)
+    if rc != CJ_OK:
+        raise CJError(rc, "cj_autotune_depth")
+    return {"best": best.value, "gupd": dict(zip((1, 2, 4, 8), list(rates)))}
 
 
 def cj_solution_lo(plan, u_lo, stream=None) -> None:

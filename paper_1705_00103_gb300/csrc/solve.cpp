@@ -6,6 +6,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <new>
 
 #include "cj_internal.h"
@@ -13,6 +14,28 @@
 namespace {
 
 thread_local char g_err[256] = "";
+
+// Autotuned FP32 temporal depth per (stencil, size class); size class = floor(log2(Nx*Ny)/2),
+// i.e. grids within a factor 2 of each other per side share a class.  0 = not tuned.
+std::mutex g_tune_mu;
+int g_tuned_depth[3][32] = {};
+
+int stencil_slot(int st) { return st == 5 ? 0 : st == 9 ? 1 : 2; }
+
+int size_class(int Nx, int Ny) {
+    long long n = (long long)Nx * Ny;
+    int c = 0;
+    while (n > 3) {
+        n >>= 2;
+        ++c;
+    }
+    return c < 32 ? c : 31;
+}
+
+int tuned_depth(int st, int Nx, int Ny) {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    return g_tuned_depth[stencil_slot(st)][size_class(Nx, Ny)];
+}
 
 const double kEps = 1.1102230246251565e-16;  // 2^-53
 
@@ -375,7 +398,9 @@ cj_status cj_plan_create(int Nx, int Ny, cj_stencil st, cj_bc bc, double tol,
         // default FP32 temporal depth, from measurements at 4096^2 (cj_sweeps_f32, Gupd/s at
         // depth 1 / 4): 5-point 404 / 472, 9-point 341 / 388, 17-point 272 / 177; small
         // grids have too few strips for the wavefront kernel, so they keep depth 1
+        const int tuned = tuned_depth(st, Nx, Ny);
         p->depth = o.temporal_depth ? o.temporal_depth
+                   : tuned          ? tuned
                                     : (st != CJ_ST17 && (long long)Nx * Ny >= (1LL << 20) ? 4 : 1);
         long long unit = p->precision != CJ_FP64 ? p->M_in : p->M;
         p->max_sweeps = o.max_sweeps ? o.max_sweeps : 64 * unit;
@@ -507,6 +532,63 @@ cj_status cj_sweeps_f32(cj_plan *p, const float *r, long long ldr, float *e, lon
     long long launches = 0;
     CJ_TRY(fp32_sweeps(p, &cur, &nxt, p->rt, first, count, s, &launches), "sweep32");
     CJ_TRY(launch_export32(p, cur, e, lde, s), "export32");
+    return CJ_OK;
+}
+
+cj_status cj_autotune_depth(int Nx, int Ny, cj_stencil st, int sweeps, void *stream,
+                            int *best_depth, double *gupd) {
+    if (Nx < 1 || Ny < 1 || sweeps < 8) return CJ_ERR_INVALID_ARG;
+    if (st != CJ_ST5 && st != CJ_ST9 && st != CJ_ST17) return CJ_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    const int depths[4] = {1, 2, 4, 8};
+    double rate[4] = {0, 0, 0, 0};
+    int best = 1;
+    cudaEvent_t e0, e1;
+    CJ_TRY(cudaEventCreate(&e0), "autotune event");
+    CJ_TRY(cudaEventCreate(&e1), "autotune event");
+    for (int k = 0; k < 4; ++k) {
+        cj_options o{};
+        o.precision = CJ_FP32_INNER;
+        o.inner_cycle = 64;
+        o.temporal_depth = depths[k];
+        cj_plan *p = nullptr;
+        cj_status st2 = cj_plan_create(Nx, Ny, st, CJ_BC_DIRICHLET0, 1e-6, &o, &p);
+        if (st2 != CJ_OK) {
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+            return st2;
+        }
+        float *cur = p->e0, *nxt = p->e1;
+        long long launches = 0;
+        cudaError_t err = fp32_sweeps(p, &cur, &nxt, p->rt, 0, 8, s, &launches);  // warm-up
+        if (err == cudaSuccess) err = cudaEventRecord(e0, s);
+        if (err == cudaSuccess) err = fp32_sweeps(p, &cur, &nxt, p->rt, 0, sweeps, s, &launches);
+        if (err == cudaSuccess) err = cudaEventRecord(e1, s);
+        if (err == cudaSuccess) err = cudaEventSynchronize(e1);
+        float ms = 0.0f;
+        if (err == cudaSuccess) err = cudaEventElapsedTime(&ms, e0, e1);
+        cj_plan_destroy(p);
+        if (err != cudaSuccess) {
+            set_cuda_error(err, "autotune");
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+            return CJ_ERR_CUDA;
+        }
+        rate[k] = (double)Nx * Ny * sweeps / (ms * 1e-3) / 1e9;
+    }
+    int kbest = 0;  // the fastest depth; the shallower one on a tie
+    for (int k = 1; k < 4; ++k)
+        if (rate[k] > rate[kbest]) kbest = k;
+    best = depths[kbest];
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        g_tuned_depth[stencil_slot(st)][size_class(Nx, Ny)] = best;
+    }
+    if (best_depth) *best_depth = best;
+    if (gupd)
+        for (int k = 0; k < 4; ++k) gupd[k] = rate[k];
     return CJ_OK;
 }
 

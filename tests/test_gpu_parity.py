@@ -339,3 +339,23 @@ def test_mixed_solve_with_temporal_blocking_matches_oracle(cj, torch, st):
         res = cj.cj_solve(p.handle, dev(torch, f), ud)
     assert res["sweeps"] == ref["sweeps"] and res["cycles"] == ref["outer"]
     np.testing.assert_array_equal(ud.cpu().numpy(), ref["u"])
+
+
+# ----------------------------------------------------------------- autotuner, history
+
+def test_autotune_depth_records_the_fastest(cj, torch):
+    out = cj.cj_autotune_depth(1024, 1024, 9, sweeps=32)
+    rates = out["gupd"]
+    assert out["best"] in (1, 2, 4, 8) and all(v > 0 for v in rates.values())
+    assert rates[out["best"]] == max(rates.values())
+
+
+def test_solve_history_records_every_residual_test(cj, torch):
+    Nx, Ny, st = 96, 80, 9
+    f = workloads.smooth_random_rhs(Nx, Ny, 21)
+    with cj.Plan(Nx, Ny, st, 1e-10, precision=cj.CJ_FP32_INNER_DD, inner_cycle=64) as p:
+        ud = torch.zeros((Ny, Nx), dtype=torch.float64, device="cuda")
+        res = cj.cj_solve_history(p.handle, dev(torch, f), ud)
+    h = res["history"]
+    assert len(h) == res["cycles"] + 1 and h[0] == pytest.approx(1.0) and h[-1] == res["rel_res_l2"]
+    assert res["rc"] == cj.CJ_OK and h[-1] <= 1e-10
