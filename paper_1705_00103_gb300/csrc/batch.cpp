@@ -91,6 +91,7 @@ class Engine {
 
     void destroy() {
         if (!s_) return;
+        cudaSetDevice(dev_);  // the engine's device, whichever thread tears it down
         cudaStreamSynchronize(s_);
         for (int q = 0; q < max_slots_; ++q)
             if (mem_[q].base) cudaFree(mem_[q].base);

@@ -396,7 +396,7 @@ cj_status cj_plan_create(int Nx, int Ny, cj_stencil st, cj_bc bc, double tol,
             for (long long k = 0; k < p->M_in; ++k) p->w32[k] = (float)wi[k];
         }
         // default FP32 temporal depth, from measurements at 4096^2 (cj_sweeps_f32, Gupd/s at
-        // depth 1 / 4): 5-point 404 / 472, 9-point 341 / 388, 17-point 272 / 177; small
+        // depth 1 / 4): 5-point 404 / 468, 9-point 341 / 469, 17-point 272 / 163; small
         // grids have too few strips for the wavefront kernel, so they keep depth 1
         const int tuned = tuned_depth(st, Nx, Ny);
         p->depth = o.temporal_depth ? o.temporal_depth

@@ -1,7 +1,7 @@
 // Wavefront temporal blocking of the FP32 inner sweep (sm_103a): K consecutive weighted
 // sweeps e <- e + w_n (L e - r) per HBM round trip, each with its own weight.
 //
-// A block of 256 threads owns a strip of 256 staged columns (one per thread: 256 - 2H output
+// A block of kWaveW threads owns a strip of kWaveW staged columns (one per thread: kWaveW - 2H output
 // columns plus an x-halo of H = r K on each side, r = stencil radius) and streams down a
 // block of rows.  Every iteration loads one new input row and pushes the K stages one row
 // further: stage s computes row y_in - r s from the rows y_in - r s - r .. y_in - r s + r of
@@ -28,7 +28,7 @@
 
 namespace {
 
-constexpr int kWaveW = 256;   // threads = staged columns per block
+constexpr int kWaveW = 128;   // threads = staged columns per block (measured best of 128, 256, 512)
 
 struct WaveWeights {
     float w[kTbMaxDepth];
