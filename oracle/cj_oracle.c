@@ -48,6 +48,10 @@
  *      FP64 defect-correction loop r = b - L u, rt = (float) r, one FP32 CJM cycle of
  *      length M_in on L e = rt from e = 0 with w32_n = (float)(omega_n / c), then
  *      u <- u + (double) e.  The stop test is the FP64 residual of R8.
+ *   R14 FP32 evaluation (not in the paper): the FP32 inner sweep evaluates L e - r in
+ *      difference form, sum_k c_k (e_k - e_C) - r, grouped like R9 without a centre term;
+ *      on a 8192^2 grid the pair-sum form loses ~40 % of the lowest mode's L e in FP32, the
+ *      difference form keeps it to a few FP32 ulps.
  *   R11 double-FP64 outer (not in the paper): as R10, but the solution is the unevaluated
  *      sum u_hi + u_lo of two FP64 arrays and the defect is evaluated to about twice FP64
  *      precision: D (L u_hi - b), D = 1, 6 or 72 the stencil's denominator, is a sum of
@@ -338,35 +342,29 @@ static float at32(const float *u, int Nx, int Ny, int i, int j) {
     return s * u[(size_t)(j - 1) * Nx + (i - 1)];
 }
 
-/* r = (L e)(i, j) - rk in FP32, same grouping as resid_at; the coefficients are the
- * FP32 quotients (e.g. 4.0f/6.0f). */
+/* r = (L e)(i, j) - rk in FP32, in difference form (reading R14): every neighbour enters as
+ * its difference from the centre, (e_k - e_C), which is exact in FP32 whenever the two are
+ * within a factor 2 of each other (Sterbenz), as they are for the smooth low modes the
+ * solver is slowest on; L e = sum_k c_k (e_k - e_C) because the stencil coefficients sum
+ * to zero.  Groups as in resid_at (pairs, axis and diagonal groups), coefficients are the
+ * FP32 quotients (e.g. 4.0f/6.0f); no centre term. */
 static float resid_at32(int st, const float *u, int Nx, int Ny, int i, int j, float rk) {
     float uC = at32(u, Nx, Ny, i, j);
-    float v1 = at32(u, Nx, Ny, i, j - 1) + at32(u, Nx, Ny, i, j + 1);
-    float p0 = at32(u, Nx, Ny, i - 1, j) + at32(u, Nx, Ny, i + 1, j);
-    if (st == 5) {
-        float a = p0 + v1;
-        return a + fmaf(-4.0f, uC, -rk);
-    }
-    float pm = at32(u, Nx, Ny, i - 1, j - 1) + at32(u, Nx, Ny, i + 1, j - 1);
-    float pp = at32(u, Nx, Ny, i - 1, j + 1) + at32(u, Nx, Ny, i + 1, j + 1);
-    if (st == 9) {
-        float a = p0 + v1;
-        float d = pm + pp;
-        return fmaf(4.0f / 6.0f, a, fmaf(1.0f / 6.0f, d, fmaf(-20.0f / 6.0f, uC, -rk)));
-    }
-    float v2 = at32(u, Nx, Ny, i, j - 2) + at32(u, Nx, Ny, i, j + 2);
-    float P0 = at32(u, Nx, Ny, i - 2, j) + at32(u, Nx, Ny, i + 2, j);
-    float Pm = at32(u, Nx, Ny, i - 2, j - 2) + at32(u, Nx, Ny, i + 2, j - 2);
-    float Pp = at32(u, Nx, Ny, i - 2, j + 2) + at32(u, Nx, Ny, i + 2, j + 2);
-    float a1 = p0 + v1;
-    float a2 = P0 + v2;
-    float d1 = pm + pp;
-    float d2 = Pm + Pp;
-    return fmaf(64.0f / 72.0f, a1,
-                fmaf(-4.0f / 72.0f, a2,
-                     fmaf(16.0f / 72.0f, d1,
-                          fmaf(-1.0f / 72.0f, d2, fmaf(-300.0f / 72.0f, uC, -rk)))));
+#define D32(di, dj) (at32(u, Nx, Ny, i + (di), j + (dj)) - uC)
+    float v1 = D32(0, -1) + D32(0, 1);
+    float p0 = D32(-1, 0) + D32(1, 0);
+    if (st == 5) return (p0 + v1) - rk;
+    float pm = D32(-1, -1) + D32(1, -1);
+    float pp = D32(-1, 1) + D32(1, 1);
+    if (st == 9) return fmaf(4.0f / 6.0f, p0 + v1, fmaf(1.0f / 6.0f, pm + pp, -rk));
+    float v2 = D32(0, -2) + D32(0, 2);
+    float P0 = D32(-2, 0) + D32(2, 0);
+    float Pm = D32(-2, -2) + D32(2, -2);
+    float Pp = D32(-2, 2) + D32(2, 2);
+#undef D32
+    return fmaf(64.0f / 72.0f, p0 + v1,
+                fmaf(-4.0f / 72.0f, P0 + v2,
+                     fmaf(16.0f / 72.0f, pm + pp, fmaf(-1.0f / 72.0f, Pm + Pp, -rk))));
 }
 
 /* One FP32 weighted sweep e_out = e + w (L e - r). */

@@ -213,7 +213,7 @@ __device__ __forceinline__ void sweep_tile(SlotDev &S, const TileRef &T, int k, 
                 store_node<(ST == 17 ? 2 : 1), float>(out, *g, i, j, fmaf(w, r, uc));
             }
         } op{eout, &S.g32, i, S.w32[S.counter]};
-        march_prefetch<ST, float>(ein, S.rt, S.g32, i, T.j0, T.j1, 1.0f, op);
+        march32<ST, true>(ein, S.rt, S.g32, i, T.j0, T.j1, op);
     } else {
         float w[kTbMaxDepth];
         for (int s = 0; s < k; ++s) w[s] = S.w32[S.counter + s];

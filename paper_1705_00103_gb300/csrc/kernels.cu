@@ -39,7 +39,8 @@ struct SweepOp {
     }
 };
 
-// One weighted sweep: out = u + w (L u - b).
+// One weighted sweep: out = u + w (L u - b).  FP64 in the pair-sum order above; FP32 in the
+// difference form (march32), which keeps the smooth modes' digits on fine grids.
 template <int ST, typename T>
 __global__ void __launch_bounds__(kBX) sweep_kernel(const T *__restrict__ u,
                                                     const T *__restrict__ b, T *__restrict__ out,
@@ -49,7 +50,10 @@ __global__ void __launch_bounds__(kBX) sweep_kernel(const T *__restrict__ u,
     const int j1 = min(j0 + ty - 1, g.Ny);
     if (i > g.Nx) return;
     SweepOp<ST, T> op{out, &g, i, w};
-    march<ST, T>(u, b, g, i, j0, j1, one, op);
+    if constexpr (sizeof(T) == 4)
+        march32<ST, false>(u, b, g, i, j0, j1, op);
+    else
+        march<ST, T>(u, b, g, i, j0, j1, one, op);
 }
 
 struct ResidOp {

@@ -255,6 +255,81 @@ __device__ __forceinline__ void march_prefetch(const T *__restrict__ u, const T 
     }
 }
 
+// FP32 residual in difference form, L e - rk = sum_k c_k (e_k - e_C) - rk: every neighbour
+// enters as its (for smooth e, exact) difference from the centre, so the smooth low modes
+// keep their digits on fine grids where the neighbour sums would cancel against the centre
+// term.  N(di, dj) returns the neighbour at offset (di, dj); groups as in the FP64 order.
+template <int ST, class F>
+__device__ __forceinline__ float resid_diff32(F N, float uC, float rk) {
+    const float v1 = (N(0, -1) - uC) + (N(0, 1) - uC);
+    const float p0 = (N(-1, 0) - uC) + (N(1, 0) - uC);
+    if (ST == 5) return (p0 + v1) - rk;
+    const float pm = (N(-1, -1) - uC) + (N(1, -1) - uC);
+    const float pp = (N(-1, 1) - uC) + (N(1, 1) - uC);
+    if (ST == 9) return fmaf(4.0f / 6.0f, p0 + v1, fmaf(1.0f / 6.0f, pm + pp, -rk));
+    const float v2 = (N(0, -2) - uC) + (N(0, 2) - uC);
+    const float P0 = (N(-2, 0) - uC) + (N(2, 0) - uC);
+    const float Pm = (N(-2, -2) - uC) + (N(2, -2) - uC);
+    const float Pp = (N(-2, 2) - uC) + (N(2, 2) - uC);
+    return fmaf(64.0f / 72.0f, p0 + v1,
+                fmaf(-4.0f / 72.0f, P0 + v2,
+                     fmaf(16.0f / 72.0f, pm + pp, fmaf(-1.0f / 72.0f, Pm + Pp, -rk))));
+}
+
+// FP32 y-march in difference form: column i, rows j0..j1, op(j, r, e(i,j)) with
+// r = (L e - b)(i, j).  Each thread keeps the (2R+1) x (2R+1) neighbourhood of its column
+// in registers and loads one new row of 2R+1 values (and b) per step; with PF the next
+// row's loads are issued one step ahead (the padded layout always holds the rows touched).
+template <int ST, bool PF, class Op>
+__device__ __forceinline__ void march32(const float *__restrict__ u, const float *__restrict__ b,
+                                        const Grid &g, int i, int j0, int j1, Op &op) {
+    constexpr int R = ST == 17 ? 2 : 1, W = 2 * R + 1;
+    const long long P = g.pitch;
+    const float *col = u + g.idx(i, 0);  // node (i, 0); row k at col + k * P
+    const float *bcol = b + g.idx(i, 0);
+    float win[W][W];  // win[row offset + R][column offset + R] around (i, j)
+#pragma unroll
+    for (int dy = -R; dy < R; ++dy) {
+        const float *row = col + (long long)(j0 + dy) * P;
+#pragma unroll
+        for (int dx = -R; dx <= R; ++dx) win[dy + R + 1][dx + R] = __ldg(row + dx);
+    }
+    float nxt[W], nb = 0.0f;
+    if (PF) {
+        const float *row = col + (long long)(j0 + R) * P;
+#pragma unroll
+        for (int dx = -R; dx <= R; ++dx) nxt[dx + R] = __ldg(row + dx);
+        nb = __ldg(bcol + (long long)j0 * P);
+    }
+    for (int j = j0; j <= j1; ++j) {
+        // shift the window up one row and bring in row j + R
+#pragma unroll
+        for (int q = 0; q < W - 1; ++q)
+#pragma unroll
+            for (int dx = 0; dx < W; ++dx) win[q][dx] = win[q + 1][dx];
+        float bk;
+        if (PF) {
+#pragma unroll
+            for (int dx = 0; dx < W; ++dx) win[W - 1][dx] = nxt[dx];
+            bk = nb;
+            int jn = j + R + 1;
+            if (jn > g.Ny + 2) jn = g.Ny + 2;  // clamped; that load is never used
+            const float *row = col + (long long)jn * P;
+#pragma unroll
+            for (int dx = -R; dx <= R; ++dx) nxt[dx + R] = __ldg(row + dx);
+            nb = __ldg(bcol + (long long)(j + 1) * P);
+        } else {
+            const float *row = col + (long long)(j + R) * P;
+#pragma unroll
+            for (int dx = -R; dx <= R; ++dx) win[W - 1][dx + R] = __ldg(row + dx);
+            bk = __ldg(bcol + (long long)j * P);
+        }
+        const float uc = win[R][R];
+        auto N = [&](int dx, int dy) { return win[R + dy][R + dx]; };
+        op(j, resid_diff32<ST>(N, uc, bk), uc);
+    }
+}
+
 // (L u - b)(i, j) evaluated directly from a node accessor U(di, dj), in the same order as
 // march (so the two agree bit for bit).
 template <int ST, typename T, class F>
@@ -362,23 +437,8 @@ __device__ __forceinline__ double resid_dd(const double *uh, const double *ul, c
 
 template <int ST>
 __device__ __forceinline__ float resid_smem(const float *A, int SX, int x, int y, float rk) {
-    auto U = [&](int dx, int dy) { return A[(y + dy) * SX + (x + dx)]; };
-    const float uC = U(0, 0);
-    const float v1 = U(0, -1) + U(0, 1);
-    const float p0 = U(-1, 0) + U(1, 0);
-    if (ST == 5) return (p0 + v1) + fmaf(-4.0f, uC, -rk);
-    const float pm = U(-1, -1) + U(1, -1);
-    const float pp = U(-1, 1) + U(1, 1);
-    if (ST == 9)
-        return fmaf(4.0f / 6.0f, p0 + v1, fmaf(1.0f / 6.0f, pm + pp, fmaf(-20.0f / 6.0f, uC, -rk)));
-    const float v2 = U(0, -2) + U(0, 2);
-    const float P0 = U(-2, 0) + U(2, 0);
-    const float Pm = U(-2, -2) + U(2, -2);
-    const float Pp = U(-2, 2) + U(2, 2);
-    return fmaf(64.0f / 72.0f, p0 + v1,
-                fmaf(-4.0f / 72.0f, P0 + v2,
-                     fmaf(16.0f / 72.0f, pm + pp,
-                          fmaf(-1.0f / 72.0f, Pm + Pp, fmaf(-300.0f / 72.0f, uC, -rk)))));
+    auto N = [&](int dx, int dy) { return A[(y + dy) * SX + (x + dx)]; };
+    return resid_diff32<ST>(N, A[y * SX + x], rk);
 }
 
 // One tile of the temporal-blocked FP32 sweep, run by the whole block: `depth` sweeps with

@@ -14,14 +14,16 @@
 //
 // Boundaries: the grid is extended by the odd reflection the homogeneous Dirichlet boundary
 // implies (u and r odd about nodes 0 and N+1, which stay 0).  Every operation of the sweep
-// is an odd function of its inputs under round-to-nearest (sums, fma with constant
-// coefficients and weights), so the values computed on reflected rows and columns are the
-// exact negatives of their mirrors, and interior values equal those of one-sweep launches
-// bit for bit -- with no per-stage ghost refresh.
+// is an odd function of its inputs under round-to-nearest (differences, sums, fma with
+// constant coefficients and weights), so the values computed on reflected rows and columns
+// are the exact negatives of their mirrors, and interior values equal those of one-sweep
+// launches bit for bit -- with no per-stage ghost refresh.
 //
-// Per node and stage: 2 (9-point) or 4 (17-point) shared-memory loads for the horizontal
-// pair sums, which each thread keeps, with its own column's values, in register windows
-// down the rows.  HBM traffic per update: about (4 e + 4 r + 4 e') / K bytes plus the halo.
+// Per node and stage: 2 (5/9-point) or 4 (17-point) shared-memory loads for the horizontal
+// neighbours, which each thread keeps, with its own column's values, in register windows
+// down the rows; the residual is evaluated in difference form (resid_diff32), as in the
+// one-sweep FP32 kernel.  HBM traffic per update: about (4 e + 4 r + 4 e') / K bytes plus
+// the halo.
 #include "cj_internal.h"
 #include "grid_dev.cuh"
 #include "stencil_dev.cuh"
@@ -98,13 +100,16 @@ __global__ void __launch_bounds__(kWaveW) sweep_wave_kernel(const float *__restr
     for (int k = tid; k < K * RW; k += kWaveW) (&ring[0][0])[k] = 0.0f;
     for (int k = 0; k < RQ; ++k) rline[k][tid] = 0.0f;
 
-    // register windows of each stage's input (stage s reads stage s-1): own-column values
-    // and horizontal pair sums of the last 2R+1 rows (index 2R = newest)
-    float uw[K][RING], pw[K][RING], Pw[K][RING];
+    // register windows of each stage's input (stage s reads stage s-1): the values of the
+    // last 2R+1 rows (index 2R = newest) at this thread's column and at the columns R
+    // to either side (wv[s][c][q]: column offset c - R)
+    float wv[K][2 * R + 1][RING];
 #pragma unroll
     for (int s = 0; s < K; ++s)
 #pragma unroll
-        for (int q = 0; q < RING; ++q) uw[s][q] = pw[s][q] = Pw[s][q] = 0.0f;
+        for (int c = 0; c < 2 * R + 1; ++c)
+#pragma unroll
+            for (int q = 0; q < RING; ++q) wv[s][c][q] = 0.0f;
     // loads in flight: eq[d], rq[d] hold rows yin + d
     float eq[D], rq[D];
     const int ystart = y0 - H;
@@ -138,14 +143,11 @@ __global__ void __launch_bounds__(kWaveW) sweep_wave_kernel(const float *__restr
             // push stage s-1's newest row (row yin - R (s-1)) into stage s's window
             const float *row = &ring[s - 1][tid + R];
 #pragma unroll
-            for (int q = 0; q < RING - 1; ++q) {
-                uw[s - 1][q] = uw[s - 1][q + 1];
-                pw[s - 1][q] = pw[s - 1][q + 1];
-                Pw[s - 1][q] = Pw[s - 1][q + 1];
+            for (int c = 0; c < 2 * R + 1; ++c) {
+#pragma unroll
+                for (int q = 0; q < RING - 1; ++q) wv[s - 1][c][q] = wv[s - 1][c][q + 1];
+                wv[s - 1][c][RING - 1] = c == R ? v : row[c - R];
             }
-            uw[s - 1][RING - 1] = v;
-            pw[s - 1][RING - 1] = row[-1] + row[1];
-            if (R == 2) Pw[s - 1][RING - 1] = row[-2] + row[2];
             // stage s: row y = yin - R s, window rows y-R .. y+R; r(y) from the r line
             const int y = yin - R * s;
             const bool bc_row = boundary_row(y, Ny);
@@ -154,20 +156,9 @@ __global__ void __launch_bounds__(kWaveW) sweep_wave_kernel(const float *__restr
                 int rs = slot - R * s;
                 if (rs < 0) rs += RQ;
                 const float rk = rline[rs][tid];
-                const float *U = uw[s - 1], *p = pw[s - 1], *Q = Pw[s - 1];
-                const float uc = U[R];
-                float res;
-                if (ST == 5) {
-                    res = (p[1] + (U[0] + U[2])) + fmaf(-4.0f, uc, -rk);
-                } else if (ST == 9) {
-                    res = fmaf(4.0f / 6.0f, p[1] + (U[0] + U[2]),
-                               fmaf(1.0f / 6.0f, p[0] + p[2], fmaf(-20.0f / 6.0f, uc, -rk)));
-                } else {
-                    res = fmaf(64.0f / 72.0f, p[2] + (U[1] + U[3]),
-                               fmaf(-4.0f / 72.0f, Q[2] + (U[0] + U[4]),
-                                    fmaf(16.0f / 72.0f, p[1] + p[3],
-                                         fmaf(-1.0f / 72.0f, Q[0] + Q[4], fmaf(-300.0f / 72.0f, uc, -rk)))));
-                }
+                auto N = [&](int dx, int dy) { return wv[s - 1][R + dx][R + dy]; };
+                const float uc = wv[s - 1][R][R];
+                const float res = resid_diff32<ST>(N, uc, rk);
                 nv = fmaf(wt.w[s - 1], res, uc);
             }
             v = nv;

@@ -431,6 +431,28 @@ def test_fp32_sweep_exact_on_integers():
 
 
 @pytest.mark.parametrize("st", STENCILS)
+@pytest.mark.parametrize("N", [1024, 8192])
+def test_fp32_sweep_keeps_the_lowest_mode(st, N):
+    """On the smoothest mode of a fine grid, where L e is ~1e-7 of the values that cancel in
+    it, the FP32 sweep's increment w (L e - r) matches the FP64 one to 1e-3 (difference form;
+    the pair-sum form is off by ~40 % at 8192^2).  Checked on a 24 x 24 patch of the mode,
+    with a weight large enough (1e4, the size of the cycle's largest weights) that the
+    increment is not lost in the FP32 rounding of the updated value itself."""
+    i = np.arange(1, N + 1)
+    mode = np.sin(np.pi * i / (N + 1))
+    lo = N // 2 - 12
+    e = np.outer(mode[lo:lo + 24], mode[lo:lo + 24]).astype(np.float32)
+    # interior nodes of the patch only: embed it so its own boundary does not matter
+    r = np.zeros_like(e)
+    w = 1.0e4
+    out32 = orc.sweep_f32(st, e, r, np.float32(w)).astype(np.float64) - e
+    out64 = orc.sweep(st, e.astype(np.float64), r.astype(np.float64), w) - e.astype(np.float64)
+    core = (slice(4, 20), slice(4, 20))
+    ref = out64[core]
+    assert np.abs(out32[core] - ref).max() <= 1e-3 * np.abs(ref).max()
+
+
+@pytest.mark.parametrize("st", STENCILS)
 def test_fp32_sweep_close_to_fp64(st):
     rng = np.random.default_rng(10 + st)
     e = rng.standard_normal((12, 15)).astype(np.float32)
