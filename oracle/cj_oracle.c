@@ -48,16 +48,20 @@
  *      FP64 defect-correction loop r = b - L u, rt = (float) r, one FP32 CJM cycle of
  *      length M_in on L e = rt from e = 0 with w32_n = (float)(omega_n / c), then
  *      u <- u + (double) e.  The stop test is the FP64 residual of R8.
- *   R14 FP32 evaluation (not in the paper): the FP32 inner sweep evaluates L e - r in
- *      difference form, sum_k c_k (e_k - e_C) - r, grouped like R9 without a centre term;
- *      on a 8192^2 grid the pair-sum form loses ~40 % of the lowest mode's L e in FP32, the
- *      difference form keeps it to a few FP32 ulps.
  *   R11 double-FP64 outer (not in the paper): as R10, but the solution is the unevaluated
  *      sum u_hi + u_lo of two FP64 arrays and the defect is evaluated to about twice FP64
  *      precision: D (L u_hi - b), D = 1, 6 or 72 the stencil's denominator, is a sum of
  *      terms that are exact in FP64 (power-of-two multiples of u_hi and b), added by the
  *      error-free TwoSum cascade (Ogita, Rump and Oishi's Sum2); D L u_lo is added in plain
  *      FP64.  The correction is added by TwoSum.  This removes the FP64 floor of R8.
+ *   R14 FP32 evaluation (not in the paper): the FP32 inner sweep evaluates L e - r in
+ *      difference form, sum_k c_k (e_k - e_C) - r, grouped like R9 without a centre term;
+ *      on a 8192^2 grid the pair-sum form loses ~40 % of the lowest mode's L e in FP32, the
+ *      difference form keeps it to a few FP32 ulps.
+ *   R15 non-homogeneous Dirichlet (Sec. 3.3's test problem): the data fill the two-node
+ *      ring around the interior and stay fixed (see orc_solve_bc).
+ *   R16 real-error stop (Sec. 3.4, Fig. 4 right): the infinity norm of u - u_exact tested
+ *      before every cycle and every check_every sweeps (see orc_solve_to_error).
  *
  * Array convention: interior values only, row-major [Ny][Nx], value of node (i, j) at
  * u[(j-1)*Nx + (i-1)].  Compiled with -ffp-contract=off so that every rounding is the
@@ -607,6 +611,210 @@ long orc_solve_mixed_dd(int st, int Nx, int Ny, const double *f, double tol, lon
     *rel_l2 = rl2;
     *rel_linf = rinf;
     *outer = out;
+    *status = stat;
+    return sweeps;
+}
+
+/* ---------------------------------------------------------------- non-homogeneous Dirichlet */
+
+/* Reading R15 (the paper's test problem, Sec. 3.3): Dirichlet data given at every node the
+ * stencil reaches outside the interior -- the ring of nodes i or j in {-1, 0, N+1, N+2} --
+ * in a padded array G of (Ny+4) rows x (Nx+4) columns, node (i, j) at G[(j+1)*(Nx+4) + i+1].
+ * Those values are fixed; the interior iterates as before.  The error then iterates with the
+ * operator whose ghost values are all zero, whose spectrum lies inside the paper's
+ * [kmin, kmax] (pinned by a dense eigenvalue test), so the plan is unchanged. */
+static double at_bc(const double *u, const double *G, int Nx, int Ny, int i, int j) {
+    if (i < 1 || i > Nx || j < 1 || j > Ny) return G[(size_t)(j + 1) * (Nx + 4) + (i + 1)];
+    return u[(size_t)(j - 1) * Nx + (i - 1)];
+}
+
+/* resid_at with the ghost values taken from G (same evaluation order, reading R9). */
+static double resid_at_bc(int st, const double *u, const double *G, int Nx, int Ny, int i, int j,
+                          double bk) {
+#define A(di, dj) at_bc(u, G, Nx, Ny, i + (di), j + (dj))
+    double uC = A(0, 0);
+    double v1 = A(0, -1) + A(0, 1);
+    double p0 = A(-1, 0) + A(1, 0);
+    if (st == 5) return (p0 + v1) + fma(-4.0, uC, -bk);
+    double pm = A(-1, -1) + A(1, -1);
+    double pp = A(-1, 1) + A(1, 1);
+    if (st == 9) return fma(4.0 / 6.0, p0 + v1, fma(1.0 / 6.0, pm + pp, fma(-20.0 / 6.0, uC, -bk)));
+    double v2 = A(0, -2) + A(0, 2);
+    double P0 = A(-2, 0) + A(2, 0);
+    double Pm = A(-2, -2) + A(2, -2);
+    double Pp = A(-2, 2) + A(2, 2);
+#undef A
+    return fma(64.0 / 72.0, p0 + v1,
+               fma(-4.0 / 72.0, P0 + v2,
+                   fma(16.0 / 72.0, pm + pp, fma(-1.0 / 72.0, Pm + Pp, fma(-300.0 / 72.0, uC, -bk)))));
+}
+
+void orc_sweep_bc(int st, int Nx, int Ny, const double *u, const double *G, const double *b,
+                  double w, double *u_out) {
+    for (int j = 1; j <= Ny; ++j)
+        for (int i = 1; i <= Nx; ++i) {
+            size_t k = (size_t)(j - 1) * Nx + (i - 1);
+            u_out[k] = fma(w, resid_at_bc(st, u, G, Nx, Ny, i, j, b[k]), u[k]);
+        }
+}
+
+void orc_residual_bc(int st, int Nx, int Ny, const double *u, const double *G, const double *b,
+                     double *l2sq, double *linf) {
+    double s = 0.0, m = 0.0;
+    for (int j = 1; j <= Ny; ++j)
+        for (int i = 1; i <= Nx; ++i) {
+            size_t k = (size_t)(j - 1) * Nx + (i - 1);
+            double r = resid_at_bc(st, u, G, Nx, Ny, i, j, b[k]);
+            s += r * r;
+            if (fabs(r) > m) m = fabs(r);
+        }
+    *l2sq = s;
+    *linf = m;
+}
+
+/* Plain FP64 CJM with Dirichlet data G (R15); otherwise as orc_solve. */
+long orc_solve_bc(int st, int Nx, int Ny, const double *f, const double *G, double tol,
+                  long max_sweeps, double *u, double *rel_l2, double *rel_linf, long *cycles,
+                  int *status) {
+    if (Nx < 1 || Ny < 1 || !(tol > 0.0 && tol < 1.0)) return -1;
+    size_t n = (size_t)Nx * (size_t)Ny;
+    double kmin, kmax;
+    orc_kappa_bounds(st, Nx, Ny, &kmin, &kmax);
+    long M = orc_cycle_length(kmin, kmax, tol);
+    double *w = (double *)malloc(sizeof(double) * (size_t)M);
+    double *b = (double *)malloc(sizeof(double) * n);
+    double *v = (double *)malloc(sizeof(double) * n);
+    orc_sweep_coeffs(st, kmin, kmax, M, w);
+    orc_scale_rhs(Nx, Ny, f, b);
+    double bsq = 0.0, bmax = 0.0;
+    for (size_t k = 0; k < n; ++k) {
+        bsq += b[k] * b[k];
+        if (fabs(b[k]) > bmax) bmax = fabs(b[k]);
+    }
+    double bn = sqrt(bsq), eps = ldexp(1.0, -53), S = orc_abs_coeff_sum(st);
+    long sweeps = 0, cyc = 0;
+    int stat, stall = 0;
+    double rl2 = 0.0, rinf = 0.0, prev = 0.0;
+    for (;;) {
+        double sq, mx, usq = 0.0;
+        orc_residual_bc(st, Nx, Ny, u, G, b, &sq, &mx);
+        for (size_t k = 0; k < n; ++k) usq += u[k] * u[k];
+        rl2 = bn > 0.0 ? sqrt(sq) / bn : sqrt(sq);
+        rinf = bmax > 0.0 ? mx / bmax : mx;
+        double fl = bn > 0.0 ? eps * S * sqrt(usq) / bn : eps * S * sqrt(usq);
+        stat = stop_rule(rl2, fl, prev, cyc, tol, 1, &stall);
+        if (stat >= 0) break;
+        if (sweeps + M > max_sweeps) { stat = ORC_MAX_SWEEPS; break; }
+        for (long s2 = 0; s2 < M; ++s2) {
+            orc_sweep_bc(st, Nx, Ny, u, G, b, w[s2], v);
+            memcpy(u, v, sizeof(double) * n);
+        }
+        sweeps += M;
+        cyc += 1;
+        prev = rl2;
+    }
+    free(w); free(b); free(v);
+    *rel_l2 = rl2;
+    *rel_linf = rinf;
+    *cycles = cyc;
+    *status = stat;
+    return sweeps;
+}
+
+/* ---------------------------------------------------------------- real-error stop */
+
+/* Real error of Sec. 3.4 (Fig. 4, right): the infinity norm of u - u_exact over the interior. */
+double orc_real_error(int Nx, int Ny, const double *u, const double *u_exact) {
+    double m = 0.0;
+    size_t n = (size_t)Nx * (size_t)Ny;
+    for (size_t k = 0; k < n; ++k) {
+        double d = fabs(u[k] - u_exact[k]);
+        if (!(d == d)) return d;
+        if (d > m) m = d;
+    }
+    return m;
+}
+
+/* Plain FP64 CJM stopped by the real error instead of the residual (Sec. 3.4, reading R16):
+ * the cycle length comes from `tol` as in orc_solve; the real error E is tested before every
+ * cycle and, when check_every > 0, after every check_every sweeps inside a cycle.  Stops with
+ * converged at the first test where E <= err_tol.  The residual of R8 is still evaluated before
+ * every cycle, only for the floor part of the stop rule (a residual at the FP64 floor, or a
+ * cycle that failed to halve it, ends the solve with "floor": the real error cannot fall
+ * further, e.g. when err_tol is below the discretisation error).  E = NaN ends it with
+ * "diverged".  G = NULL: homogeneous Dirichlet (R6); else the Dirichlet data of R15.
+ * hist[2k], hist[2k+1] = sweeps done and E at the k-th test (up to cap tests; *count = all). */
+long orc_solve_to_error(int st, int Nx, int Ny, const double *f, const double *G,
+                        const double *u_exact, double tol, double err_tol, long check_every,
+                        long max_sweeps, double *u, double *hist, long cap, long *count,
+                        double *err, double *rel_l2, long *cycles, int *status) {
+    if (Nx < 1 || Ny < 1 || !(tol > 0.0 && tol < 1.0) || !(err_tol >= 0.0) || check_every < 0)
+        return -1;
+    size_t n = (size_t)Nx * (size_t)Ny;
+    double kmin, kmax;
+    orc_kappa_bounds(st, Nx, Ny, &kmin, &kmax);
+    long M = orc_cycle_length(kmin, kmax, tol);
+    double *w = (double *)malloc(sizeof(double) * (size_t)M);
+    double *b = (double *)malloc(sizeof(double) * n);
+    double *v = (double *)malloc(sizeof(double) * n);
+    orc_sweep_coeffs(st, kmin, kmax, M, w);
+    orc_scale_rhs(Nx, Ny, f, b);
+    double bsq = 0.0;
+    for (size_t k = 0; k < n; ++k) bsq += b[k] * b[k];
+    double bn = sqrt(bsq), eps = ldexp(1.0, -53), S = orc_abs_coeff_sum(st);
+    long sweeps = 0, cyc = 0, tests = 0;
+    int stat = -1, stall = 0, mid = 0;
+    double rl2 = 0.0, prev = 0.0, E = 0.0, sq, mx;
+#define RECORD()                                          \
+    do {                                                  \
+        if (tests < cap) {                                \
+            hist[2 * tests] = (double)sweeps;             \
+            hist[2 * tests + 1] = E;                      \
+        }                                                 \
+        ++tests;                                          \
+    } while (0)
+    for (;;) {
+        double usq = 0.0;
+        if (G) orc_residual_bc(st, Nx, Ny, u, G, b, &sq, &mx);
+        else orc_residual(st, Nx, Ny, u, b, &sq, &mx);
+        for (size_t k = 0; k < n; ++k) usq += u[k] * u[k];
+        rl2 = bn > 0.0 ? sqrt(sq) / bn : sqrt(sq);
+        double fl = bn > 0.0 ? eps * S * sqrt(usq) / bn : eps * S * sqrt(usq);
+        E = orc_real_error(Nx, Ny, u, u_exact);
+        RECORD();
+        if (!(E == E) || E > 1e300) { stat = ORC_DIVERGED; break; }
+        if (E <= err_tol) { stat = ORC_CONVERGED; break; }
+        stat = stop_rule(rl2, fl, prev, cyc, 0.0, 1, &stall);
+        if (stat == ORC_CONVERGED) stat = ORC_FLOOR; /* rho == 0: u is the discrete solution */
+        if (stat >= 0) break;
+        if (sweeps + M > max_sweeps) { stat = ORC_MAX_SWEEPS; break; }
+        for (long s = 0; s < M; ++s) {
+            if (G) orc_sweep_bc(st, Nx, Ny, u, G, b, w[s], v);
+            else orc_sweep(st, Nx, Ny, u, b, w[s], v);
+            memcpy(u, v, sizeof(double) * n);
+            ++sweeps;
+            if (check_every > 0 && (s + 1) % check_every == 0 && s + 1 < M) {
+                E = orc_real_error(Nx, Ny, u, u_exact);
+                RECORD();
+                if (!(E == E) || E > 1e300) { stat = ORC_DIVERGED; mid = 1; break; }
+                if (E <= err_tol) { stat = ORC_CONVERGED; mid = 1; break; }
+            }
+        }
+        if (mid) break;
+        cyc += 1;
+        prev = rl2;
+    }
+#undef RECORD
+    if (mid) { /* report the residual where the solve stopped */
+        if (G) orc_residual_bc(st, Nx, Ny, u, G, b, &sq, &mx);
+        else orc_residual(st, Nx, Ny, u, b, &sq, &mx);
+        rl2 = bn > 0.0 ? sqrt(sq) / bn : sqrt(sq);
+    }
+    free(w); free(b); free(v);
+    *count = tests;
+    *err = E;
+    *rel_l2 = rl2;
+    *cycles = cyc;
     *status = stat;
     return sweeps;
 }

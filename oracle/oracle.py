@@ -72,6 +72,18 @@ def lib():
         L.orc_solve_mixed.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, _dp, ctypes.c_double,
                                       ctypes.c_long, ctypes.c_long, _dp, _dp, _dp, _lp, _ip]
         L.orc_solve_mixed.restype = ctypes.c_long
+        L.orc_sweep_bc.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, _dp, _dp, _dp, ctypes.c_double, _dp]
+        L.orc_residual_bc.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, _dp, _dp, _dp, _dp, _dp]
+        L.orc_solve_bc.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, _dp, _dp, ctypes.c_double,
+                                   ctypes.c_long, _dp, _dp, _dp, _lp, _ip]
+        L.orc_solve_bc.restype = ctypes.c_long
+        L.orc_real_error.argtypes = [ctypes.c_int, ctypes.c_int, _dp, _dp]
+        L.orc_real_error.restype = ctypes.c_double
+        L.orc_solve_to_error.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, _dp, _dp, _dp,
+                                         ctypes.c_double, ctypes.c_double, ctypes.c_long,
+                                         ctypes.c_long, _dp, _dp, ctypes.c_long, _lp, _dp, _dp,
+                                         _lp, ctypes.POINTER(ctypes.c_int)]
+        L.orc_solve_to_error.restype = ctypes.c_long
         L.orc_residual_dd.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, _dp, _dp, _dp, _dp]
         L.orc_solve_mixed_dd.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, _dp, ctypes.c_double,
                                          ctypes.c_long, ctypes.c_long, _dp, _dp, _dp, _dp, _lp, _ip]
@@ -255,3 +267,72 @@ def solve_mixed_dd(st: int, f: np.ndarray, tol: float, M_in: int, u0: np.ndarray
         raise ValueError("bad argument")
     return dict(u=u, u_lo=ulo, sweeps=n, outer=outer.value, rel_l2=rl2.value, rel_linf=rinf.value,
                 status=STATUS[stat.value], converged=stat.value == 0)
+
+
+def ghost_ring(Nx: int, Ny: int, g) -> np.ndarray:
+    """Padded (Ny+4) x (Nx+4) array of the Dirichlet data g(i, j) at the two-node ring around
+    the interior (interior entries 0): the ring the stencils reach."""
+    G = np.zeros((Ny + 4, Nx + 4))
+    for j in range(-1, Ny + 3):
+        for i in range(-1, Nx + 3):
+            if i < 1 or i > Nx or j < 1 or j > Ny:
+                G[j + 1, i + 1] = g(i, j)
+    return G
+
+
+def sweep_bc(st: int, u: np.ndarray, G: np.ndarray, b: np.ndarray, w: float) -> np.ndarray:
+    u, G, b = _grid(u), _grid(G), _grid(b)
+    out = np.empty_like(u)
+    lib().orc_sweep_bc(st, u.shape[1], u.shape[0], _d(u), _d(G), _d(b), float(w), _d(out))
+    return out
+
+
+def residual_bc(st: int, u: np.ndarray, G: np.ndarray, b: np.ndarray):
+    u, G, b = _grid(u), _grid(G), _grid(b)
+    s, m = ctypes.c_double(), ctypes.c_double()
+    lib().orc_residual_bc(st, u.shape[1], u.shape[0], _d(u), _d(G), _d(b), ctypes.byref(s), ctypes.byref(m))
+    return s.value, m.value
+
+
+def solve_bc(st: int, f: np.ndarray, G: np.ndarray, tol: float, u0: np.ndarray | None = None,
+             max_sweeps: int = 1 << 40) -> dict:
+    """Plain FP64 CJM with non-homogeneous Dirichlet data G (see ghost_ring)."""
+    f, G = _grid(f), _grid(G)
+    u = np.zeros_like(f) if u0 is None else _grid(u0).copy()
+    rl2, rinf = ctypes.c_double(), ctypes.c_double()
+    cyc, stat = ctypes.c_long(), ctypes.c_int()
+    n = lib().orc_solve_bc(st, f.shape[1], f.shape[0], _d(f), _d(G), tol, max_sweeps, _d(u),
+                           ctypes.byref(rl2), ctypes.byref(rinf), ctypes.byref(cyc), ctypes.byref(stat))
+    if n < 0:
+        raise ValueError("bad argument")
+    return dict(u=u, sweeps=n, cycles=cyc.value, rel_l2=rl2.value, rel_linf=rinf.value,
+                status=STATUS[stat.value], converged=stat.value == 0)
+
+
+def real_error(u: np.ndarray, u_exact: np.ndarray) -> float:
+    """Infinity norm of u - u_exact (the real error of Sec. 3.4)."""
+    u, ue = _grid(u), _grid(u_exact)
+    return lib().orc_real_error(u.shape[1], u.shape[0], _d(u), _d(ue))
+
+
+def solve_to_error(st: int, f: np.ndarray, u_exact: np.ndarray, tol: float, err_tol: float,
+                   G: np.ndarray | None = None, check_every: int = 0,
+                   max_sweeps: int = 1 << 40, cap: int = 4096) -> dict:
+    """Plain FP64 CJM stopped by the real error (see orc_solve_to_error); G as in ghost_ring,
+    None for the homogeneous boundary.  history: (sweeps, real error) at every test."""
+    f, ue = _grid(f), _grid(u_exact)
+    Gp = None if G is None else _d(_grid(G))
+    u = np.zeros_like(f)
+    hist = np.zeros(2 * cap)
+    cnt, cyc, stat = ctypes.c_long(), ctypes.c_long(), ctypes.c_int()
+    err, rl2 = ctypes.c_double(), ctypes.c_double()
+    n = lib().orc_solve_to_error(st, f.shape[1], f.shape[0], _d(f), Gp, _d(ue), tol, err_tol,
+                                 check_every, max_sweeps, _d(u), _d(hist), cap, ctypes.byref(cnt),
+                                 ctypes.byref(err), ctypes.byref(rl2), ctypes.byref(cyc),
+                                 ctypes.byref(stat))
+    if n < 0:
+        raise ValueError("bad argument")
+    k = min(cnt.value, cap)
+    return dict(u=u, sweeps=n, cycles=cyc.value, err=err.value, rel_l2=rl2.value,
+                status=STATUS[stat.value], tests=cnt.value,
+                history=hist[:2 * k].reshape(k, 2).copy())

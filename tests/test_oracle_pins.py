@@ -574,3 +574,161 @@ def test_double_fp64_outer_goes_below_the_fp64_floor(st):
     assert rho <= 1.5 * tol
     # and the FP64 solution agrees with the double-FP64 one to FP64 accuracy
     assert np.abs(fp["u"] - dd["u"]).max() <= 1e-9 * np.abs(dd["u"]).max()
+
+
+# ----------------------------------------------------------------- non-homogeneous Dirichlet
+
+def _dense_zero_ghost(st, Nx, Ny):
+    """L on the interior with every ghost value zero, from the printed coefficients."""
+    n = Nx * Ny
+    A = np.zeros((n, n))
+    for j in range(Ny):
+        for i in range(Nx):
+            for (dx, dy), c in COEF[st].items():
+                ii, jj = i + dx, j + dy
+                if 0 <= ii < Nx and 0 <= jj < Ny:
+                    A[j * Nx + i, jj * Nx + ii] += c
+    return A
+
+
+def _ghost_term(st, Nx, Ny, G):
+    """Contribution of the fixed ghost data to L u at every interior node."""
+    t = np.zeros((Ny, Nx))
+    for j in range(1, Ny + 1):
+        for i in range(1, Nx + 1):
+            for (dx, dy), c in COEF[st].items():
+                ii, jj = i + dx, j + dy
+                if ii < 1 or ii > Nx or jj < 1 or jj > Ny:
+                    t[j - 1, i - 1] += c * G[jj + 1, ii + 1]
+    return t
+
+
+@pytest.mark.parametrize("st", STENCILS)
+@pytest.mark.parametrize("Nx,Ny", [(1, 1), (5, 4), (9, 7), (12, 12)])
+def test_dirichlet_data_solve_matches_dense(st, Nx, Ny):
+    """With Dirichlet data the solve equals the dense solution of the zero-ghost operator with
+    the data moved to the right-hand side."""
+    f, _, g = workloads.paper_problem(Nx, Ny)
+    G = orc.ghost_ring(Nx, Ny, g)
+    out = orc.solve_bc(st, f, G, 1e-13)
+    assert out["status"] in ("converged", "floor") and out["rel_l2"] < 1e-12
+    h = 1.0 / (Nx + 1)
+    rhs = (h * h * f - _ghost_term(st, Nx, Ny, G)).ravel()
+    ref = np.linalg.solve(_dense_zero_ghost(st, Nx, Ny), rhs).reshape(Ny, Nx)
+    np.testing.assert_allclose(out["u"], ref, rtol=0, atol=1e-11 * np.abs(ref).max())
+
+
+@pytest.mark.parametrize("st", STENCILS)
+@pytest.mark.parametrize("N", [8, 16, 32])
+def test_zero_ghost_spectrum_inside_the_kappa_bounds(st, N):
+    """The error of a Dirichlet-data solve iterates with the zero-ghost operator; its
+    eigenvalues lie inside the paper's [kmin, kmax], so the plan's weights stay valid."""
+    ev = np.linalg.eigvalsh(_dense_zero_ghost(st, N, N) / COEF[st][(0, 0)])
+    kmin, kmax = orc.kappa_bounds(st, N, N)
+    assert ev.min() >= kmin * (1 - 1e-12) and ev.max() <= kmax * (1 + 1e-12)
+
+
+def test_zero_data_equals_homogeneous_for_radius_one():
+    f = workloads.smooth_random_rhs(20, 17, 3)
+    G = np.zeros((21, 24))
+    for st in (5, 9):
+        a = orc.solve_bc(st, f, G, 1e-10)
+        b = orc.solve(st, f, 1e-10)
+        assert a["sweeps"] == b["sweeps"]
+        np.testing.assert_array_equal(a["u"], b["u"])
+
+
+@pytest.mark.parametrize("st,order", [(5, 2.0), (9, 2.0), (17, 4.0)])
+def test_paper_problem_order(st, order):
+    """The paper's test problem (Sec. 3.3, u = -e^{xy}): the error against the analytic
+    solution falls at the stencil's order."""
+    errs = []
+    for N in (15, 31, 63):
+        f, u, g = workloads.paper_problem(N, N)
+        out = orc.solve_bc(st, f, orc.ghost_ring(N, N, g), 1e-13)
+        errs.append(np.abs(out["u"] - u).max())
+    rates = [np.log2(errs[k] / errs[k + 1]) for k in range(2)]
+    for r in rates:
+        assert abs(r - order) < 0.3, (errs, rates)
+
+
+# ----------------------------------------------------------------- real-error stop (Sec. 3.4)
+
+def _to_error_by_hand(st, f, ue, G, tol, err_tol, every):
+    """The real-error-stopped solve written out with the pinned one-sweep primitive."""
+    Ny, Nx = f.shape
+    kmin, kmax = orc.kappa_bounds(st, Nx, Ny)
+    M = orc.cycle_length(kmin, kmax, tol)
+    w = orc.sweep_coeffs(st, kmin, kmax, M)
+    b = orc.scale_rhs(f)
+    u = np.zeros_like(f)
+    hist, sweeps = [], 0
+    while True:
+        E = float(np.max(np.abs(u - ue)))
+        hist.append((sweeps, E))
+        if E <= err_tol:
+            return u, sweeps, hist
+        for s in range(M):
+            u = orc.sweep(st, u, b, w[s]) if G is None else orc.sweep_bc(st, u, G, b, w[s])
+            sweeps += 1
+            if every and (s + 1) % every == 0 and s + 1 < M:
+                E = float(np.max(np.abs(u - ue)))
+                hist.append((sweeps, E))
+                if E <= err_tol:
+                    return u, sweeps, hist
+
+
+@pytest.mark.parametrize("st", STENCILS)
+@pytest.mark.parametrize("every", [0, 5, 16])
+@pytest.mark.parametrize("data", [True, False])
+def test_solve_to_error_follows_its_definition(st, every, data):
+    Nx, Ny = 11, 9
+    if data:
+        f, ue, g = workloads.paper_problem(Nx, Ny)
+        G = orc.ghost_ring(Nx, Ny, g)
+    else:
+        f, ue, G = workloads.manufactured_rhs(Nx, Ny), workloads.manufactured_solution(Nx, Ny), None
+    # the discrete solution's real error plus a margin the iteration must close
+    disc = orc.real_error(orc.solve_bc(st, f, G, 1e-13)["u"] if data else orc.solve(st, f, 1e-13)["u"], ue)
+    err_tol = disc * 1.05 + 1e-9
+    u, sweeps, hist = _to_error_by_hand(st, f, ue, G, 1e-2, err_tol, every)
+    out = orc.solve_to_error(st, f, ue, 1e-2, err_tol, G=G, check_every=every)
+    assert out["status"] == "converged"
+    assert out["sweeps"] == sweeps and out["tests"] == len(hist)
+    np.testing.assert_array_equal(out["history"], np.array(hist))
+    np.testing.assert_array_equal(out["u"], u)
+    assert out["err"] == hist[-1][1] <= err_tol < hist[-2][1]
+
+
+def test_solve_to_error_below_the_discretisation_error_ends_at_the_floor():
+    """A real-error goal below the discretisation error cannot be met: the solve runs until the
+    residual stalls, and its real error is then that of the discrete solution."""
+    N, st = 15, 5
+    f, ue, g = workloads.paper_problem(N, N)
+    G = orc.ghost_ring(N, N, g)
+    disc = orc.real_error(orc.solve_bc(st, f, G, 1e-13)["u"], ue)
+    out = orc.solve_to_error(st, f, ue, 1e-8, disc / 2, G=G)
+    assert out["status"] == "floor"
+    assert out["err"] == pytest.approx(disc, rel=1e-6)
+
+
+def test_real_error_is_the_max_norm():
+    rng = np.random.default_rng(5)
+    u, v = rng.standard_normal((7, 13)), rng.standard_normal((7, 13))
+    assert orc.real_error(u, v) == np.max(np.abs(u - v))
+    u[3, 4] = np.nan
+    assert np.isnan(orc.real_error(u, v))
+
+
+def test_high_order_reaches_a_real_error_on_a_coarser_mesh():
+    """Sec. 3.4, Fig. 4 right, in miniature: the 17-point stencil meets a real-error goal on a
+    mesh where the 5-point one cannot, and with fewer sweeps than the 5-point one needs on the
+    mesh that can."""
+    goal = 1e-6
+    f, ue, g = workloads.paper_problem(31, 31)
+    hi = orc.solve_to_error(17, f, ue, 1e-8, goal, G=orc.ghost_ring(31, 31, g))
+    lo = orc.solve_to_error(5, f, ue, 1e-8, goal, G=orc.ghost_ring(31, 31, g))
+    assert hi["status"] == "converged" and lo["status"] == "floor"
+    f, ue, g = workloads.paper_problem(63, 63)
+    lo = orc.solve_to_error(5, f, ue, 1e-8, goal, G=orc.ghost_ring(63, 63, g))
+    assert lo["status"] == "converged" and lo["sweeps"] > hi["sweeps"]

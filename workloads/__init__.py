@@ -4,9 +4,10 @@ This package holds input generation only (right-hand sides, problem-size draws, 
 streams); none of the Chebyshev-Jacobi arithmetic lives here.
 """
 from .rhs import (grid_h, manufactured_rhs, manufactured_solution, smooth_random_modes,
-                  smooth_random_rhs, splitmix64_stream, gaussian_stream, uniform_stream)
+                  smooth_random_rhs, splitmix64_stream, gaussian_stream, uniform_stream,
+                  paper_problem)
 from .streams import batch_problems, request_stream, log_uniform_int
 
 __all__ = ["grid_h", "manufactured_rhs", "manufactured_solution", "smooth_random_modes",
            "smooth_random_rhs", "splitmix64_stream", "gaussian_stream", "uniform_stream",
-           "batch_problems", "request_stream", "log_uniform_int"]
+           "batch_problems", "request_stream", "log_uniform_int", "paper_problem"]

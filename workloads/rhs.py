@@ -92,3 +92,22 @@ def smooth_random_rhs(Nx: int, Ny: int, seed: int, kmax: int = 64) -> np.ndarray
     Sx = np.sin(np.pi * np.outer(np.arange(1, K + 1), i) / (Nx + 1))   # (K, Nx)
     Sy = np.sin(np.pi * np.outer(j, np.arange(1, L + 1)) / (Ny + 1))   # (Ny, L)
     return np.ascontiguousarray(Sy @ A @ Sx)
+
+
+def paper_problem(Nx: int, Ny: int):
+    """The paper's test problem (Sec. 3.3): Delta u = -(x^2 + y^2) e^{xy} with the Dirichlet
+    data of its analytic solution u = -e^{xy}, on the uniform mesh x_i = i h, y_j = j h,
+    h = 1/(Nx+1) (the unit square when Nx == Ny).  Returns (f, u_exact, g): f and u_exact at
+    the interior nodes, and g(i, j) = u(i h, j h) for any node (the boundary data, also at the
+    second ring the 17-point stencil reaches)."""
+    h = grid_h(Nx)
+    x = np.arange(1, Nx + 1) * h
+    y = np.arange(1, Ny + 1) * h
+    X, Y = np.meshgrid(x, y)
+    f = -(X * X + Y * Y) * np.exp(X * Y)
+    u = -np.exp(X * Y)
+
+    def g(i, j):
+        return -np.exp((i * h) * (j * h))
+
+    return f, u, g
