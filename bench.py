@@ -58,9 +58,11 @@ def parse_args(argv=None):
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-mixed", action="store_true")
-    ap.add_argument("--workload", default="solve", choices=["solve", "batch", "serve"],
-                    help="solve: the plain FP64 9-point 4096^2 solve (default); batch: the 512-problem "
-                         "batched workload; serve: a bounded sample of the request stream")
+    ap.add_argument("--workload", default="solve", choices=["solve", "highorder", "paper", "batch", "serve"],
+                    help="solve: the plain FP64 9-point 4096^2 solve (default); highorder: the 17-point "
+                         "8192^2 mixed-precision solve; paper: the paper's test problem (Table 1 point and Fig. 4 "
+                         "right); batch: the 512-problem batched workload; serve: a "
+                         "bounded sample of the request stream")
     ap.add_argument("--serve-requests", type=int, default=48)
     return ap.parse_args(argv)
 
@@ -331,6 +333,160 @@ def mixed_paths(cj, f, stream, plain):
     return out
 
 
+def run_highorder(args):
+    """The 17-point 8192^2 problem (seeded smooth RHS, seed 2) to relative residual 1e-10 by
+    FP32 inner cycles inside double-FP64 defect correction; each step one solve.  The plain
+    FP64 cycle of the same problem (65,536 sweeps, which stops above 1e-10 at its rounding
+    floor) is timed on 64 sweeps and extrapolated, labelled as such."""
+    import torch
+
+    import paper_1705_00103_gb300 as cj
+    import workloads
+    torch.cuda.set_device(0)
+    cj.build.build()
+    N, st = 8192, 17
+    f = torch.from_numpy(workloads.smooth_random_rhs(N, N, 2)).cuda()
+    stream = torch.cuda.current_stream()
+    plan = cj.Plan(N, N, st, TOL, precision=cj.CJ_FP32_INNER_DD)
+    u = torch.zeros_like(f)
+    for _ in range(args.warmup):
+        u.zero_()
+        cj.cj_solve(plan.handle, f, u, stream)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(0)
+    clocks.start()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    res = []
+    for _ in range(args.steps):
+        u.zero_()
+        res.append(cj.cj_solve(plan.handle, f, u, stream))
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1)
+    info = plan.info()
+    plan.close()
+    sweeps = sum(r["sweeps"] for r in res)
+    # plain FP64: time 64 sweeps of its cycle, extrapolate to one cycle of M sweeps
+    with cj.Plan(N, N, st, TOL) as p64:
+        M = p64.info()["M"]
+        g = torch.zeros_like(f)
+        cj.cj_sweeps(p64.handle, f, g, 0, 4)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        cj.cj_sweeps(p64.handle, f, g, 0, 64)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        per64 = e0.elapsed_time(e1) / 64 * 1e-3
+    r = res[-1]
+    out = {"metric": METRIC, "value": N * N * sweeps / (ms * 1e-3) / 1e9, "unit": UNIT, "n_gpus": 1,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64x2",
+           "data": "synthetic",
+           "config": {"workload": "17-point alpha=2/3, 8192x8192, smooth random RHS (seed 2), tol 1e-10, FP32 "
+                                  "inner cycles in double-FP64 defect correction",
+                      "inner_cycle": info["M_inner"], "l2_flush": "none needed: grids of 268-537 MB"},
+           "time_to_tol_s": ms / args.steps * 1e-3, "status": cj.cj_status_string(r["rc"]),
+           "rel_res_l2": r["rel_res_l2"], "fp32_sweeps": r["sweeps"], "outer_steps": r["cycles"],
+           "plain_fp64_cycle_s_extrapolated": per64 * M,
+           "plain_fp64_note": "one 65,536-sweep FP64 cycle extrapolated from 64 timed sweeps; the plain "
+                              "FP64 solve cannot reach 1e-10 here (its rounding floor is ~8e-10)",
+           "clocks": clk}
+    print(json.dumps(out), flush=True)
+
+
+def paper_solve(cj, torch, N, st, tol, stream, err_goal=None, check_every=0):
+    """One solve of the paper's test problem (Sec. 3.3) with its Dirichlet data: to the
+    relative residual tol, or, with err_goal, to that real error (Sec. 3.4)."""
+    import workloads
+    f, ue, g = workloads.paper_problem(N, N)
+    fd, ued, Gd = f_to(torch, f), f_to(torch, ue), f_to(torch, cj.dirichlet_ring(N, N, g))
+    u = torch.zeros_like(fd)
+    with cj.Plan(N, N, st, tol, bc=cj.CJ_BC_DIRICHLET) as p:
+        cj.cj_set_boundary(p.handle, Gd, stream)
+        M = p.info()["M"]
+        every = max(1, M // 64) if check_every else 0
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        if err_goal is None:
+            r = cj.cj_solve(p.handle, fd, u, stream)
+        else:
+            r = cj.cj_solve_to_error(p.handle, fd, u, ued, err_goal, every, stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+    r["time_s"] = e0.elapsed_time(e1) * 1e-3
+    r["M"] = M
+    r["real_error_final"] = float((u - ued).abs().max())
+    return r
+
+
+def f_to(torch, a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def run_paper(args):
+    """The paper's own experiments on its test problem (Sec. 3.3, u = -e^{xy}) with plain FP64
+    CJM: (a) the N = 1024 point of Fig. 3 / Table 1 for the 5-, 9- and 17-point stencils, tol =
+    N^-2; (b) Fig. 4 right: the 17-point stencil on N = 128 and the 5-point one on N = 2048,
+    each until the real error reaches 1e-8 (tested every M/64 sweeps).  A step runs all five
+    solves; value = their grid-point updates per second."""
+    import torch
+
+    import paper_1705_00103_gb300 as cj
+    torch.cuda.set_device(0)
+    cj.build.build()
+    stream = torch.cuda.current_stream()
+    N3, tol3 = 1024, 1.0 / 1024 ** 2
+    runs = [("table1", 5, N3, tol3, None), ("table1", 9, N3, tol3, None), ("table1", 17, N3, tol3, None),
+            ("fig4", 17, 128, 1e-8, 1e-8), ("fig4", 5, 2048, 1e-8, 1e-8)]
+
+    def step():
+        return [paper_solve(cj, torch, N, st, tol, stream, goal, check_every=goal is not None)
+                for _, st, N, tol, goal in runs]
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(0)
+    clocks.start()
+    t_dev = 0.0
+    upd = 0
+    for _ in range(args.steps):
+        res = step()
+        t_dev += sum(r["time_s"] for r in res)
+        upd += sum(N * N * r["sweeps"] for (_, _, N, _, _), r in zip(runs, res))
+    clk = clocks.stop()
+
+    def brief(r, kind, st, N):
+        d = {"stencil": st, "N": N, "M": r["M"], "sweeps": r["sweeps"], "cycles": r["cycles"],
+             "time_s": r["time_s"], "status": cj.cj_status_string(r["rc"]), "rel_res_l2": r["rel_res_l2"],
+             "real_error": r["real_error_final"]}
+        if kind == "fig4":
+            h = r["history"]
+            pick = np.unique(np.linspace(0, len(h) - 1, min(len(h), 17)).astype(int))
+            d["real_error_vs_sweeps"] = [[int(h[k, 0]), float(h[k, 1])] for k in pick]
+        return d
+
+    t3 = [brief(r, k, st, N) for (k, st, N, _, _), r in zip(runs, res) if k == "table1"]
+    f4 = [brief(r, k, st, N) for (k, st, N, _, _), r in zip(runs, res) if k == "fig4"]
+    out = {"metric": METRIC, "value": upd / t_dev / 1e9, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": t_dev / args.steps * 1e3, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": "the paper's test problem (Sec. 3.3): Delta u = -(x^2+y^2) e^{xy} with the "
+                                  "Dirichlet data of u = -e^{xy}; plain FP64 CJM",
+                      "table1": "N = 1024, stencils 5/9/17, tol = N^-2",
+                      "fig4_right": "17-point N = 128 vs 5-point N = 2048, real error goal 1e-8",
+                      "l2_flush": "none: the 2048^2 arrays (34 MB) fit in L2; the timing is of whole solves"},
+           "table1": t3, "fig4_right": f4,
+           "fig4_sweep_ratio_5pt_over_17pt": f4[1]["sweeps"] / max(1, f4[0]["sweeps"]),
+           "fig4_time_ratio_5pt_over_17pt": f4[1]["time_s"] / max(1e-12, f4[0]["time_s"]),
+           "clocks": clk}
+    print(json.dumps(out), flush=True)
+
+
 def run_batch(args):
     """The batched workload (512 problems, sides log-uniform in [64, 2048], 5/9-point,
     tol 1e-8, FP32-inner / FP64-outer) through cj_solve_batch; each step one batch."""
@@ -477,6 +633,10 @@ def main(argv=None):
         raise SystemExit("--warmup must be >= 3")
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "highorder":
+        run_highorder(args)
+    elif args.workload == "paper":
+        run_paper(args)
     elif args.workload == "batch":
         run_batch(args)
     elif args.workload == "serve":

@@ -49,7 +49,11 @@ typedef enum {
 
 typedef enum { CJ_ST5 = 5, CJ_ST9 = 9, CJ_ST17 = 17 } cj_stencil;
 
-typedef enum { CJ_BC_DIRICHLET0 = 0 } cj_bc;
+typedef enum {
+    CJ_BC_DIRICHLET0 = 0,  /* homogeneous Dirichlet; 17-point: odd reflection for the 2nd ring */
+    CJ_BC_DIRICHLET = 1    /* Dirichlet data given at both rings around the interior (the paper's
+                              test problem, Sec. 3.3), set by cj_set_boundary; CJ_FP64 only */
+} cj_bc;
 
 typedef enum {
     CJ_FP64 = 0,          /* plain CJM: every sweep in FP64 */
@@ -149,6 +153,30 @@ cj_status cj_solve_history(cj_plan *plan, const double *f, long long ld_f, doubl
                            int cap, int *count);
 
 /*
+ * cj_solve_to_error -- plain FP64 CJM stopped by the real error instead of the residual
+ * (Sec. 3.4 and Fig. 4 right, where the analytic solution of the test problem of Sec. 3.3 is
+ * known and the solve runs until the infinity norm of u - u_exact reaches a goal).
+ *   f, u: as in cj_solve (device, Ny x ld doubles; u in/out).
+ *   u_exact: device, Ny x ld_exact doubles, the analytic solution at the interior nodes.
+ *   err_tol: the real-error goal (>= 0).
+ *   check_every: the real error is tested before every cycle and, when > 0, after every
+ *     check_every sweeps inside a cycle (0: at cycle ends only); the plan's tolerance sets
+ *     only the cycle length M.
+ *   history: host array of 2*cap doubles (may be NULL when cap = 0) receiving (sweeps done,
+ *     real error) at every test; *count (may be NULL) = number of tests made (may exceed cap).
+ *   *real_error (may be NULL): the real error at the last test.
+ * Returns CJ_OK when the goal is met; CJ_FLOOR when the residual, still evaluated before every
+ * cycle, stalls first (a goal below the discretisation error); CJ_ERR_NOT_CONVERGED when the
+ * sweep budget is spent; CJ_ERR_DIVERGED on a non-finite error; CJ_ERR_INVALID_ARG for a plan
+ * that is not CJ_FP64, a NULL u_exact, ld_exact < Nx, err_tol < 0 or check_every < 0.
+ * Works with either boundary type (cj_set_boundary data for CJ_BC_DIRICHLET plans).
+ */
+cj_status cj_solve_to_error(cj_plan *plan, const double *f, long long ld_f, double *u,
+                            long long ld_u, const double *u_exact, long long ld_exact,
+                            double err_tol, long long check_every, void *stream, cj_result *res,
+                            double *real_error, double *history, int cap, int *count);
+
+/*
  * cj_solve_host -- cj_solve for host arrays: copies f (Ny x Nx, ld = Nx) and the initial
  * guess u to the device in one transfer each, solves, and copies u back (Sec. 3.2:
  * one transfer in, one out).  u_host is in/out.
@@ -172,6 +200,18 @@ cj_status cj_sweeps(cj_plan *plan, const double *f, long long ld_f, double *u, l
  */
 cj_status cj_sweeps_f32(cj_plan *plan, const float *r, long long ld_r, float *e, long long ld_e,
                         long long first, long long count, void *stream);
+
+/*
+ * cj_set_boundary -- Dirichlet data of a CJ_BC_DIRICHLET plan (Sec. 3.3: "the analytic
+ * solution ... can be used to compute the boundaries"): g is a device array of Ny+4 rows of
+ * ld_g >= Nx+4 doubles with node (i, j), -1 <= i <= Nx+2, -1 <= j <= Ny+2, at
+ * g[(j+1)*ld_g + (i+1)]; only the two-node ring around the interior is read (the 5- and
+ * 9-point stencils use its inner ring only).  The values stay in the plan and are used by
+ * every later cj_solve / cj_sweeps / cj_residual of the plan until set again.  The error of
+ * the iteration then sees the operator with zero ghosts, whose spectrum lies inside the
+ * paper's [kmin, kmax], so the weights are unchanged.  Asynchronous on `stream`.
+ */
+cj_status cj_set_boundary(cj_plan *plan, const double *g, long long ld_g, void *stream);
 
 /*
  * cj_autotune_depth -- measure the FP32 sweep at temporal depths 1, 2, 4 and 8 on an Nx x Ny

@@ -19,7 +19,7 @@ CJ_OK, CJ_FLOOR, CJ_PENDING = 0, 1, 2
 CJ_ERR_INVALID_ARG, CJ_ERR_NOMEM, CJ_ERR_NOT_CONVERGED = -1, -2, -3
 CJ_ERR_DIVERGED, CJ_ERR_TIMEOUT, CJ_ERR_CUDA, CJ_ERR_BUDGET = -4, -5, -6, -7
 CJ_ST5, CJ_ST9, CJ_ST17 = 5, 9, 17
-CJ_BC_DIRICHLET0 = 0
+CJ_BC_DIRICHLET0, CJ_BC_DIRICHLET = 0, 1
 CJ_FP64, CJ_FP32_INNER, CJ_FP32_INNER_DD = 0, 1, 2
 
 
@@ -100,12 +100,18 @@ def _lib():
         L.cj_solve_history.argtypes = [_vp, _vp, _ll, _vp, _ll, _vp, ctypes.POINTER(cj_result),
                                        _dp, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]
         L.cj_solve_history.restype = ctypes.c_int
+        L.cj_solve_to_error.argtypes = [_vp, _vp, _ll, _vp, _ll, _vp, _ll, ctypes.c_double, _ll, _vp,
+                                        ctypes.POINTER(cj_result), _dp, _dp, ctypes.c_int,
+                                        ctypes.POINTER(ctypes.c_int)]
+        L.cj_solve_to_error.restype = ctypes.c_int
         L.cj_solve_host.argtypes = [_vp, _vp, _vp, _vp, ctypes.POINTER(cj_result)]
         L.cj_solve_host.restype = ctypes.c_int
         L.cj_sweeps.argtypes = [_vp, _vp, _ll, _vp, _ll, _ll, _ll, _vp]
         L.cj_sweeps.restype = ctypes.c_int
         L.cj_sweeps_f32.argtypes = [_vp, _vp, _ll, _vp, _ll, _ll, _ll, _vp]
         L.cj_sweeps_f32.restype = ctypes.c_int
+        L.cj_set_boundary.argtypes = [_vp, _vp, _ll, _vp]
+        L.cj_set_boundary.restype = ctypes.c_int
         L.cj_autotune_depth.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, _vp,
                                         ctypes.POINTER(ctypes.c_int), _dp]
         L.cj_autotune_depth.restype = ctypes.c_int
@@ -154,6 +160,9 @@ def _grid(t, dtype_name: str):
     return t.data_ptr(), t.stride(0)
 
 
+_plan_shape = {}   # plan handle -> (Nx, Ny), for the shape checks of the bindings
+
+
 def cj_plan_create(Nx: int, Ny: int, st: int, tol: float, precision: int = CJ_FP64,
                    literal_n: int = 0, inner_cycle: int = 0, max_sweeps: int = 0,
                    bc: int = CJ_BC_DIRICHLET0, temporal_depth: int = 0):
@@ -163,10 +172,12 @@ def cj_plan_create(Nx: int, Ny: int, st: int, tol: float, precision: int = CJ_FP
     rc = _lib().cj_plan_create(Nx, Ny, st, bc, tol, ctypes.byref(opt), ctypes.byref(h))
     if rc != CJ_OK:
         raise CJError(rc, "cj_plan_create")
+    _plan_shape[h.value] = (Nx, Ny)
     return h.value
 
 
 def cj_plan_destroy(plan) -> None:
+    _plan_shape.pop(plan, None)
     _lib().cj_plan_destroy(plan)
 
 
@@ -192,6 +203,31 @@ def cj_solve(plan, f, u, stream=None, check: bool = True) -> dict:
         raise CJError(rc, "cj_solve")
     d = res.as_dict()
     d["rc"] = rc
+    return d
+
+
+def cj_solve_to_error(plan, f, u, u_exact, err_tol: float, check_every: int = 0, stream=None,
+                      cap: int = 4096, check: bool = True) -> dict:
+    """Plain FP64 solve stopped by the real error max |u - u_exact| (device tensors; u in/out).
+    Returns the cj_result fields plus real_error and history ((sweeps, real error) per test)."""
+    fp, ldf = _grid(f, "float64")
+    up, ldu = _grid(u, "float64")
+    ep, lde = _grid(u_exact, "float64")
+    res = cj_result()
+    err = ctypes.c_double()
+    hist = np.zeros(2 * cap)
+    cnt = ctypes.c_int()
+    rc = _lib().cj_solve_to_error(plan, fp, ldf, up, ldu, ep, lde, err_tol, check_every,
+                                  _stream(stream), ctypes.byref(res), ctypes.byref(err),
+                                  hist.ctypes.data_as(_dp), cap, ctypes.byref(cnt))
+    if check and rc < 0 and rc not in (CJ_ERR_NOT_CONVERGED, CJ_ERR_DIVERGED):
+        raise CJError(rc, "cj_solve_to_error")
+    d = res.as_dict()
+    d["rc"] = rc
+    d["real_error"] = err.value
+    d["tests"] = cnt.value
+    k = min(cnt.value, cap)
+    d["history"] = hist[:2 * k].reshape(k, 2).copy()
     return d
 
 
@@ -241,6 +277,28 @@ def cj_sweeps_f32(plan, r, e, first: int, count: int, stream=None) -> None:
     rc = _lib().cj_sweeps_f32(plan, rp, ldr, ep, lde, first, count, _stream(stream))
     if rc != CJ_OK:
         raise CJError(rc, "cj_sweeps_f32")
+
+
+def dirichlet_ring(Nx: int, Ny: int, g) -> np.ndarray:
+    """Host array of shape (Ny+4, Nx+4) for cj_set_boundary: g(i, j) (vectorised over integer
+    node indices) at every node with i or j in {-1, 0, N+1, N+2}, zero inside."""
+    i = np.arange(-1, Nx + 3)[None, :]
+    j = np.arange(-1, Ny + 3)[:, None]
+    G = np.array(np.broadcast_to(g(i, j), (Ny + 4, Nx + 4)), dtype=np.float64)
+    G[2:Ny + 2, 2:Nx + 2] = 0.0
+    return G
+
+
+def cj_set_boundary(plan, g, stream=None) -> None:
+    """Dirichlet data of a CJ_BC_DIRICHLET plan: g is a CUDA float64 tensor of shape
+    (Ny+4, >= Nx+4) holding node (i, j) at g[j+1, i+1] (the two rings around the interior)."""
+    Nx, Ny = _plan_shape.get(plan, (0, 0))
+    if g.dim() != 2 or g.shape[0] != Ny + 4 or g.shape[1] < Nx + 4:
+        raise CJError(CJ_ERR_INVALID_ARG, "cj_set_boundary: g must have shape (Ny+4, >= Nx+4)")
+    gp, ld = _grid(g, "float64")
+    rc = _lib().cj_set_boundary(plan, gp, ld, _stream(stream))
+    if rc != CJ_OK:
+        raise CJError(rc, "cj_set_boundary")
 
 
 def cj_autotune_depth(Nx: int, Ny: int, st: int, sweeps: int = 64, stream=None) -> dict:

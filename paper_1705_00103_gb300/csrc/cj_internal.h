@@ -38,7 +38,7 @@ struct March {
 };
 
 struct cj_plan {
-    int Nx, Ny, st, r, precision, literal_n;
+    int Nx, Ny, st, r, precision, literal_n, bc;
     double tol, kmin, kmax, c, S, h2;
     long long M, M_in, max_sweeps;
     int depth = 1;            // FP32 sweeps per launch (temporal blocking depth)
@@ -73,6 +73,11 @@ March plan_march(int Nx, int Ny, int st, bool fp64);
 // caller grids -> padded b = h^2 f and u; red[3..4] = (sum b^2, max |b|)
 cudaError_t launch_import(const cj_plan *p, const double *f, long long ldf, const double *u,
                           long long ldu, double *b_out, double *u_out, cudaStream_t s);
+// Dirichlet data into the ghost ring of both FP64 solution buffers (CJ_BC_DIRICHLET plans)
+cudaError_t launch_set_ring(const cj_plan *p, const double *gdat, long long ldg, cudaStream_t s);
+// real error of u_pad against the caller's u_exact: red[5..6] = (sum d^2, max |d|)
+cudaError_t launch_real_error(const cj_plan *p, const double *u_pad, const double *ue, long long lde,
+                              cudaStream_t s);
 cudaError_t launch_export(const cj_plan *p, const double *u_pad, double *u, long long ldu,
                           cudaStream_t s);
 cudaError_t launch_sweep64(const cj_plan *p, const double *u, double *out, double w,

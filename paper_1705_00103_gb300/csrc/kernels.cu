@@ -28,20 +28,24 @@
 
 namespace {
 
-template <int ST, typename T>
+// Stores the updated node; for the 17-point stencil with MIRROR also its reflection ghosts
+// (without MIRROR the ghost ring holds fixed Dirichlet data).
+template <int ST, typename T, bool MIRROR = true>
 struct SweepOp {
     T *out;
     const Grid *g;
     int i;
     T w;
     __device__ __forceinline__ void operator()(int j, T r, T uc) {
-        store_node<(ST == 17 ? 2 : 1)>(out, *g, i, j, Ar<T>::fm(w, r, uc));
+        store_node<((ST == 17 && MIRROR) ? 2 : 1)>(out, *g, i, j, Ar<T>::fm(w, r, uc));
     }
 };
 
 // One weighted sweep: out = u + w (L u - b).  FP64 in the pair-sum order above; FP32 in the
 // difference form (march32), which keeps the smooth modes' digits on fine grids.
-template <int ST, typename T>
+// MIRROR: rewrite the odd-reflection ghosts of the 17-point stencil (homogeneous boundary);
+// without it the ghost ring holds fixed Dirichlet data and is left alone.
+template <int ST, typename T, bool MIRROR = true>
 __global__ void __launch_bounds__(kBX) sweep_kernel(const T *__restrict__ u,
                                                     const T *__restrict__ b, T *__restrict__ out,
                                                     Grid g, int ty, T w, T one) {
@@ -49,7 +53,7 @@ __global__ void __launch_bounds__(kBX) sweep_kernel(const T *__restrict__ u,
     const int j0 = blockIdx.y * ty + 1;
     const int j1 = min(j0 + ty - 1, g.Ny);
     if (i > g.Nx) return;
-    SweepOp<ST, T> op{out, &g, i, w};
+    SweepOp<ST, T, MIRROR> op{out, &g, i, w};
     if constexpr (sizeof(T) == 4)
         march32<ST, false>(u, b, g, i, j0, j1, op);
     else
@@ -243,8 +247,34 @@ cudaError_t launch_sweep64(const cj_plan *p, const double *u, double *out, doubl
     switch (p->st) {
         case 5: sweep_kernel<5, double><<<grid, kBX, 0, s>>>(u, p->b, out, p->g64, p->m64.ty, w, 1.0); break;
         case 9: sweep_kernel<9, double><<<grid, kBX, 0, s>>>(u, p->b, out, p->g64, p->m64.ty, w, 1.0); break;
-        default: sweep_kernel<17, double><<<grid, kBX, 0, s>>>(u, p->b, out, p->g64, p->m64.ty, w, 1.0); break;
+        default:
+            if (p->bc == CJ_BC_DIRICHLET)
+                sweep_kernel<17, double, false><<<grid, kBX, 0, s>>>(u, p->b, out, p->g64, p->m64.ty, w, 1.0);
+            else
+                sweep_kernel<17, double><<<grid, kBX, 0, s>>>(u, p->b, out, p->g64, p->m64.ty, w, 1.0);
+            break;
     }
+    return cudaGetLastError();
+}
+
+// Dirichlet data g (node (i, j) at g[(j+1) ldg + i+1], i, j in -1..N+2) into the ghost ring of
+// both FP64 solution buffers.
+__global__ void __launch_bounds__(256) ring_kernel(const double *__restrict__ gdat, long long ldg,
+                                                  double *u0, double *u1, Grid g) {
+    const long long W = g.Nx + 4, H = g.Ny + 4;
+    for (long long k = blockIdx.x * 256LL + threadIdx.x; k < W * H; k += (long long)gridDim.x * 256) {
+        const int i = (int)(k % W) - 1, j = (int)(k / W) - 1;
+        if (i >= 1 && i <= g.Nx && j >= 1 && j <= g.Ny) continue;
+        const double v = gdat[(long long)(j + 1) * ldg + (i + 1)];
+        u0[g.idx(i, j)] = v;
+        if (u1) u1[g.idx(i, j)] = v;
+    }
+}
+
+cudaError_t launch_set_ring(const cj_plan *p, const double *gdat, long long ldg, cudaStream_t s) {
+    const long long cells = (long long)(p->Nx + 4) * (p->Ny + 4);
+    const int blocks = (int)((cells + 255) / 256 < 4096 ? (cells + 255) / 256 : 4096);
+    ring_kernel<<<blocks, 256, 0, s>>>(gdat, ldg, p->u0, p->u1, p->g64);
     return cudaGetLastError();
 }
 
@@ -276,7 +306,7 @@ cudaError_t launch_residual(const cj_plan *p, const double *u_pad, float *rt, fl
 cudaError_t launch_import(const cj_plan *p, const double *f, long long ldf, const double *u,
                           long long ldu, double *b_out, double *u_out, cudaStream_t s) {
     dim3 grid = copy_grid(p->g64);
-    if (p->r == 2)
+    if (p->r == 2 && p->bc == CJ_BC_DIRICHLET0)
         import_kernel<2><<<grid, kBX, 0, s>>>(f, ldf, u, ldu, b_out, u_out, p->g64, p->h2, p->partials);
     else
         import_kernel<1><<<grid, kBX, 0, s>>>(f, ldf, u, ldu, b_out, u_out, p->g64, p->h2, p->partials);

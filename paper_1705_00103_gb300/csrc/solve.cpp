@@ -2,12 +2,14 @@
 // precalculated before starting the iterative algorithm", then M weighted sweeps per
 // cycle), the sweep and residual entry points.  Host C++; the device work is in
 // kernels.cu.
+#include <algorithm>
 #include <chrono>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <mutex>
 #include <new>
+#include <utility>
 
 #include "cj_internal.h"
 
@@ -93,6 +95,7 @@ struct History {
 
 struct Norms {
     double l2, inf, fl;
+    double err, err_sq;  // real error: max |u - u_exact| and sum (u - u_exact)^2 (red[5..6])
 };
 
 // Reads red[] (filled by the residual and import reductions) after a stream sync.  The
@@ -110,6 +113,8 @@ cj_status fetch_norms(cj_plan *p, cudaStream_t s, Norms *n, double eps = kEps) {
     n->l2 = bn > 0.0 ? rn / bn : rn;
     n->inf = bmax > 0.0 ? r[1] / bmax : r[1];
     n->fl = bn > 0.0 ? eps * p->S * un / bn : eps * p->S * un;
+    n->err_sq = r[5];
+    n->err = r[6];
     return CJ_OK;
 }
 
@@ -169,6 +174,112 @@ cj_status run_fp64(cj_plan *p, cudaStream_t s, double **cur_out, cj_result *res,
         sweeps += p->M;
         cycles += 1;
         prev = n.l2;
+    }
+    res->sweep_seconds = 1e-3 * sweep_ms;
+    *cur_out = cur;
+    res->sweeps = sweeps;
+    res->cycles = (int)cycles;
+    res->status = stat;
+    res->rel_res_l2 = n.l2;
+    res->rel_res_inf = n.inf;
+    res->floor_est = n.fl;
+    return (cj_status)stat;
+}
+
+// Real-error stop (Sec. 3.4, Fig. 4 right): plain FP64 cycles of the plan's length; the real
+// error E = max |u - u_exact| is tested before every cycle and every `every` sweeps inside one
+// (every = 0: at cycle ends only) and the solve stops at the first test with E <= err_tol.  The
+// residual is still evaluated before every cycle, for the floor part of the stop rule only (a
+// goal below the discretisation error ends with CJ_FLOOR once the residual stalls).  hist
+// receives (sweeps, E) pairs.
+struct ErrorStop {
+    const double *ue;
+    long long lde;
+    double tol;
+    long long every;
+    double *hist;
+    int cap, n;
+    void add(long long sweeps, double e) {
+        if (n < cap) {
+            hist[2 * n] = (double)sweeps;
+            hist[2 * n + 1] = e;
+        }
+        ++n;
+    }
+};
+
+cj_status run_fp64_to_error(cj_plan *p, cudaStream_t s, ErrorStop *es, double **cur_out,
+                            cj_result *res) {
+    double *cur = p->u0, *nxt = p->u1;
+    long long sweeps = 0, cycles = 0;
+    double prev = 0.0, sweep_ms = 0.0;
+    Norms n{};
+    int stat = -1, stall = 0;
+    bool mid = false;
+    for (;;) {
+        CJ_TRY(launch_residual(p, cur, nullptr, nullptr, s), "residual");
+        CJ_TRY(launch_real_error(p, cur, es->ue, es->lde, s), "real error");
+        res->launches += 4;
+        cj_status st = fetch_norms(p, s, &n);
+        if (st != CJ_OK) return st;
+        es->add(sweeps, n.err);
+        if (!(n.err_sq == n.err_sq) || n.err > 1e300) {
+            stat = CJ_ERR_DIVERGED;
+            break;
+        }
+        if (n.err <= es->tol) {
+            stat = CJ_OK;
+            break;
+        }
+        stat = stop_rule(n.l2, n.fl, prev, cycles, 0.0, 1, &stall);
+        if (stat == CJ_OK) stat = CJ_FLOOR;  // zero residual: u is the discrete solution
+        if (stat != -1) break;
+        if (sweeps + p->M > p->max_sweeps) {
+            stat = CJ_ERR_NOT_CONVERGED;
+            break;
+        }
+        for (long long k = 0; k < p->M;) {
+            const long long chunk = es->every > 0 ? std::min(es->every, p->M - k) : p->M - k;
+            CJ_TRY(cudaEventRecord(p->ev0, s), "event");
+            for (long long q = 0; q < chunk; ++q) {
+                CJ_TRY(launch_sweep64(p, cur, nxt, p->w[k + q], s), "sweep");
+                std::swap(cur, nxt);
+            }
+            CJ_TRY(cudaEventRecord(p->ev1, s), "event");
+            res->launches += chunk;
+            k += chunk;
+            sweeps += chunk;
+            if (k < p->M) {
+                CJ_TRY(launch_real_error(p, cur, es->ue, es->lde, s), "real error");
+                res->launches += 2;
+                st = fetch_norms(p, s, &n);
+                if (st != CJ_OK) return st;
+                sweep_ms += elapsed_ms(p);
+                es->add(sweeps, n.err);
+                if (!(n.err_sq == n.err_sq) || n.err > 1e300) {
+                    stat = CJ_ERR_DIVERGED;
+                    mid = true;
+                    break;
+                }
+                if (n.err <= es->tol) {
+                    stat = CJ_OK;
+                    mid = true;
+                    break;
+                }
+            } else {
+                CJ_TRY(cudaStreamSynchronize(s), "cycle sync");
+                sweep_ms += elapsed_ms(p);
+            }
+        }
+        if (mid) break;
+        cycles += 1;
+        prev = n.l2;
+    }
+    if (mid) {  // the residual where the solve stopped
+        CJ_TRY(launch_residual(p, cur, nullptr, nullptr, s), "residual");
+        res->launches += 2;
+        cj_status st = fetch_norms(p, s, &n);
+        if (st != CJ_OK) return st;
     }
     res->sweep_seconds = 1e-3 * sweep_ms;
     *cur_out = cur;
@@ -353,13 +464,14 @@ cj_status cj_plan_create(int Nx, int Ny, cj_stencil st, cj_bc bc, double tol,
     if (opt) o = *opt;
     if (Nx < 1 || Ny < 1 || Nx > (1 << 20) || Ny > (1 << 20)) return CJ_ERR_INVALID_ARG;
     if (st != CJ_ST5 && st != CJ_ST9 && st != CJ_ST17) return CJ_ERR_INVALID_ARG;
-    if (bc != CJ_BC_DIRICHLET0) return CJ_ERR_INVALID_ARG;
+    if (bc != CJ_BC_DIRICHLET0 && bc != CJ_BC_DIRICHLET) return CJ_ERR_INVALID_ARG;
     if (!(tol > 0.0 && tol < 1.0)) return CJ_ERR_INVALID_ARG;
     if (o.precision != CJ_FP64 && o.precision != CJ_FP32_INNER && o.precision != CJ_FP32_INNER_DD)
         return CJ_ERR_INVALID_ARG;
     if (o.inner_cycle != 0 && !is_pow2(o.inner_cycle)) return CJ_ERR_INVALID_ARG;
     if (o.max_sweeps < 0) return CJ_ERR_INVALID_ARG;
     if (o.temporal_depth < 0 || o.temporal_depth > kTbMaxDepth) return CJ_ERR_INVALID_ARG;
+    if (bc == CJ_BC_DIRICHLET && o.precision != CJ_FP64) return CJ_ERR_INVALID_ARG;
 
     cj_plan *p = new (std::nothrow) cj_plan();
     if (!p) return CJ_ERR_NOMEM;
@@ -370,6 +482,7 @@ cj_status cj_plan_create(int Nx, int Ny, cj_stencil st, cj_bc bc, double tol,
         p->r = st == CJ_ST17 ? 2 : 1;
         p->precision = o.precision;
         p->literal_n = o.literal_n ? 1 : 0;
+        p->bc = bc;
         p->tol = tol;
         plan_kappa_bounds(st, p->literal_n ? (double)Nx : (double)(Nx + 1),
                           p->literal_n ? (double)Ny : (double)(Ny + 1), &p->kmin, &p->kmax);
@@ -477,6 +590,34 @@ cj_status cj_solve_history(cj_plan *p, const double *f, long long ldf, double *u
     h.cap = cap;
     cj_status st = solve_core(p, f, ldf, u, ldu, (cudaStream_t)stream, res, &h);
     if (count) *count = h.n;
+    return st;
+}
+
+cj_status cj_solve_to_error(cj_plan *p, const double *f, long long ldf, double *u, long long ldu,
+                            const double *u_exact, long long ld_exact, double err_tol,
+                            long long check_every, void *stream, cj_result *res, double *real_error,
+                            double *history, int cap, int *count) {
+    cj_status a = check_grid_args(p, f, ldf, u, ldu);
+    if (a != CJ_OK) return a;
+    if (!u_exact || ld_exact < p->Nx || !(err_tol >= 0.0) || check_every < 0 || cap < 0 ||
+        (cap > 0 && !history) || p->precision != CJ_FP64)
+        return CJ_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    auto t0 = std::chrono::steady_clock::now();
+    cj_result r{};
+    ErrorStop es{u_exact, ld_exact, err_tol, check_every, history, cap, 0};
+    CJ_TRY(launch_import(p, f, ldf, u, ldu, p->b, p->u0, s), "import");
+    r.launches = 2;
+    double *cur = nullptr;
+    cj_status st = run_fp64_to_error(p, s, &es, &cur, &r);
+    if (count) *count = es.n;
+    if (st < 0 && st != CJ_ERR_NOT_CONVERGED && st != CJ_ERR_DIVERGED) return st;
+    CJ_TRY(launch_export(p, cur, u, ldu, s), "export");
+    r.launches += 1;
+    CJ_TRY(cudaStreamSynchronize(s), "solve sync");
+    r.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    if (res) *res = r;
+    if (real_error) *real_error = p->h_red[6];
     return st;
 }
 
@@ -589,6 +730,12 @@ cj_status cj_autotune_depth(int Nx, int Ny, cj_stencil st, int sweeps, void *str
     if (best_depth) *best_depth = best;
     if (gupd)
         for (int k = 0; k < 4; ++k) gupd[k] = rate[k];
+    return CJ_OK;
+}
+
+cj_status cj_set_boundary(cj_plan *p, const double *g, long long ldg, void *stream) {
+    if (!p || !g || p->bc != CJ_BC_DIRICHLET || ldg < p->Nx + 4) return CJ_ERR_INVALID_ARG;
+    CJ_TRY(launch_set_ring(p, g, ldg, (cudaStream_t)stream), "boundary ring");
     return CJ_OK;
 }
 

@@ -3,6 +3,7 @@ and rejects invalid arguments before touching the GPU."""
 import ctypes
 import os
 import re
+import numpy as np
 
 import pytest
 
@@ -25,7 +26,8 @@ def lib():
 def test_header_declares_the_boundary():
     names = _declared_functions()
     for n in ("cj_plan_create", "cj_plan_destroy", "cj_plan_info", "cj_solve", "cj_solve_host",
-              "cj_solve_history", "cj_solution_lo",
+              "cj_solve_history", "cj_solution_lo", "cj_set_boundary", "cj_solve_to_error", "cj_autotune_depth",
+              "cj_solve_batch", "cj_server_create", "cj_submit", "cj_poll",
               "cj_sweeps", "cj_sweeps_f32", "cj_residual", "cj_status_string", "cj_last_error"):
         assert n in names
 
@@ -45,7 +47,8 @@ def test_invalid_arguments_rejected_without_gpu():
     bad = [dict(Nx=0, Ny=4, st=5, tol=1e-6), dict(Nx=4, Ny=-1, st=5, tol=1e-6),
            dict(Nx=4, Ny=4, st=7, tol=1e-6), dict(Nx=4, Ny=4, st=9, tol=0.0),
            dict(Nx=4, Ny=4, st=9, tol=1.0), dict(Nx=4, Ny=4, st=17, tol=1e-6, inner_cycle=12),
-           dict(Nx=4, Ny=4, st=17, tol=1e-6, precision=3), dict(Nx=4, Ny=4, st=5, tol=1e-6, bc=1)]
+           dict(Nx=4, Ny=4, st=17, tol=1e-6, precision=3), dict(Nx=4, Ny=4, st=5, tol=1e-6, bc=2),
+           dict(Nx=4, Ny=4, st=9, tol=1e-6, bc=1, precision=1)]
     for kw in bad:
         with pytest.raises(cj.CJError) as ei:
             cj.cj_plan_create(**kw)
@@ -63,3 +66,13 @@ def test_status_strings(lib):
     assert lib.cj_status_string(0) == b"converged"
     assert lib.cj_status_string(1).startswith(b"stopped at")
     assert lib.cj_status_string(-6) == b"CUDA error"
+
+
+def test_dirichlet_ring_layout_matches_the_oracle():
+    """The binding's ring builder puts g(i, j) where the oracle's data array has it."""
+    import paper_1705_00103_gb300 as cj
+    from oracle import oracle as orc
+    import workloads
+    for Nx, Ny in [(1, 1), (5, 3), (17, 9)]:
+        _, _, g = workloads.paper_problem(Nx, Ny)
+        np.testing.assert_array_equal(cj.dirichlet_ring(Nx, Ny, g), orc.ghost_ring(Nx, Ny, g))

@@ -359,3 +359,113 @@ def test_solve_history_records_every_residual_test(cj, torch):
     h = res["history"]
     assert len(h) == res["cycles"] + 1 and h[0] == pytest.approx(1.0) and h[-1] == res["rel_res_l2"]
     assert res["rc"] == cj.CJ_OK and h[-1] <= 1e-10
+
+
+# ----------------------------------------------------------------- Dirichlet data (Sec. 3.3)
+
+def _ring(torch, Nx, Ny, g, ld_extra=3):
+    G = orc.ghost_ring(Nx, Ny, g)
+    Gd = torch.zeros((Ny + 4, Nx + 4 + ld_extra), dtype=torch.float64, device="cuda")
+    Gd[:, :Nx + 4] = torch.from_numpy(G).cuda()
+    return G, Gd
+
+
+@pytest.mark.parametrize("st", STENCILS)
+@pytest.mark.parametrize("Nx,Ny", [(1, 1), (17, 9), (130, 70)])
+def test_dirichlet_data_sweeps_bit_exact(cj, torch, st, Nx, Ny):
+    f, _, g = workloads.paper_problem(Nx, Ny)
+    u0 = np.random.default_rng(Nx + st).standard_normal((Ny, Nx))
+    G, Gd = _ring(torch, Nx, Ny, g)
+    with cj.Plan(Nx, Ny, st, 1e-8, bc=cj.CJ_BC_DIRICHLET) as p:
+        cj.cj_set_boundary(p.handle, Gd)
+        w = p.info()["w"]
+        fd, ud = dev(torch, f), dev(torch, u0)
+        b = orc.scale_rhs(f)
+        ref = u0.copy()
+        for k in range(min(5, len(w))):
+            cj.cj_sweeps(p.handle, fd, ud, k, 1)
+            ref = orc.sweep_bc(st, ref, G, b, w[k])
+            np.testing.assert_array_equal(ud.cpu().numpy(), ref, err_msg="sweep %d" % k)
+
+
+@pytest.mark.parametrize("st", STENCILS)
+@pytest.mark.parametrize("N,tol", [(64, 1e-10), (33, 1e-8)])
+def test_dirichlet_data_solve_matches_oracle(cj, torch, st, N, tol):
+    f, u_exact, g = workloads.paper_problem(N, N)
+    G, Gd = _ring(torch, N, N, g)
+    ref = orc.solve_bc(st, f, G, tol)
+    with cj.Plan(N, N, st, tol, bc=cj.CJ_BC_DIRICHLET) as p:
+        cj.cj_set_boundary(p.handle, Gd)
+        ud = torch.zeros((N, N), dtype=torch.float64, device="cuda")
+        res = cj.cj_solve(p.handle, dev(torch, f), ud)
+    assert res["sweeps"] == ref["sweeps"] and res["cycles"] == ref["cycles"]
+    np.testing.assert_array_equal(ud.cpu().numpy(), ref["u"])
+    # and it is the paper's problem: close to u = -e^{xy}
+    assert np.abs(ud.cpu().numpy() - u_exact).max() < 1e-3
+
+
+def test_dirichlet_data_argument_checks(cj, torch):
+    with pytest.raises(cj.CJError):
+        cj.cj_plan_create(16, 16, 9, 1e-8, bc=cj.CJ_BC_DIRICHLET, precision=cj.CJ_FP32_INNER)
+    g = torch.zeros((20, 20), dtype=torch.float64, device="cuda")
+    with cj.Plan(16, 16, 9, 1e-8) as p:
+        with pytest.raises(cj.CJError):
+            cj.cj_set_boundary(p.handle, g)
+    with cj.Plan(16, 16, 9, 1e-8, bc=cj.CJ_BC_DIRICHLET) as p:
+        with pytest.raises(cj.CJError):
+            cj.cj_set_boundary(p.handle, g[:, :19])
+
+
+# ----------------------------------------------------------------- real-error stop (Sec. 3.4)
+
+@pytest.mark.parametrize("st", STENCILS)
+@pytest.mark.parametrize("N,every,data", [(40, 0, True), (40, 37, True), (33, 16, False), (1, 0, True)])
+def test_solve_to_error_matches_oracle(cj, torch, st, N, every, data):
+    if data:
+        f, ue, g = workloads.paper_problem(N, N)
+        G, Gd = _ring(torch, N, N, g)
+        ref_u = orc.solve_bc(st, f, G, 1e-13)["u"]
+    else:
+        f, ue, G = workloads.manufactured_rhs(N, N), workloads.manufactured_solution(N, N), None
+        ref_u = orc.solve(st, f, 1e-13)["u"]
+    err_tol = orc.real_error(ref_u, ue) * 1.05 + 1e-9
+    ref = orc.solve_to_error(st, f, ue, 1e-4, err_tol, G=G, check_every=every)
+    with cj.Plan(N, N, st, 1e-4, bc=cj.CJ_BC_DIRICHLET if data else cj.CJ_BC_DIRICHLET0) as p:
+        if data:
+            cj.cj_set_boundary(p.handle, Gd)
+        ud = torch.zeros((N, N), dtype=torch.float64, device="cuda")
+        res = cj.cj_solve_to_error(p.handle, dev(torch, f), ud, dev(torch, ue), err_tol, every)
+    assert ref["status"] == "converged" and res["rc"] == cj.CJ_OK
+    assert res["sweeps"] == ref["sweeps"] and res["cycles"] == ref["cycles"]
+    assert res["tests"] == ref["tests"]
+    np.testing.assert_array_equal(res["history"], ref["history"])
+    np.testing.assert_array_equal(ud.cpu().numpy(), ref["u"])
+    assert res["real_error"] == ref["err"]
+    assert res["rel_res_l2"] == pytest.approx(ref["rel_l2"], rel=1e-10)
+
+
+def test_solve_to_error_goal_below_discretisation_error(cj, torch):
+    N, st = 31, 5
+    f, ue, g = workloads.paper_problem(N, N)
+    G, Gd = _ring(torch, N, N, g)
+    disc = orc.real_error(orc.solve_bc(st, f, G, 1e-13)["u"], ue)
+    ref = orc.solve_to_error(st, f, ue, 1e-8, disc / 2, G=G)
+    with cj.Plan(N, N, st, 1e-8, bc=cj.CJ_BC_DIRICHLET) as p:
+        cj.cj_set_boundary(p.handle, Gd)
+        ud = torch.zeros((N, N), dtype=torch.float64, device="cuda")
+        res = cj.cj_solve_to_error(p.handle, dev(torch, f), ud, dev(torch, ue), disc / 2)
+    assert ref["status"] == "floor" and res["rc"] == cj.CJ_FLOOR
+    assert res["sweeps"] == ref["sweeps"]
+    np.testing.assert_array_equal(ud.cpu().numpy(), ref["u"])
+
+
+def test_solve_to_error_argument_checks(cj, torch):
+    z = torch.zeros((8, 8), dtype=torch.float64, device="cuda")
+    with cj.Plan(8, 8, 9, 1e-6, precision=cj.CJ_FP32_INNER) as p:
+        with pytest.raises(cj.CJError):
+            cj.cj_solve_to_error(p.handle, z, z.clone(), z, 1e-3)
+    with cj.Plan(8, 8, 9, 1e-6) as p:
+        with pytest.raises(cj.CJError):
+            cj.cj_solve_to_error(p.handle, z, z.clone(), z, -1.0)
+        with pytest.raises(cj.CJError):
+            cj.cj_solve_to_error(p.handle, z, z.clone(), z, 1e-3, check_every=-2)
