@@ -62,6 +62,8 @@
  *      ring around the interior and stay fixed (see orc_solve_bc).
  *   R16 real-error stop (Sec. 3.4, Fig. 4 right): the infinity norm of u - u_exact tested
  *      before every cycle and every check_every sweeps (see orc_solve_to_error).
+ *   R18 classical Jacobi (the comparison method of Sec. 3.4): omega = 1, residual tested every
+ *      M sweeps (see orc_solve_jacobi).
  *
  * Array convention: interior values only, row-major [Ny][Nx], value of node (i, j) at
  * u[(j-1)*Nx + (i-1)].  Compiled with -ffp-contract=off so that every rounding is the
@@ -815,6 +817,64 @@ long orc_solve_to_error(int st, int Nx, int Ny, const double *f, const double *G
     *err = E;
     *rel_l2 = rl2;
     *cycles = cyc;
+    *status = stat;
+    return sweeps;
+}
+
+/* ---------------------------------------------------------------- classical Jacobi */
+
+/* Classical Jacobi (omega = 1, the paper's comparison method, Sec. 3.4 and Table 1), reading
+ * R18: every sweep uses w = 1/c; the residual of R8 is tested every M sweeps, M the CJM cycle
+ * length of the same tolerance (R2); stops converged at rho <= tol, "floor" at rho <= 4 fl or
+ * when an interval of M sweeps did not lower rho (Jacobi's residual falls monotonically in
+ * exact arithmetic), "diverged" on a non-finite rho.  G = NULL: homogeneous Dirichlet (R6);
+ * else the Dirichlet data of R15.  *intervals = the M-sweep intervals done. */
+long orc_solve_jacobi(int st, int Nx, int Ny, const double *f, const double *G, double tol,
+                      long max_sweeps, double *u, double *rel_l2, double *rel_linf,
+                      long *intervals, int *status) {
+    if (Nx < 1 || Ny < 1 || !(tol > 0.0 && tol < 1.0)) return -1;
+    size_t n = (size_t)Nx * (size_t)Ny;
+    double kmin, kmax;
+    orc_kappa_bounds(st, Nx, Ny, &kmin, &kmax);
+    long M = orc_cycle_length(kmin, kmax, tol);
+    double w = 1.0 / orc_centre(st);
+    double *b = (double *)malloc(sizeof(double) * n);
+    double *v = (double *)malloc(sizeof(double) * n);
+    orc_scale_rhs(Nx, Ny, f, b);
+    double bsq = 0.0, bmax = 0.0;
+    for (size_t k = 0; k < n; ++k) {
+        bsq += b[k] * b[k];
+        if (fabs(b[k]) > bmax) bmax = fabs(b[k]);
+    }
+    double bn = sqrt(bsq), eps = ldexp(1.0, -53), S = orc_abs_coeff_sum(st);
+    long sweeps = 0, done = 0;
+    int stat;
+    double rl2 = 0.0, rinf = 0.0, prev = 0.0;
+    for (;;) {
+        double sq, mx, usq = 0.0;
+        if (G) orc_residual_bc(st, Nx, Ny, u, G, b, &sq, &mx);
+        else orc_residual(st, Nx, Ny, u, b, &sq, &mx);
+        for (size_t k = 0; k < n; ++k) usq += u[k] * u[k];
+        rl2 = bn > 0.0 ? sqrt(sq) / bn : sqrt(sq);
+        rinf = bmax > 0.0 ? mx / bmax : mx;
+        double fl = bn > 0.0 ? eps * S * sqrt(usq) / bn : eps * S * sqrt(usq);
+        if (rl2 <= tol) { stat = ORC_CONVERGED; break; }
+        if (!(rl2 == rl2) || rl2 > 1e300) { stat = ORC_DIVERGED; break; }
+        if (rl2 <= 4.0 * fl || (done > 0 && rl2 >= prev)) { stat = ORC_FLOOR; break; }
+        if (sweeps + M > max_sweeps) { stat = ORC_MAX_SWEEPS; break; }
+        for (long s = 0; s < M; ++s) {
+            if (G) orc_sweep_bc(st, Nx, Ny, u, G, b, w, v);
+            else orc_sweep(st, Nx, Ny, u, b, w, v);
+            memcpy(u, v, sizeof(double) * n);
+        }
+        sweeps += M;
+        done += 1;
+        prev = rl2;
+    }
+    free(b); free(v);
+    *rel_l2 = rl2;
+    *rel_linf = rinf;
+    *intervals = done;
     *status = stat;
     return sweeps;
 }

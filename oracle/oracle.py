@@ -77,6 +77,9 @@ def lib():
         L.orc_solve_bc.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, _dp, _dp, ctypes.c_double,
                                    ctypes.c_long, _dp, _dp, _dp, _lp, _ip]
         L.orc_solve_bc.restype = ctypes.c_long
+        L.orc_solve_jacobi.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, _dp, _dp, ctypes.c_double,
+                                       ctypes.c_long, _dp, _dp, _dp, _lp, ctypes.POINTER(ctypes.c_int)]
+        L.orc_solve_jacobi.restype = ctypes.c_long
         L.orc_real_error.argtypes = [ctypes.c_int, ctypes.c_int, _dp, _dp]
         L.orc_real_error.restype = ctypes.c_double
         L.orc_solve_to_error.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, _dp, _dp, _dp,
@@ -336,3 +339,20 @@ def solve_to_error(st: int, f: np.ndarray, u_exact: np.ndarray, tol: float, err_
     return dict(u=u, sweeps=n, cycles=cyc.value, err=err.value, rel_l2=rl2.value,
                 status=STATUS[stat.value], tests=cnt.value,
                 history=hist[:2 * k].reshape(k, 2).copy())
+
+
+def solve_jacobi(st: int, f: np.ndarray, tol: float, G: np.ndarray | None = None,
+                 u0: np.ndarray | None = None, max_sweeps: int = 1 << 40) -> dict:
+    """Classical Jacobi (omega = 1) with the residual tested every M sweeps (orc_solve_jacobi)."""
+    f = _grid(f)
+    Gp = None if G is None else _d(_grid(G))
+    u = np.zeros_like(f) if u0 is None else _grid(u0).copy()
+    rl2, rinf = ctypes.c_double(), ctypes.c_double()
+    done, stat = ctypes.c_long(), ctypes.c_int()
+    n = lib().orc_solve_jacobi(st, f.shape[1], f.shape[0], _d(f), Gp, tol, max_sweeps, _d(u),
+                               ctypes.byref(rl2), ctypes.byref(rinf), ctypes.byref(done),
+                               ctypes.byref(stat))
+    if n < 0:
+        raise ValueError("bad argument")
+    return dict(u=u, sweeps=n, cycles=done.value, rel_l2=rl2.value, rel_linf=rinf.value,
+                status=STATUS[stat.value], converged=stat.value == 0)

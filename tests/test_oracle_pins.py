@@ -732,3 +732,52 @@ def test_high_order_reaches_a_real_error_on_a_coarser_mesh():
     f, ue, g = workloads.paper_problem(63, 63)
     lo = orc.solve_to_error(5, f, ue, 1e-8, goal, G=orc.ghost_ring(63, 63, g))
     assert lo["status"] == "converged" and lo["sweeps"] > hi["sweeps"]
+
+
+# ----------------------------------------------------------------- classical Jacobi (Sec. 3.4)
+
+@pytest.mark.parametrize("st", STENCILS)
+@pytest.mark.parametrize("N,tol", [(15, 1e-6), (24, 1e-4)])
+def test_jacobi_damps_the_lowest_mode_by_one_minus_kmin_per_sweep(st, N, tol):
+    """omega = 1 multiplies the lowest sine mode by (1 - kmin) per sweep, kmin the paper's bound
+    (exact for that mode), so the sweep count and the final residual follow in closed form."""
+    h = 1.0 / (N + 1)
+    x = np.arange(1, N + 1) * h
+    f = np.outer(np.sin(np.pi * x), np.sin(np.pi * x))
+    out = orc.solve_jacobi(st, f, tol)
+    kmin, kmax = orc.kappa_bounds(st, N, N)
+    M = orc.cycle_length(kmin, kmax, tol)
+    q = 1.0 - kmin
+    n = int(np.ceil(np.log(tol) / (M * np.log(q))))
+    assert out["status"] == "converged" and out["sweeps"] == n * M and out["cycles"] == n
+    assert out["rel_l2"] == pytest.approx(q ** (n * M), rel=1e-8)
+
+
+@pytest.mark.parametrize("st", STENCILS)
+def test_jacobi_solution_with_data_matches_dense(st):
+    Nx, Ny = 7, 6
+    f, _, g = workloads.paper_problem(Nx, Ny)
+    G = orc.ghost_ring(Nx, Ny, g)
+    out = orc.solve_jacobi(st, f, 1e-12, G=G)
+    assert out["status"] in ("converged", "floor") and out["rel_l2"] < 1e-11
+    h = 1.0 / (Nx + 1)
+    rhs = (h * h * f - _ghost_term(st, Nx, Ny, G)).ravel()
+    ref = np.linalg.solve(_dense_zero_ghost(st, Nx, Ny), rhs).reshape(Ny, Nx)
+    np.testing.assert_allclose(out["u"], ref, rtol=0, atol=1e-10 * np.abs(ref).max())
+
+
+def test_jacobi_needs_far_more_sweeps_than_cjm():
+    f = workloads.smooth_random_rhs(31, 31, 4)
+    j = orc.solve_jacobi(9, f, 1e-8)
+    c = orc.solve(9, f, 1e-8)
+    assert j["status"] == c["status"] == "converged"
+    assert j["sweeps"] > 10 * c["sweeps"]
+    np.testing.assert_allclose(j["u"], c["u"], rtol=0, atol=1e-7 * np.abs(c["u"]).max())
+
+
+def test_jacobi_budget_and_argument_checks():
+    f = workloads.smooth_random_rhs(20, 20, 1)
+    out = orc.solve_jacobi(5, f, 1e-10, max_sweeps=100)
+    assert out["status"] == "max_sweeps" and out["sweeps"] <= 100
+    with pytest.raises(ValueError):
+        orc.solve_jacobi(5, f, 0.0)
