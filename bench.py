@@ -64,6 +64,8 @@ def parse_args(argv=None):
                          "right); batch: the 512-problem batched workload; serve: a "
                          "bounded sample of the request stream")
     ap.add_argument("--serve-requests", type=int, default=48)
+    ap.add_argument("--no-jacobi", action="store_true",
+                    help="paper workload: skip the classical Jacobi solves of Table 1 (minutes)")
     return ap.parse_args(argv)
 
 
@@ -397,14 +399,15 @@ def run_highorder(args):
     print(json.dumps(out), flush=True)
 
 
-def paper_solve(cj, torch, N, st, tol, stream, err_goal=None, check_every=0):
+def paper_solve(cj, torch, N, st, tol, stream, err_goal=None, check_every=0, method=0):
     """One solve of the paper's test problem (Sec. 3.3) with its Dirichlet data: to the
-    relative residual tol, or, with err_goal, to that real error (Sec. 3.4)."""
+    relative residual tol, or, with err_goal, to that real error (Sec. 3.4); method 1 is
+    classical Jacobi."""
     import workloads
     f, ue, g = workloads.paper_problem(N, N)
     fd, ued, Gd = f_to(torch, f), f_to(torch, ue), f_to(torch, cj.dirichlet_ring(N, N, g))
     u = torch.zeros_like(fd)
-    with cj.Plan(N, N, st, tol, bc=cj.CJ_BC_DIRICHLET) as p:
+    with cj.Plan(N, N, st, tol, bc=cj.CJ_BC_DIRICHLET, method=method) as p:
         cj.cj_set_boundary(p.handle, Gd, stream)
         M = p.info()["M"]
         every = max(1, M // 64) if check_every else 0
@@ -427,12 +430,45 @@ def f_to(torch, a):
     return torch.from_numpy(np.ascontiguousarray(a)).cuda()
 
 
+def table1_ratios(cj, torch, stream, t3, N, tol):
+    """Table 1 on this machine: classical Jacobi on the GPU (one solve per stencil, timed with
+    CUDA events), and the serial times of both methods extrapolated from the single-threaded
+    C oracle's time per sweep on the same grid (the two methods' sweeps cost the same there)
+    times each method's sweep count.  ratios["a/b"] = time of a / time of b."""
+    import workloads
+    from oracle import oracle as orc
+    for row in t3:
+        st = row["stencil"]
+        j = paper_solve(cj, torch, N, st, tol, stream, method=1)
+        f, _, g = workloads.paper_problem(N, N)
+        G = orc.ghost_ring(N, N, g)
+        b = orc.scale_rhs(f)
+        u = np.zeros_like(f)
+        t0 = time.perf_counter()
+        k = 0
+        while k < 3 or time.perf_counter() - t0 < 1.0:
+            u = orc.sweep_bc(st, u, G, b, 0.25)
+            k += 1
+        per = (time.perf_counter() - t0) / k
+        t = {"j": j["sweeps"] * per, "j_gpu": j["time_s"], "cj": row["sweeps"] * per, "cj_gpu": row["time_s"]}
+        row["jacobi_gpu"] = {"sweeps": j["sweeps"], "time_s": j["time_s"], "intervals": j["cycles"],
+                             "status": cj.cj_status_string(j["rc"]), "rel_res_l2": j["rel_res_l2"],
+                             "real_error": j["real_error_final"]}
+        row["serial_oracle_s_per_sweep"] = per
+        row["serial_note"] = "j and cj serial times = sweeps x the oracle's time per sweep (%d sweeps timed)" % k
+        row["ratios"] = {"%s/%s" % (a, c): t[a] / t[c] for a, c in
+                         [("j", "j_gpu"), ("j", "cj"), ("j", "cj_gpu"), ("j_gpu", "cj"), ("j_gpu", "cj_gpu"),
+                          ("cj", "cj_gpu")]}
+
+
 def run_paper(args):
     """The paper's own experiments on its test problem (Sec. 3.3, u = -e^{xy}) with plain FP64
     CJM: (a) the N = 1024 point of Fig. 3 / Table 1 for the 5-, 9- and 17-point stencils, tol =
     N^-2; (b) Fig. 4 right: the 17-point stencil on N = 128 and the 5-point one on N = 2048,
     each until the real error reaches 1e-8 (tested every M/64 sweeps).  A step runs all five
-    solves; value = their grid-point updates per second."""
+    solves; value = their grid-point updates per second.  After the timed steps, unless
+    --no-jacobi, classical Jacobi solves the N = 1024 problems once each for the Table 1
+    ratios (table1_ratios)."""
     import torch
 
     import paper_1705_00103_gb300 as cj
@@ -471,6 +507,8 @@ def run_paper(args):
         return d
 
     t3 = [brief(r, k, st, N) for (k, st, N, _, _), r in zip(runs, res) if k == "table1"]
+    if not args.no_jacobi:
+        table1_ratios(cj, torch, stream, t3, N3, tol3)
     f4 = [brief(r, k, st, N) for (k, st, N, _, _), r in zip(runs, res) if k == "fig4"]
     out = {"metric": METRIC, "value": upd / t_dev / 1e9, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": t_dev / args.steps * 1e3, "higher_is_better": True,

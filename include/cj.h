@@ -64,6 +64,15 @@ typedef enum {
                              below the FP64 floor (see cj_result.floor_est) */
 } cj_precision;
 
+typedef enum {
+    CJ_CJM = 0,     /* Chebyshev-Jacobi: the weights of Sec. 2.1, one cycle of M sweeps between
+                       residual tests */
+    CJ_JACOBI = 1   /* classical Jacobi (omega = 1 at every sweep), the paper's comparison
+                       method (Sec. 3.4, Table 1); the residual is tested every M sweeps, M the
+                       CJM cycle length of the same tolerance; it stops at the floor when an
+                       interval does not lower the residual.  CJ_FP64 only */
+} cj_method;
+
 /* Optional plan settings; pass NULL for the defaults (all fields 0). */
 typedef struct {
     int precision;          /* cj_precision (default CJ_FP64) */
@@ -73,7 +82,9 @@ typedef struct {
     int temporal_depth;     /* FP32-inner modes: sweeps fused per HBM round trip (temporal
                                blocking), 1..8; 0 = auto: 4 for the 5- and 9-point stencils
                                on grids of at least 2^20 nodes, else 1 */
-    long long max_sweeps;   /* sweep budget of one solve; 0 = 64 cycles */
+    long long max_sweeps;   /* sweep budget of one solve; 0 = 64 cycles (CJ_JACOBI: the larger
+                               of 64 intervals and 4 ln(1/tol) / kmin sweeps) */
+    int method;             /* cj_method (default CJ_CJM) */
 } cj_options;
 
 /* What one solve did.  The relative residuals are those of the returned u:

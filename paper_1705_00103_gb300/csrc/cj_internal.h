@@ -39,6 +39,7 @@ struct March {
 
 struct cj_plan {
     int Nx, Ny, st, r, precision, literal_n, bc;
+    int method = 0;           // cj_method: CJ_CJM or CJ_JACOBI (every w_n = 1/c)
     double tol, kmin, kmax, c, S, h2;
     long long M, M_in, max_sweeps;
     int depth = 1;            // FP32 sweeps per launch (temporal blocking depth)

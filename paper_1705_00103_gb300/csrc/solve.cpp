@@ -83,6 +83,15 @@ int stop_rule(double rho, double fl, double prev, long long cycles, double tol, 
     return -1;
 }
 
+// Stop rule of classical Jacobi, tested every M sweeps: its residual falls monotonically in
+// exact arithmetic, so an interval that did not lower it has reached the rounding floor.
+int jacobi_stop_rule(double rho, double fl, double prev, long long intervals, double tol) {
+    if (rho <= tol) return CJ_OK;
+    if (!(rho == rho) || rho > 1e300) return CJ_ERR_DIVERGED;
+    if (rho <= 4.0 * fl || (intervals > 0 && rho >= prev)) return CJ_FLOOR;
+    return -1;
+}
+
 // Optional convergence history of the call in progress (rho at every residual test).
 struct History {
     double *buf = nullptr;
@@ -155,7 +164,8 @@ cj_status run_fp64(cj_plan *p, cudaStream_t s, double **cur_out, cj_result *res,
         if (st != CJ_OK) return st;
         if (timed) sweep_ms += elapsed_ms(p);
         h->add(n.l2);
-        stat = stop_rule(n.l2, n.fl, prev, cycles, p->tol, 1, &stall);
+        stat = p->method == CJ_JACOBI ? jacobi_stop_rule(n.l2, n.fl, prev, cycles, p->tol)
+                                      : stop_rule(n.l2, n.fl, prev, cycles, p->tol, 1, &stall);
         if (stat != -1) break;
         if (sweeps + p->M > p->max_sweeps) {
             stat = CJ_ERR_NOT_CONVERGED;
@@ -472,6 +482,8 @@ cj_status cj_plan_create(int Nx, int Ny, cj_stencil st, cj_bc bc, double tol,
     if (o.max_sweeps < 0) return CJ_ERR_INVALID_ARG;
     if (o.temporal_depth < 0 || o.temporal_depth > kTbMaxDepth) return CJ_ERR_INVALID_ARG;
     if (bc == CJ_BC_DIRICHLET && o.precision != CJ_FP64) return CJ_ERR_INVALID_ARG;
+    if (o.method != CJ_CJM && o.method != CJ_JACOBI) return CJ_ERR_INVALID_ARG;
+    if (o.method == CJ_JACOBI && o.precision != CJ_FP64) return CJ_ERR_INVALID_ARG;
 
     cj_plan *p = new (std::nothrow) cj_plan();
     if (!p) return CJ_ERR_NOMEM;
@@ -499,7 +511,11 @@ cj_status cj_plan_create(int Nx, int Ny, cj_stencil st, cj_bc bc, double tol,
             free_plan(p);
             return CJ_ERR_INVALID_ARG;
         }
-        plan_sweep_coeffs(st, p->kmin, p->kmax, p->M, p->w);
+        p->method = o.method;
+        if (p->method == CJ_JACOBI)
+            p->w.assign((size_t)p->M, 1.0 / p->c);  // omega = 1: w = 1/c at every sweep
+        else
+            plan_sweep_coeffs(st, p->kmin, p->kmax, p->M, p->w);
         p->M_in = 0;
         if (p->precision != CJ_FP64) {
             p->M_in = o.inner_cycle ? o.inner_cycle : plan_inner_cycle(p->kmin, p->kmax, p->M);
@@ -517,6 +533,12 @@ cj_status cj_plan_create(int Nx, int Ny, cj_stencil st, cj_bc bc, double tol,
                                     : (st != CJ_ST17 && (long long)Nx * Ny >= (1LL << 20) ? 4 : 1);
         long long unit = p->precision != CJ_FP64 ? p->M_in : p->M;
         p->max_sweeps = o.max_sweeps ? o.max_sweeps : 64 * unit;
+        if (p->method == CJ_JACOBI && !o.max_sweeps) {
+            // Jacobi's lowest mode falls by 1 - kmin per sweep: ln(1/tol)/kmin sweeps, x 4
+            const double need = 4.0 * std::log(1.0 / tol) / p->kmin;
+            if (need > (double)p->max_sweeps)
+                p->max_sweeps = need < 9e15 ? (long long)need : (1LL << 53);
+        }
     } catch (...) {
         free_plan(p);
         return CJ_ERR_NOMEM;
@@ -600,7 +622,7 @@ cj_status cj_solve_to_error(cj_plan *p, const double *f, long long ldf, double *
     cj_status a = check_grid_args(p, f, ldf, u, ldu);
     if (a != CJ_OK) return a;
     if (!u_exact || ld_exact < p->Nx || !(err_tol >= 0.0) || check_every < 0 || cap < 0 ||
-        (cap > 0 && !history) || p->precision != CJ_FP64)
+        (cap > 0 && !history) || p->precision != CJ_FP64 || p->method != CJ_CJM)
         return CJ_ERR_INVALID_ARG;
     cudaStream_t s = (cudaStream_t)stream;
     auto t0 = std::chrono::steady_clock::now();

@@ -469,3 +469,37 @@ def test_solve_to_error_argument_checks(cj, torch):
             cj.cj_solve_to_error(p.handle, z, z.clone(), z, -1.0)
         with pytest.raises(cj.CJError):
             cj.cj_solve_to_error(p.handle, z, z.clone(), z, 1e-3, check_every=-2)
+
+
+# ----------------------------------------------------------------- classical Jacobi (Sec. 3.4)
+
+@pytest.mark.parametrize("st", STENCILS)
+@pytest.mark.parametrize("Nx,Ny,tol,data", [(30, 21, 1e-6, False), (33, 33, 1e-5, True), (1, 1, 1e-8, False)])
+def test_jacobi_solve_matches_oracle(cj, torch, st, Nx, Ny, tol, data):
+    if data:
+        f, _, g = workloads.paper_problem(Nx, Ny)
+        G, Gd = _ring(torch, Nx, Ny, g)
+    else:
+        f, G = workloads.smooth_random_rhs(Nx, Ny, 8), None
+    ref = orc.solve_jacobi(st, f, tol, G=G)
+    with cj.Plan(Nx, Ny, st, tol, method=cj.CJ_JACOBI,
+                 bc=cj.CJ_BC_DIRICHLET if data else cj.CJ_BC_DIRICHLET0) as p:
+        assert set(p.info()["w"]) == {1.0 / orc.centre(st)}
+        if data:
+            cj.cj_set_boundary(p.handle, Gd)
+        ud = torch.zeros((Ny, Nx), dtype=torch.float64, device="cuda")
+        res = cj.cj_solve(p.handle, dev(torch, f), ud)
+    assert res["sweeps"] == ref["sweeps"] and res["cycles"] == ref["cycles"]
+    assert {0: "converged", 1: "floor"}[res["status"]] == ref["status"]
+    np.testing.assert_array_equal(ud.cpu().numpy(), ref["u"])
+
+
+def test_jacobi_argument_checks(cj, torch):
+    with pytest.raises(cj.CJError):
+        cj.cj_plan_create(8, 8, 9, 1e-6, method=2)
+    with pytest.raises(cj.CJError):
+        cj.cj_plan_create(8, 8, 9, 1e-6, method=cj.CJ_JACOBI, precision=cj.CJ_FP32_INNER)
+    z = torch.zeros((8, 8), dtype=torch.float64, device="cuda")
+    with cj.Plan(8, 8, 9, 1e-6, method=cj.CJ_JACOBI) as p:
+        with pytest.raises(cj.CJError):
+            cj.cj_solve_to_error(p.handle, z, z.clone(), z, 1e-3)
