@@ -85,6 +85,10 @@ typedef struct {
     long long max_sweeps;   /* sweep budget of one solve; 0 = 64 cycles (CJ_JACOBI: the larger
                                of 64 intervals and 4 ln(1/tol) / kmin sweeps) */
     int method;             /* cj_method (default CJ_CJM) */
+    int launch;             /* plain FP64 cycles: 0 = auto (a CUDA graph of the cycle's sweeps on
+                               grids of up to 2^22 nodes, where one sweep is shorter than a host
+                               launch; one launch per sweep above), 1 = one launch per sweep,
+                               2 = the graph at any size (needs an even M) */
 } cj_options;
 
 /* What one solve did.  The relative residuals are those of the returned u:

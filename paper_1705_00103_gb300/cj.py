@@ -22,12 +22,13 @@ CJ_ST5, CJ_ST9, CJ_ST17 = 5, 9, 17
 CJ_BC_DIRICHLET0, CJ_BC_DIRICHLET = 0, 1
 CJ_FP64, CJ_FP32_INNER, CJ_FP32_INNER_DD = 0, 1, 2
 CJ_CJM, CJ_JACOBI = 0, 1
+CJ_LAUNCH_AUTO, CJ_LAUNCH_STREAM, CJ_LAUNCH_GRAPH = 0, 1, 2
 
 
 class cj_options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("literal_n", ctypes.c_int),
                 ("inner_cycle", ctypes.c_int), ("temporal_depth", ctypes.c_int),
-                ("max_sweeps", ctypes.c_longlong), ("method", ctypes.c_int)]
+                ("max_sweeps", ctypes.c_longlong), ("method", ctypes.c_int), ("launch", ctypes.c_int)]
 
 
 class cj_result(ctypes.Structure):
@@ -166,9 +167,10 @@ _plan_shape = {}   # plan handle -> (Nx, Ny), for the shape checks of the bindin
 
 def cj_plan_create(Nx: int, Ny: int, st: int, tol: float, precision: int = CJ_FP64,
                    literal_n: int = 0, inner_cycle: int = 0, max_sweeps: int = 0,
-                   bc: int = CJ_BC_DIRICHLET0, temporal_depth: int = 0, method: int = 0):
+                   bc: int = CJ_BC_DIRICHLET0, temporal_depth: int = 0, method: int = 0,
+                   launch: int = 0):
     """Returns a plan handle (int); free it with cj_plan_destroy."""
-    opt = cj_options(precision, literal_n, inner_cycle, temporal_depth, max_sweeps, method)
+    opt = cj_options(precision, literal_n, inner_cycle, temporal_depth, max_sweeps, method, launch)
     h = _vp()
     rc = _lib().cj_plan_create(Nx, Ny, st, bc, tol, ctypes.byref(opt), ctypes.byref(h))
     if rc != CJ_OK:

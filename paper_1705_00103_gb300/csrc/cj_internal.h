@@ -55,6 +55,12 @@ struct cj_plan {
     double *h_red = nullptr;                              // pinned copy of red
     int max_parts = 0;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;             // brackets of a cycle's sweeps
+    // FP64 cycle as a CUDA graph (small grids, graph.cu): device weight table, table position,
+    // the instantiated graph of graph_G sweeps + position advance
+    double *w_dev = nullptr;
+    long long *pos = nullptr;
+    cudaGraphExec_t graph = nullptr;
+    int graph_G = 0;
 };
 
 // ---- plan math (plan.cpp)
@@ -68,6 +74,14 @@ void plan_sweep_coeffs(int st, double kmin, double kmax, long long M, std::vecto
 // ---- error reporting (solve.cpp)
 void set_cuda_error(cudaError_t e, const char *where);
 void set_error_text(const char *msg);
+
+// ---- FP64 cycles as CUDA graphs (graph.cu)
+// true when the plan's grid is small enough for its sweeps to be bound by host launches
+bool sweep_graph_wanted(const cj_plan *p);
+// builds p->w_dev, p->pos and p->graph (call once, on the plan's device)
+cudaError_t make_sweep_graph(cj_plan *p);
+// one full cycle (p->M sweeps from u0, ending in u0) on stream s
+cudaError_t launch_sweep_cycle_graph(const cj_plan *p, cudaStream_t s);
 
 // ---- kernel launchers (kernels.cu); every launcher returns the launch error
 March plan_march(int Nx, int Ny, int st, bool fp64);

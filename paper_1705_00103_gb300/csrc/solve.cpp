@@ -56,6 +56,9 @@ void free_plan(cj_plan *p) {
     if (p->h_red) cudaFreeHost(p->h_red);
     if (p->ev0) cudaEventDestroy(p->ev0);
     if (p->ev1) cudaEventDestroy(p->ev1);
+    if (p->graph) cudaGraphExecDestroy(p->graph);
+    cudaFree(p->w_dev);
+    cudaFree(p->pos);
     delete p;
 }
 
@@ -172,11 +175,17 @@ cj_status run_fp64(cj_plan *p, cudaStream_t s, double **cur_out, cj_result *res,
             break;
         }
         CJ_TRY(cudaEventRecord(p->ev0, s), "event");
-        for (long long k = 0; k < p->M; ++k) {
-            CJ_TRY(launch_sweep64(p, cur, nxt, p->w[k], s), "sweep");
-            double *t = cur;
-            cur = nxt;
-            nxt = t;
+        if (p->graph) {
+            // a cycle from u0 ends in u0 (M even)
+            CJ_TRY(launch_sweep_cycle_graph(p, s), "sweep graph");
+            res->launches += p->M / p->graph_G;  // the position advances
+        } else {
+            for (long long k = 0; k < p->M; ++k) {
+                CJ_TRY(launch_sweep64(p, cur, nxt, p->w[k], s), "sweep");
+                double *t = cur;
+                cur = nxt;
+                nxt = t;
+            }
         }
         CJ_TRY(cudaEventRecord(p->ev1, s), "event");
         timed = true;
@@ -484,6 +493,7 @@ cj_status cj_plan_create(int Nx, int Ny, cj_stencil st, cj_bc bc, double tol,
     if (bc == CJ_BC_DIRICHLET && o.precision != CJ_FP64) return CJ_ERR_INVALID_ARG;
     if (o.method != CJ_CJM && o.method != CJ_JACOBI) return CJ_ERR_INVALID_ARG;
     if (o.method == CJ_JACOBI && o.precision != CJ_FP64) return CJ_ERR_INVALID_ARG;
+    if (o.launch < 0 || o.launch > 2) return CJ_ERR_INVALID_ARG;
 
     cj_plan *p = new (std::nothrow) cj_plan();
     if (!p) return CJ_ERR_NOMEM;
@@ -571,6 +581,9 @@ cj_status cj_plan_create(int Nx, int Ny, cj_stencil st, cj_bc bc, double tol,
     if (e == cudaSuccess) e = cudaMallocHost((void **)&p->h_red, 8 * sizeof(double));
     if (e == cudaSuccess) e = cudaEventCreate(&p->ev0);
     if (e == cudaSuccess) e = cudaEventCreate(&p->ev1);
+    const bool graph = p->precision == CJ_FP64 && p->M % 2 == 0 &&
+                       (o.launch == 2 || (o.launch == 0 && sweep_graph_wanted(p)));
+    if (e == cudaSuccess && graph) e = make_sweep_graph(p);
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
     if (e != cudaSuccess) {
         set_cuda_error(e, "plan allocation");

@@ -503,3 +503,36 @@ def test_jacobi_argument_checks(cj, torch):
     with cj.Plan(8, 8, 9, 1e-6, method=cj.CJ_JACOBI) as p:
         with pytest.raises(cj.CJError):
             cj.cj_solve_to_error(p.handle, z, z.clone(), z, 1e-3)
+
+
+# ----------------------------------------------------------------- graph-launched cycles
+
+@pytest.mark.parametrize("st", STENCILS)
+@pytest.mark.parametrize("method,data", [(0, False), (0, True), (1, False)])
+def test_launch_modes_give_identical_solves(cj, torch, st, method, data):
+    """A cycle issued as one launch per sweep, as the CUDA graph of the cycle, or by the automatic
+    choice gives the same bits, equal to the oracle's."""
+    Nx, Ny, tol = 75, 52, 1e-7
+    if data:
+        f, _, g = workloads.paper_problem(Nx, Ny)
+        G, Gd = _ring(torch, Nx, Ny, g)
+        ref = orc.solve_bc(st, f, G, tol)
+    else:
+        f = workloads.smooth_random_rhs(Nx, Ny, 12)
+        ref = orc.solve_jacobi(st, f, tol) if method else orc.solve(st, f, tol)
+    outs = []
+    for launch in (cj.CJ_LAUNCH_STREAM, cj.CJ_LAUNCH_GRAPH, cj.CJ_LAUNCH_AUTO):
+        with cj.Plan(Nx, Ny, st, tol, method=method, launch=launch,
+                     bc=cj.CJ_BC_DIRICHLET if data else cj.CJ_BC_DIRICHLET0) as p:
+            if data:
+                cj.cj_set_boundary(p.handle, Gd)
+            ud = torch.zeros((Ny, Nx), dtype=torch.float64, device="cuda")
+            res = cj.cj_solve(p.handle, dev(torch, f), ud)
+            # a second solve on the same plan replays the graph from the start of the table
+            ud2 = torch.zeros_like(ud)
+            res2 = cj.cj_solve(p.handle, dev(torch, f), ud2)
+        assert res["sweeps"] == res2["sweeps"] == ref["sweeps"]
+        assert torch.equal(ud, ud2)
+        outs.append(ud.cpu().numpy())
+    for u in outs:
+        np.testing.assert_array_equal(u, ref["u"])
