@@ -64,6 +64,8 @@
  *      before every cycle and every check_every sweeps (see orc_solve_to_error).
  *   R18 classical Jacobi (the comparison method of Sec. 3.4): omega = 1, residual tested every
  *      M sweeps (see orc_solve_jacobi).
+ *   R19 position-dependent coefficient masks (Sec. 3.2): the Jacobi-normalised sweep with the
+ *      caller's eigenvalue bounds (see orc_solve_mask).
  *
  * Array convention: interior values only, row-major [Ny][Nx], value of node (i, j) at
  * u[(j-1)*Nx + (i-1)].  Compiled with -ffp-contract=off so that every rounding is the
@@ -875,6 +877,182 @@ long orc_solve_jacobi(int st, int Nx, int Ny, const double *f, const double *G, 
     *rel_l2 = rl2;
     *rel_linf = rinf;
     *intervals = done;
+    *status = stat;
+    return sweeps;
+}
+
+/* ---------------------------------------------------------------- coefficient masks */
+
+/* Position-dependent coefficient masks (Sec. 3.2, the masks of neighbours at distance one
+ * and two, with Cartesian, polar and bipolar examples), reading R19.  The operator is
+ *   (A u)(i, j) = sum over the mask's offsets (dx, dy) of c_{dx,dy}(i, j) u(i+dx, j+dy),
+ * A u = f.  Patterns: 5 (the cross |dx|+|dy| = 1), 9 (the 3x3 box), 17 (the 17 points of
+ * Eq. 2: the 3x3 box, (+-2, 0), (0, +-2) and (+-2, +-2)), 25 (the 5x5 box).  The off-centre
+ * offsets are taken in row-major order (dy = -R..R, then dx = -R..R).  Nodes outside the
+ * interior take the Dirichlet data of R15 (G) or 0.
+ * Coefficients: plane 0 is the centre c_C, planes 1..K the off-centre offsets in that order;
+ * value of plane k at (i, j) = coef[k*sp + (j-1)*sy + (i-1)*sx] (a stride of 0 repeats a
+ * plane along that axis).  An optional factor s(i, j) = scale[(j-1)*ssy + (i-1)*ssx]
+ * multiplies every coefficient.
+ * The iteration runs on the Jacobi-normalised system D^-1 A u = D^-1 f, D = diag(s c_C):
+ *   chat_k = c_k / c_C (s cancels), bhat = f / (s c_C),
+ *   r = (u_C - bhat) + sum_k chat_k u_k   (one subtraction, then fma in offset order),
+ *   u' = u_C - w_n r                      (fma(-w_n, r, u_C)),
+ * w_n = omega_n = 1/lambda_n of R1 in the order of R3 for the caller's [kmin, kmax] of D^-1 A
+ * (the paper gives the bounds only for its uniform Cartesian stencils), or w_n = 1 for
+ * classical Jacobi.  Residual test (R8 on the normalised system): rho = ||r||_2 / ||bhat||_2;
+ * floor estimate with S = 2 (a bound on 1 + sum |chat_k| for the diagonally dominant masks). */
+int orc_mask_offsets(int pat, int *dx, int *dy) {
+    int R = (pat == 5 || pat == 9) ? 1 : 2, K = 0;
+    for (int y = -R; y <= R; ++y)
+        for (int x = -R; x <= R; ++x) {
+            int ax = x < 0 ? -x : x, ay = y < 0 ? -y : y, m = ax > ay ? ax : ay, in;
+            if (x == 0 && y == 0) continue;
+            if (pat == 5) in = ax + ay == 1;
+            else if (pat == 9) in = m == 1;
+            else if (pat == 17) in = m == 1 || (ax == 2 && ay == 0) || (ax == 0 && ay == 2) || (ax == 2 && ay == 2);
+            else in = 1;
+            if (!in) continue;
+            dx[K] = x;
+            dy[K] = y;
+            ++K;
+        }
+    return K;
+}
+
+static double mask_at(const double *u, const double *G, int Nx, int Ny, int i, int j) {
+    if (i < 1 || i > Nx || j < 1 || j > Ny) return G ? G[(size_t)(j + 1) * (Nx + 4) + (i + 1)] : 0.0;
+    return u[(size_t)(j - 1) * Nx + (i - 1)];
+}
+
+/* chat: K planes of Nx*Ny (full layout); dC = s c_C (Nx*Ny).  Returns K, or -1 if the pattern
+ * is unknown or a centre coefficient is 0. */
+int orc_mask_normalize(int pat, int Nx, int Ny, const double *coef, long sx, long sy, long sp,
+                       const double *scale, long ssx, long ssy, double *chat, double *dC) {
+    int dx[24], dy[24];
+    if (pat != 5 && pat != 9 && pat != 17 && pat != 25) return -1;
+    int K = orc_mask_offsets(pat, dx, dy);
+    size_t n = (size_t)Nx * (size_t)Ny;
+    for (int j = 1; j <= Ny; ++j)
+        for (int i = 1; i <= Nx; ++i) {
+            size_t node = (size_t)(j - 1) * Nx + (i - 1);
+            long at = (long)(j - 1) * sy + (long)(i - 1) * sx;
+            double cC = coef[at];
+            if (cC == 0.0) return -1;
+            for (int k = 0; k < K; ++k) chat[(size_t)k * n + node] = coef[(long)(k + 1) * sp + at] / cC;
+            dC[node] = scale ? scale[(long)(j - 1) * ssy + (long)(i - 1) * ssx] * cC : cC;
+        }
+    return K;
+}
+
+/* r = (D^-1 A u - bhat)(i, j) in the order above. */
+static double mask_resid(int K, const int *dx, const int *dy, const double *u, const double *G,
+                         int Nx, int Ny, int i, int j, const double *bhat, const double *chat) {
+    size_t n = (size_t)Nx * (size_t)Ny, node = (size_t)(j - 1) * Nx + (i - 1);
+    double r = u[node] - bhat[node];
+    for (int k = 0; k < K; ++k)
+        r = fma(chat[(size_t)k * n + node], mask_at(u, G, Nx, Ny, i + dx[k], j + dy[k]), r);
+    return r;
+}
+
+void orc_sweep_mask(int pat, int Nx, int Ny, const double *u, const double *G, const double *bhat,
+                    const double *chat, double w, double *u_out) {
+    int dx[24], dy[24];
+    int K = orc_mask_offsets(pat, dx, dy);
+    for (int j = 1; j <= Ny; ++j)
+        for (int i = 1; i <= Nx; ++i) {
+            size_t node = (size_t)(j - 1) * Nx + (i - 1);
+            u_out[node] = fma(-w, mask_resid(K, dx, dy, u, G, Nx, Ny, i, j, bhat, chat), u[node]);
+        }
+}
+
+void orc_residual_mask(int pat, int Nx, int Ny, const double *u, const double *G, const double *bhat,
+                       const double *chat, double *l2sq, double *linf) {
+    int dx[24], dy[24];
+    int K = orc_mask_offsets(pat, dx, dy);
+    double s = 0.0, m = 0.0;
+    for (int j = 1; j <= Ny; ++j)
+        for (int i = 1; i <= Nx; ++i) {
+            double r = mask_resid(K, dx, dy, u, G, Nx, Ny, i, j, bhat, chat);
+            s += r * r;
+            if (fabs(r) > m) m = fabs(r);
+        }
+    *l2sq = s;
+    *linf = m;
+}
+
+/* Per-sweep weights omega_n = 1/lambda_n in the order of R3 (the normalised system's c = 1). */
+int orc_mask_weights(double kmin, double kmax, long M, double *w) {
+    long *idx = (long *)malloc(sizeof(long) * (size_t)M);
+    if (orc_order(M, idx) != 0) { free(idx); return -1; }
+    double hs = 0.5 * (kmax + kmin), hd = 0.5 * (kmax - kmin);
+    for (long n = 0; n < M; ++n) {
+        double x = cos((double)(2 * idx[n] - 1) * ORC_PI / (double)(2 * M));
+        w[n] = 1.0 / (hs + hd * x);
+    }
+    free(idx);
+    return 0;
+}
+
+/* CJM (method 0) or classical Jacobi (method 1, R18) on a masked operator; otherwise as
+ * orc_solve / orc_solve_jacobi.  Returns the sweeps done, or -1 on a bad argument. */
+long orc_solve_mask(int pat, int Nx, int Ny, const double *f, const double *coef, long sx, long sy,
+                    long sp, const double *scale, long ssx, long ssy, double kmin, double kmax,
+                    double tol, int method, const double *G, long max_sweeps, double *u,
+                    double *rel_l2, double *rel_linf, long *cycles, int *status) {
+    if (Nx < 1 || Ny < 1 || !(tol > 0.0 && tol < 1.0) || !(kmin > 0.0 && kmin < kmax)) return -1;
+    size_t n = (size_t)Nx * (size_t)Ny;
+    double *chat = (double *)malloc(sizeof(double) * n * 24);
+    double *dC = (double *)malloc(sizeof(double) * n);
+    if (orc_mask_normalize(pat, Nx, Ny, coef, sx, sy, sp, scale, ssx, ssy, chat, dC) < 0) {
+        free(chat); free(dC);
+        return -1;
+    }
+    long M = orc_cycle_length(kmin, kmax, tol);
+    double *w = (double *)malloc(sizeof(double) * (size_t)M);
+    if (method == 1) for (long k = 0; k < M; ++k) w[k] = 1.0;
+    else orc_mask_weights(kmin, kmax, M, w);
+    double *bh = (double *)malloc(sizeof(double) * n);
+    double *v = (double *)malloc(sizeof(double) * n);
+    double bsq = 0.0, bmax = 0.0;
+    for (size_t k = 0; k < n; ++k) {
+        bh[k] = f[k] / dC[k];
+        bsq += bh[k] * bh[k];
+        if (fabs(bh[k]) > bmax) bmax = fabs(bh[k]);
+    }
+    double bn = sqrt(bsq), eps = ldexp(1.0, -53), S = 2.0;
+    long sweeps = 0, cyc = 0;
+    int stat, stall = 0;
+    double rl2 = 0.0, rinf = 0.0, prev = 0.0;
+    for (;;) {
+        double sq, mx, usq = 0.0;
+        orc_residual_mask(pat, Nx, Ny, u, G, bh, chat, &sq, &mx);
+        for (size_t k = 0; k < n; ++k) usq += u[k] * u[k];
+        rl2 = bn > 0.0 ? sqrt(sq) / bn : sqrt(sq);
+        rinf = bmax > 0.0 ? mx / bmax : mx;
+        double fl = bn > 0.0 ? eps * S * sqrt(usq) / bn : eps * S * sqrt(usq);
+        if (method == 1) {
+            if (rl2 <= tol) stat = ORC_CONVERGED;
+            else if (!(rl2 == rl2) || rl2 > 1e300) stat = ORC_DIVERGED;
+            else if (rl2 <= 4.0 * fl || (cyc > 0 && rl2 >= prev)) stat = ORC_FLOOR;
+            else stat = -1;
+        } else {
+            stat = stop_rule(rl2, fl, prev, cyc, tol, 1, &stall);
+        }
+        if (stat >= 0) break;
+        if (sweeps + M > max_sweeps) { stat = ORC_MAX_SWEEPS; break; }
+        for (long s = 0; s < M; ++s) {
+            orc_sweep_mask(pat, Nx, Ny, u, G, bh, chat, w[s], v);
+            memcpy(u, v, sizeof(double) * n);
+        }
+        sweeps += M;
+        cyc += 1;
+        prev = rl2;
+    }
+    free(chat); free(dC); free(w); free(bh); free(v);
+    *rel_l2 = rl2;
+    *rel_linf = rinf;
+    *cycles = cyc;
     *status = stat;
     return sweeps;
 }

@@ -80,6 +80,22 @@ def lib():
         L.orc_solve_jacobi.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, _dp, _dp, ctypes.c_double,
                                        ctypes.c_long, _dp, _dp, _dp, _lp, ctypes.POINTER(ctypes.c_int)]
         L.orc_solve_jacobi.restype = ctypes.c_long
+        L.orc_mask_offsets.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]
+        L.orc_mask_offsets.restype = ctypes.c_int
+        L.orc_mask_normalize.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, _dp, ctypes.c_long,
+                                         ctypes.c_long, ctypes.c_long, _dp, ctypes.c_long, ctypes.c_long,
+                                         _dp, _dp]
+        L.orc_mask_normalize.restype = ctypes.c_int
+        L.orc_sweep_mask.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, _dp, _dp, _dp, _dp,
+                                     ctypes.c_double, _dp]
+        L.orc_residual_mask.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, _dp, _dp, _dp, _dp, _dp, _dp]
+        L.orc_mask_weights.argtypes = [ctypes.c_double, ctypes.c_double, ctypes.c_long, _dp]
+        L.orc_mask_weights.restype = ctypes.c_int
+        L.orc_solve_mask.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, _dp, _dp, ctypes.c_long,
+                                     ctypes.c_long, ctypes.c_long, _dp, ctypes.c_long, ctypes.c_long,
+                                     ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_int, _dp,
+                                     ctypes.c_long, _dp, _dp, _dp, _lp, ctypes.POINTER(ctypes.c_int)]
+        L.orc_solve_mask.restype = ctypes.c_long
         L.orc_real_error.argtypes = [ctypes.c_int, ctypes.c_int, _dp, _dp]
         L.orc_real_error.restype = ctypes.c_double
         L.orc_solve_to_error.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, _dp, _dp, _dp,
@@ -355,4 +371,87 @@ def solve_jacobi(st: int, f: np.ndarray, tol: float, G: np.ndarray | None = None
     if n < 0:
         raise ValueError("bad argument")
     return dict(u=u, sweeps=n, cycles=done.value, rel_l2=rl2.value, rel_linf=rinf.value,
+                status=STATUS[stat.value], converged=stat.value == 0)
+
+
+# ----------------------------------------------------------------- coefficient masks (R19)
+
+def mask_offsets(pat: int):
+    """Off-centre offsets (dx, dy) of a mask pattern, in application order."""
+    dx, dy = (ctypes.c_int * 24)(), (ctypes.c_int * 24)()
+    K = lib().orc_mask_offsets(pat, dx, dy)
+    return [(dx[k], dy[k]) for k in range(K)]
+
+
+def _bcast(a: np.ndarray, Nx: int, Ny: int, planes: bool):
+    """A C-contiguous copy of a (possibly broadcast) coefficient array and its element strides
+    (sx, sy, sp): the last two axes have length Nx / Ny or 1 (1 = repeated along that axis)."""
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    ny, nx = a.shape[-2], a.shape[-1]
+    if nx not in (1, Nx) or ny not in (1, Ny):
+        raise ValueError("coefficient shape %s does not broadcast to (%d, %d)" % (a.shape, Ny, Nx))
+    sx = 1 if nx == Nx and Nx > 1 else 0
+    sy = nx if ny == Ny and Ny > 1 else 0
+    return a, sx, sy, nx * ny
+
+
+def mask_normalize(pat: int, coef: np.ndarray, scale: np.ndarray | None, Nx: int, Ny: int):
+    """(chat, dC): the normalised off-centre coefficients (K, Ny, Nx) and s * c_C (Ny, Nx)."""
+    c, sx, sy, sp = _bcast(coef, Nx, Ny, True)
+    K = len(mask_offsets(pat))
+    if c.shape[0] != K + 1:
+        raise ValueError("expected %d planes" % (K + 1))
+    if scale is not None:
+        sc, ssx, ssy, _ = _bcast(scale, Nx, Ny, False)
+    chat = np.zeros((max(K, 1), Ny, Nx))
+    dC = np.zeros((Ny, Nx))
+    rc = lib().orc_mask_normalize(pat, Nx, Ny, _d(c), sx, sy, sp, None if scale is None else _d(sc),
+                                  0 if scale is None else ssx, 0 if scale is None else ssy, _d(chat), _d(dC))
+    if rc < 0:
+        raise ValueError("bad mask")
+    return chat[:K], dC
+
+
+def sweep_mask(pat: int, u: np.ndarray, G, bhat: np.ndarray, chat: np.ndarray, w: float) -> np.ndarray:
+    u, bhat, chat = _grid(u), _grid(bhat), np.ascontiguousarray(chat, dtype=np.float64)
+    out = np.empty_like(u)
+    lib().orc_sweep_mask(pat, u.shape[1], u.shape[0], _d(u), None if G is None else _d(_grid(G)),
+                         _d(bhat), _d(chat), float(w), _d(out))
+    return out
+
+
+def residual_mask(pat: int, u: np.ndarray, G, bhat: np.ndarray, chat: np.ndarray):
+    u, bhat, chat = _grid(u), _grid(bhat), np.ascontiguousarray(chat, dtype=np.float64)
+    sq, mx = ctypes.c_double(), ctypes.c_double()
+    lib().orc_residual_mask(pat, u.shape[1], u.shape[0], _d(u), None if G is None else _d(_grid(G)),
+                            _d(bhat), _d(chat), ctypes.byref(sq), ctypes.byref(mx))
+    return sq.value, mx.value
+
+
+def mask_weights(kmin: float, kmax: float, M: int) -> np.ndarray:
+    w = np.zeros(M)
+    if lib().orc_mask_weights(kmin, kmax, M, _d(w)) != 0:
+        raise ValueError("M must be a power of two")
+    return w
+
+
+def solve_mask(pat: int, f: np.ndarray, coef: np.ndarray, kmin: float, kmax: float, tol: float,
+               scale: np.ndarray | None = None, G: np.ndarray | None = None, method: int = 0,
+               max_sweeps: int = 1 << 40, u0: np.ndarray | None = None) -> dict:
+    """CJM (method 0) or classical Jacobi (1) on the masked operator A u = f (orc_solve_mask)."""
+    f = _grid(f)
+    Ny, Nx = f.shape
+    c, sx, sy, sp = _bcast(coef, Nx, Ny, True)
+    if scale is not None:
+        sc, ssx, ssy, _ = _bcast(scale, Nx, Ny, False)
+    u = np.zeros_like(f) if u0 is None else _grid(u0).copy()
+    rl2, rinf = ctypes.c_double(), ctypes.c_double()
+    cyc, stat = ctypes.c_long(), ctypes.c_int()
+    n = lib().orc_solve_mask(pat, Nx, Ny, _d(f), _d(c), sx, sy, sp, None if scale is None else _d(sc),
+                             0 if scale is None else ssx, 0 if scale is None else ssy, kmin, kmax, tol,
+                             method, None if G is None else _d(_grid(G)), max_sweeps, _d(u),
+                             ctypes.byref(rl2), ctypes.byref(rinf), ctypes.byref(cyc), ctypes.byref(stat))
+    if n < 0:
+        raise ValueError("bad argument")
+    return dict(u=u, sweeps=n, cycles=cyc.value, rel_l2=rl2.value, rel_linf=rinf.value,
                 status=STATUS[stat.value], converged=stat.value == 0)
