@@ -58,10 +58,10 @@ def parse_args(argv=None):
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-mixed", action="store_true")
-    ap.add_argument("--workload", default="solve", choices=["solve", "highorder", "paper", "batch", "serve"],
+    ap.add_argument("--workload", default="solve", choices=["solve", "highorder", "paper", "masks", "batch", "serve"],
                     help="solve: the plain FP64 9-point 4096^2 solve (default); highorder: the 17-point "
                          "8192^2 mixed-precision solve; paper: the paper's test problem (Table 1 point and Fig. 4 "
-                         "right); batch: the 512-problem batched workload; serve: a "
+                         "right); masks: coefficient-mask sweeps and a polar solve; batch: the 512-problem batched workload; serve: a "
                          "bounded sample of the request stream")
     ap.add_argument("--serve-requests", type=int, default=48)
     ap.add_argument("--no-jacobi", action="store_true",
@@ -525,6 +525,93 @@ def run_paper(args):
     print(json.dumps(out), flush=True)
 
 
+def run_masks(args):
+    """Coefficient-mask sweeps (Sec. 3.2) on 4096^2 grids: the polar 5-point mask (planes that
+    vary with r only), the bipolar one (a constant mask times a node factor), and random
+    position-dependent 9- and 25-point masks (full planes).  Per case the FP64 sweep time comes
+    from two cj_sweeps calls (64 and 0 sweeps: the difference removes the import and export);
+    then a polar-mask solve of a harmonic function, N = 1024, to tol 1e-10 with its real error.
+    value = updates per second over all timed sweeps."""
+    import torch
+
+    import paper_1705_00103_gb300 as cj
+    from workloads import masks
+    torch.cuda.set_device(0)
+    cj.build.build()
+    stream = torch.cuda.current_stream()
+    N = 4096
+    cases = [("polar", 5), ("bipolar", 5), ("random", 9), ("random", 25)]
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+
+    def problem(name, pat, n):
+        if name == "random":
+            return masks.random_dominant(pat, n, n, 5)
+        return {"polar": masks.polar, "bipolar": masks.bipolar}[name](n, n)
+
+    rows, upd, t_all = [], 0, 0.0
+    clocks = ClockSampler(0)
+    for name, pat in cases:
+        P = problem(name, pat, N)
+        coef = f_to(torch, P["coef"])
+        scale = None if P["scale"] is None else f_to(torch, P["scale"])
+        fd = f_to(torch, P["f"])
+        u = torch.zeros_like(fd)
+        K = {5: 4, 9: 8, 25: 24}[pat]
+        with cj.Plan.mask(N, N, pat, coef, 1e-6, 1.999, 1e-8, scale=scale) as p:
+            for _ in range(args.warmup):
+                cj.cj_sweeps(p.handle, fd, u, 0, 8, stream)
+            torch.cuda.synchronize()
+            if not rows:
+                clocks.start()
+            best = None
+            for _ in range(args.steps):
+                ev[0].record(stream)
+                cj.cj_sweeps(p.handle, fd, u, 0, 0, stream)
+                ev[1].record(stream)
+                cj.cj_sweeps(p.handle, fd, u, 0, 64, stream)
+                ev[2].record(stream)
+                torch.cuda.synchronize()
+                t = (ev[1].elapsed_time(ev[2]) - ev[0].elapsed_time(ev[1])) * 1e-3 / 64
+                best = t if best is None else min(best, t)
+                upd += 64 * N * N
+                t_all += 64 * t
+        full = P["coef"].shape[-1] == N and P["coef"].shape[-2] == N
+        bytes_node = 24 + (8 * K if full else 0) + (0 if P["scale"] is None else 0)
+        rows.append({"mask": name, "pattern": pat, "layout": "full planes" if full else
+                     ("constant planes x node factor" if P["scale"] is not None else "planes varying with x only"),
+                     "sweep_us": best * 1e6, "gupd_s": N * N / best / 1e9,
+                     "fp64_tops": (K + 2) * N * N / best / 1e12,
+                     "fp64_frac_of_issue_peak": (K + 2) * N * N / best / 1e12 / FP64_PEAK_TOPS,
+                     "hbm_gbs_algorithmic": bytes_node * N * N / best / 1e9})
+        del coef, scale, fd, u
+    clk = clocks.stop()
+    # a polar solve with its real error
+    n = 1024
+    P = masks.polar(n, n, solution="harmonic")
+    # kmin (n+1)^2 = 4.87, 4.88 for this polar sector at n = 15, 31 (dense eigenvalues); 5 % below
+    kmin = 0.95 * 4.88 / (n + 1) ** 2
+    G = f_to(torch, cj.dirichlet_ring(n, n, P["g"]))
+    fd, ue = f_to(torch, P["f"]), f_to(torch, P["u_exact"])
+    u = torch.zeros_like(fd)
+    with cj.Plan.mask(n, n, 5, f_to(torch, P["coef"]), kmin, 2.0, 1e-10) as p:
+        cj.cj_set_boundary(p.handle, G, stream)
+        ev[0].record(stream)
+        r = cj.cj_solve(p.handle, fd, u, stream)
+        ev[1].record(stream)
+        torch.cuda.synchronize()
+    solve = {"N": n, "sweeps": r["sweeps"], "cycles": r["cycles"],
+             "time_s": ev[0].elapsed_time(ev[1]) * 1e-3, "status": cj.cj_status_string(r["rc"]),
+             "rel_res_l2": r["rel_res_l2"], "real_error": float((u - ue).abs().max()), "kmin": kmin}
+    out = {"metric": METRIC, "value": upd / t_all / 1e9, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": t_all / args.steps * 1e3, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": "coefficient-mask FP64 sweeps, 4096x4096: polar 5-pt, bipolar 5-pt, random "
+                                  "9-pt and 25-pt full planes; plus a polar solve at N = 1024",
+                      "l2_flush": "none needed: 134 MB per grid array exceeds the 129 MB L2"},
+           "sweeps": rows, "polar_solve": solve, "clocks": clk}
+    print(json.dumps(out), flush=True)
+
+
 def run_batch(args):
     """The batched workload (512 problems, sides log-uniform in [64, 2048], 5/9-point,
     tol 1e-8, FP32-inner / FP64-outer) through cj_solve_batch; each step one batch."""
@@ -675,6 +762,8 @@ def main(argv=None):
         run_highorder(args)
     elif args.workload == "paper":
         run_paper(args)
+    elif args.workload == "masks":
+        run_masks(args)
     elif args.workload == "batch":
         run_batch(args)
     elif args.workload == "serve":

@@ -131,6 +131,47 @@ const char *cj_last_error(void);
 cj_status cj_plan_create(int Nx, int Ny, cj_stencil st, cj_bc bc, double tol,
                          const cj_options *opt, cj_plan **out);
 
+/*
+ * Position-dependent coefficient masks (Sec. 3.2 and its table of Cartesian, polar and
+ * bipolar examples): the operator (A u)(i, j) = sum over the pattern's offsets (dx, dy) of
+ * s(i, j) c_{dx,dy}(i, j) u(i+dx, j+dy), A u = f, on nodes 1..Nx x 1..Ny, with the Dirichlet
+ * ring of a CJ_BC_DIRICHLET plan (zero until cj_set_boundary sets it).
+ *   pattern: 5 (the cross |dx|+|dy| = 1), 9 (the 3 x 3 box), 17 (the points of Eq. 2: the 3 x 3
+ *     box, (+-2, 0), (0, +-2), (+-2, +-2)), 25 (the 5 x 5 box).
+ *   coef: device, K+1 planes (K = 4, 8, 16, 24): plane 0 the centre c_C, then the off-centre
+ *     offsets in row-major order (dy = -R..R, then dx = -R..R); value of plane k at (i, j) =
+ *     coef[k*sp + (j-1)*sy + (i-1)*sx] (element strides; 0 repeats along that axis, e.g. a
+ *     polar mask that varies with r = x1 only has sy = 0).  Read during cj_plan_create_mask only.
+ *   scale: device or NULL (= 1), a node factor s(i, j) = scale[(j-1)*scale_sy + (i-1)*scale_sx]
+ *     of every coefficient (e.g. the bipolar (cosh nu - cos mu)/a^2).  Read during the call only.
+ *   kmin, kmax: bounds of the spectrum of D^-1 A, D = diag(s c_C), which the paper gives only
+ *     for its uniform Cartesian stencils; too small a kmin only lengthens the cycle.
+ * The solver iterates the Jacobi-normalised system (chat_k = c_k/c_C, bhat = f/(s c_C)):
+ *   r = (u_C - bhat) + sum_k chat_k u_k, u' = u_C - w_n r, w_n = omega_n (or 1 for CJ_JACOBI),
+ * and its relative residual is ||r||_2 / ||bhat||_2 (floor_est with S = 2).
+ */
+typedef enum { CJ_MASK5 = 5, CJ_MASK9 = 9, CJ_MASK17 = 17, CJ_MASK25 = 25 } cj_mask_pattern;
+
+typedef struct {
+    int pattern;                 /* cj_mask_pattern */
+    const double *coef;          /* device coefficient planes (see above) */
+    long long sx, sy, sp;        /* their element strides, >= 0 */
+    const double *scale;         /* device node factor or NULL */
+    long long scale_sx, scale_sy;
+    double kmin, kmax;           /* 0 < kmin < kmax */
+} cj_mask;
+
+/*
+ * cj_plan_create_mask -- a plan for a masked operator; use it with cj_solve, cj_solve_history,
+ * cj_solve_host, cj_solve_to_error, cj_sweeps, cj_residual and cj_set_boundary.  f is the
+ * right-hand side of A u = f as given (no h^2 scaling).  Options: CJ_FP64 only (precision),
+ * method CJ_CJM or CJ_JACOBI, max_sweeps; sweeps are launched one per kernel.  Returns
+ * CJ_ERR_INVALID_ARG for a bad size, pattern, stride, bound or option, or a zero centre
+ * coefficient (cj_last_error says which).
+ */
+cj_status cj_plan_create_mask(int Nx, int Ny, const cj_mask *mask, double tol, const cj_options *opt,
+                              cj_plan **out);
+
 /* Frees the plan and its device workspace (NULL is ignored). */
 void cj_plan_destroy(cj_plan *plan);
 

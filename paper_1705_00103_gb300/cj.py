@@ -31,6 +31,13 @@ class cj_options(ctypes.Structure):
                 ("max_sweeps", ctypes.c_longlong), ("method", ctypes.c_int), ("launch", ctypes.c_int)]
 
 
+class cj_mask(ctypes.Structure):
+    _fields_ = [("pattern", ctypes.c_int), ("coef", ctypes.c_void_p), ("sx", ctypes.c_longlong),
+                ("sy", ctypes.c_longlong), ("sp", ctypes.c_longlong), ("scale", ctypes.c_void_p),
+                ("scale_sx", ctypes.c_longlong), ("scale_sy", ctypes.c_longlong),
+                ("kmin", ctypes.c_double), ("kmax", ctypes.c_double)]
+
+
 class cj_result(ctypes.Structure):
     _fields_ = [("sweeps", ctypes.c_longlong), ("cycles", ctypes.c_int), ("status", ctypes.c_int),
                 ("rel_res_l2", ctypes.c_double), ("rel_res_inf", ctypes.c_double),
@@ -92,6 +99,9 @@ def _lib():
         L.cj_plan_create.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                      ctypes.c_double, ctypes.POINTER(cj_options), ctypes.POINTER(_vp)]
         L.cj_plan_create.restype = ctypes.c_int
+        L.cj_plan_create_mask.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.POINTER(cj_mask), ctypes.c_double,
+                                          ctypes.POINTER(cj_options), ctypes.POINTER(_vp)]
+        L.cj_plan_create_mask.restype = ctypes.c_int
         L.cj_plan_destroy.argtypes = [_vp]
         L.cj_plan_destroy.restype = None
         L.cj_plan_info.argtypes = [_vp, ctypes.POINTER(_dp), ctypes.POINTER(_ll), _dp, _dp,
@@ -175,6 +185,43 @@ def cj_plan_create(Nx: int, Ny: int, st: int, tol: float, precision: int = CJ_FP
     rc = _lib().cj_plan_create(Nx, Ny, st, bc, tol, ctypes.byref(opt), ctypes.byref(h))
     if rc != CJ_OK:
         raise CJError(rc, "cj_plan_create")
+    _plan_shape[h.value] = (Nx, Ny)
+    return h.value
+
+
+def _mask_strides(t, Nx: int, Ny: int, name: str):
+    """Element strides (sx, sy) of a CUDA float64 tensor whose last two axes have length Ny or
+    1 and Nx or 1 (1 = the same value along that axis)."""
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != torch.float64:
+        raise ValueError("%s must be a CUDA float64 tensor" % name)
+    ny, nx = t.shape[-2], t.shape[-1]
+    if nx not in (1, Nx) or ny not in (1, Ny):
+        raise ValueError("%s: trailing shape %s does not broadcast to (%d, %d)" % (name, tuple(t.shape), Ny, Nx))
+    sx = t.stride(-1) if nx == Nx and Nx > 1 else 0
+    sy = t.stride(-2) if ny == Ny and Ny > 1 else 0
+    return sx, sy
+
+
+def cj_plan_create_mask(Nx: int, Ny: int, pattern: int, coef, kmin: float, kmax: float, tol: float,
+                        scale=None, method: int = 0, max_sweeps: int = 0):
+    """Plan for a position-dependent coefficient mask (see cj_plan_create_mask in cj.h).
+    coef: CUDA float64 tensor (K+1, Ny or 1, Nx or 1) -- the centre plane, then the off-centre
+    offsets in row-major order; scale: None or a CUDA float64 tensor (Ny or 1, Nx or 1)."""
+    if coef.dim() != 3:
+        raise ValueError("coef must have shape (K+1, Ny or 1, Nx or 1)")
+    sx, sy = _mask_strides(coef, Nx, Ny, "coef")
+    m = cj_mask(pattern, coef.data_ptr(), sx, sy, coef.stride(0), None, 0, 0, kmin, kmax)
+    if scale is not None:
+        if scale.dim() != 2:
+            raise ValueError("scale must have shape (Ny or 1, Nx or 1)")
+        ssx, ssy = _mask_strides(scale, Nx, Ny, "scale")
+        m.scale, m.scale_sx, m.scale_sy = scale.data_ptr(), ssx, ssy
+    opt = cj_options(CJ_FP64, 0, 0, 0, max_sweeps, method, 0)
+    h = _vp()
+    rc = _lib().cj_plan_create_mask(Nx, Ny, ctypes.byref(m), tol, ctypes.byref(opt), ctypes.byref(h))
+    if rc != CJ_OK:
+        raise CJError(rc, "cj_plan_create_mask")
     _plan_shape[h.value] = (Nx, Ny)
     return h.value
 
@@ -426,6 +473,14 @@ class Plan:
     def __init__(self, Nx, Ny, st, tol, **kw):
         self.handle = cj_plan_create(Nx, Ny, st, tol, **kw)
         self.Nx, self.Ny, self.st, self.tol = Nx, Ny, st, tol
+
+    @classmethod
+    def mask(cls, Nx, Ny, pattern, coef, kmin, kmax, tol, **kw):
+        """Owning wrapper of cj_plan_create_mask."""
+        self = cls.__new__(cls)
+        self.handle = cj_plan_create_mask(Nx, Ny, pattern, coef, kmin, kmax, tol, **kw)
+        self.Nx, self.Ny, self.st, self.tol = Nx, Ny, pattern, tol
+        return self
 
     def info(self) -> dict:
         return cj_plan_info(self.handle)

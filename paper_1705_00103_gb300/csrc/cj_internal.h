@@ -61,6 +61,12 @@ struct cj_plan {
     long long *pos = nullptr;
     cudaGraphExec_t graph = nullptr;
     int graph_G = 0;
+    // coefficient-mask plans (mask.cu): pattern 5/9/17/25 (0 = one of the paper's stencils),
+    // normalised off-centre planes with their element strides, and dC = s c_C (full)
+    int pattern = 0;
+    double *chat = nullptr;
+    long long chat_sx = 0, chat_sy = 0, chat_sp = 0;
+    double *dC = nullptr;
 };
 
 // ---- plan math (plan.cpp)
@@ -70,10 +76,25 @@ void plan_kappa_bounds(int st, double nint_x, double nint_y, double *kmin, doubl
 long long plan_cycle_length(double kmin, double kmax, double tol);
 long long plan_inner_cycle(double kmin, double kmax, long long M);
 void plan_sweep_coeffs(int st, double kmin, double kmax, long long M, std::vector<double> &w);
+// the same with the centre c given (c = 1: the weights omega_n of a Jacobi-normalised operator)
+void plan_sweep_coeffs_c(double c, double kmin, double kmax, long long M, std::vector<double> &w);
 
 // ---- error reporting (solve.cpp)
 void set_cuda_error(cudaError_t e, const char *where);
 void set_error_text(const char *msg);
+
+// ---- coefficient masks (mask.cu)
+int mask_points(int pattern);  // off-centre points K of a pattern
+// normalised planes and dC from the caller's coefficients (synchronous); *zero_centres
+// receives the number of nodes whose centre coefficient is 0
+cudaError_t mask_prepare(cj_plan *p, const double *coef, long long sx, long long sy, long long sp,
+                         const double *scale, long long ssx, long long ssy, int *zero_centres);
+cudaError_t launch_mask_sweep(const cj_plan *p, const double *u, double *out, double w, cudaStream_t s);
+// red[0..2] = (sum r^2, max |r|, sum u^2) of the normalised residual
+cudaError_t launch_mask_residual(const cj_plan *p, const double *u, cudaStream_t s);
+// bhat = f / dC and u into the plan's buffers; red[3..4] = (sum bhat^2, max |bhat|)
+cudaError_t launch_mask_import(const cj_plan *p, const double *f, long long ldf, const double *u,
+                               long long ldu, cudaStream_t s);
 
 // ---- FP64 cycles as CUDA graphs (graph.cu)
 // true when the plan's grid is small enough for its sweeps to be bound by host launches

@@ -97,6 +97,10 @@ long long plan_inner_cycle(double kmin, double kmax, long long M) {
 // (kmax-kmin)/2 * cos((2j-1) pi / 2M), applied in the mirror-pairing order o: o = (1)
 // for M = 1; going from m to 2m, every entry j of o is followed by 2m+1-j.
 void plan_sweep_coeffs(int st, double kmin, double kmax, long long M, std::vector<double> &w) {
+    plan_sweep_coeffs_c(plan_centre(st), kmin, kmax, M, w);
+}
+
+void plan_sweep_coeffs_c(double c, double kmin, double kmax, long long M, std::vector<double> &w) {
     std::vector<long long> o(1, 1), next;
     for (long long m = 1; m < M; m *= 2) {
         next.resize(2 * m);
@@ -106,7 +110,6 @@ void plan_sweep_coeffs(int st, double kmin, double kmax, long long M, std::vecto
         }
         o.swap(next);
     }
-    double c = plan_centre(st);
     double mid = 0.5 * (kmax + kmin), half = 0.5 * (kmax - kmin);
     w.resize(M);
     for (long long n = 0; n < M; ++n) {

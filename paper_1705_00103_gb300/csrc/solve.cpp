@@ -59,6 +59,8 @@ void free_plan(cj_plan *p) {
     if (p->graph) cudaGraphExecDestroy(p->graph);
     cudaFree(p->w_dev);
     cudaFree(p->pos);
+    cudaFree(p->chat);
+    cudaFree(p->dC);
     delete p;
 }
 
@@ -152,6 +154,21 @@ cj_status check_grid_args(const cj_plan *p, const void *f, long long ldf, const 
     return CJ_OK;
 }
 
+// FP64 launchers for either operator: the paper's stencils or a coefficient mask.
+cudaError_t sweep64(const cj_plan *p, const double *u, double *out, double w, cudaStream_t s) {
+    return p->pattern ? launch_mask_sweep(p, u, out, w, s) : launch_sweep64(p, u, out, w, s);
+}
+
+cudaError_t residual64(const cj_plan *p, const double *u, cudaStream_t s) {
+    return p->pattern ? launch_mask_residual(p, u, s) : launch_residual(p, u, nullptr, nullptr, s);
+}
+
+cudaError_t import64(const cj_plan *p, const double *f, long long ldf, const double *u, long long ldu,
+                     cudaStream_t s) {
+    return p->pattern ? launch_mask_import(p, f, ldf, u, ldu, s)
+                      : launch_import(p, f, ldf, u, ldu, p->b, p->u0, s);
+}
+
 // The solve proper, once f and u have been imported into the plan's padded buffers.
 cj_status run_fp64(cj_plan *p, cudaStream_t s, double **cur_out, cj_result *res, History *h) {
     double *cur = p->u0, *nxt = p->u1;
@@ -161,7 +178,7 @@ cj_status run_fp64(cj_plan *p, cudaStream_t s, double **cur_out, cj_result *res,
     Norms n{};
     int stat, stall = 0;
     for (;;) {
-        CJ_TRY(launch_residual(p, cur, nullptr, nullptr, s), "residual");
+        CJ_TRY(residual64(p, cur, s), "residual");
         res->launches += 2;
         cj_status st = fetch_norms(p, s, &n);
         if (st != CJ_OK) return st;
@@ -181,7 +198,7 @@ cj_status run_fp64(cj_plan *p, cudaStream_t s, double **cur_out, cj_result *res,
             res->launches += p->M / p->graph_G;  // the position advances
         } else {
             for (long long k = 0; k < p->M; ++k) {
-                CJ_TRY(launch_sweep64(p, cur, nxt, p->w[k], s), "sweep");
+                CJ_TRY(sweep64(p, cur, nxt, p->w[k], s), "sweep");
                 double *t = cur;
                 cur = nxt;
                 nxt = t;
@@ -236,7 +253,7 @@ cj_status run_fp64_to_error(cj_plan *p, cudaStream_t s, ErrorStop *es, double **
     int stat = -1, stall = 0;
     bool mid = false;
     for (;;) {
-        CJ_TRY(launch_residual(p, cur, nullptr, nullptr, s), "residual");
+        CJ_TRY(residual64(p, cur, s), "residual");
         CJ_TRY(launch_real_error(p, cur, es->ue, es->lde, s), "real error");
         res->launches += 4;
         cj_status st = fetch_norms(p, s, &n);
@@ -261,7 +278,7 @@ cj_status run_fp64_to_error(cj_plan *p, cudaStream_t s, ErrorStop *es, double **
             const long long chunk = es->every > 0 ? std::min(es->every, p->M - k) : p->M - k;
             CJ_TRY(cudaEventRecord(p->ev0, s), "event");
             for (long long q = 0; q < chunk; ++q) {
-                CJ_TRY(launch_sweep64(p, cur, nxt, p->w[k + q], s), "sweep");
+                CJ_TRY(sweep64(p, cur, nxt, p->w[k + q], s), "sweep");
                 std::swap(cur, nxt);
             }
             CJ_TRY(cudaEventRecord(p->ev1, s), "event");
@@ -295,7 +312,7 @@ cj_status run_fp64_to_error(cj_plan *p, cudaStream_t s, ErrorStop *es, double **
         prev = n.l2;
     }
     if (mid) {  // the residual where the solve stopped
-        CJ_TRY(launch_residual(p, cur, nullptr, nullptr, s), "residual");
+        CJ_TRY(residual64(p, cur, s), "residual");
         res->launches += 2;
         cj_status st = fetch_norms(p, s, &n);
         if (st != CJ_OK) return st;
@@ -432,7 +449,7 @@ cj_status solve_core(cj_plan *p, const double *f, long long ldf, double *u, long
                      cudaStream_t s, cj_result *res, History *h) {
     auto t0 = std::chrono::steady_clock::now();
     cj_result r{};
-    CJ_TRY(launch_import(p, f, ldf, u, ldu, p->b, p->u0, s), "import");
+    CJ_TRY(import64(p, f, ldf, u, ldu, s), "import");
     r.launches = 2;
     double *cur = nullptr;
     cj_status st = p->precision == CJ_FP32_INNER      ? run_mixed(p, s, &cur, &r, h)
@@ -594,6 +611,66 @@ cj_status cj_plan_create(int Nx, int Ny, cj_stencil st, cj_bc bc, double tol,
     return CJ_OK;
 }
 
+cj_status cj_plan_create_mask(int Nx, int Ny, const cj_mask *m, double tol, const cj_options *opt,
+                              cj_plan **out) {
+    if (!out) return CJ_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (!m || !m->coef) return CJ_ERR_INVALID_ARG;
+    const int pat = m->pattern;
+    if (pat != 5 && pat != 9 && pat != 17 && pat != 25) return CJ_ERR_INVALID_ARG;
+    if (m->sx < 0 || m->sy < 0 || m->sp < 0 || m->scale_sx < 0 || m->scale_sy < 0) return CJ_ERR_INVALID_ARG;
+    if (!(m->kmin > 0.0 && m->kmin < m->kmax) || !(m->kmax < 1e300)) return CJ_ERR_INVALID_ARG;
+    cj_options o{};
+    if (opt) o = *opt;
+    if (o.precision != CJ_FP64 || o.literal_n != 0 || o.launch == 2) return CJ_ERR_INVALID_ARG;
+    if (!(tol > 0.0 && tol < 1.0)) return CJ_ERR_INVALID_ARG;
+    const long long M = plan_cycle_length(m->kmin, m->kmax, tol);
+    if (M > (1LL << 24)) return CJ_ERR_INVALID_ARG;
+    // the padded buffers, reductions and ring of a Dirichlet-data FP64 plan of the same size
+    // (its stencil only picks the launch shape), with one launch per sweep
+    cj_options base = o;
+    base.launch = 1;
+    const cj_stencil shape = pat == 5 ? CJ_ST5 : pat == 9 ? CJ_ST9 : CJ_ST17;
+    cj_plan *p = nullptr;
+    cj_status st = cj_plan_create(Nx, Ny, shape, CJ_BC_DIRICHLET, tol, &base, &p);
+    if (st != CJ_OK) return st;
+    try {
+        p->pattern = pat;
+        p->kmin = m->kmin;
+        p->kmax = m->kmax;
+        p->c = 1.0;
+        p->S = 2.0;
+        p->M = M;
+        if (p->method == CJ_JACOBI)
+            p->w.assign((size_t)M, 1.0);
+        else
+            plan_sweep_coeffs_c(1.0, m->kmin, m->kmax, M, p->w);
+        p->max_sweeps = o.max_sweeps ? o.max_sweeps : 64 * M;
+        if (p->method == CJ_JACOBI && !o.max_sweeps) {
+            const double need = 4.0 * std::log(1.0 / tol) / m->kmin;
+            if (need > (double)p->max_sweeps) p->max_sweeps = need < 9e15 ? (long long)need : (1LL << 53);
+        }
+    } catch (...) {
+        free_plan(p);
+        return CJ_ERR_NOMEM;
+    }
+    int zero_centres = 0;
+    cudaError_t e = mask_prepare(p, m->coef, m->sx, m->sy, m->sp, m->scale, m->scale_sx, m->scale_sy,
+                                 &zero_centres);
+    if (e != cudaSuccess) {
+        set_cuda_error(e, "mask coefficients");
+        free_plan(p);
+        return e == cudaErrorMemoryAllocation ? CJ_ERR_NOMEM : CJ_ERR_CUDA;
+    }
+    if (zero_centres) {
+        set_error_text("cj_plan_create_mask: a centre coefficient is 0");
+        free_plan(p);
+        return CJ_ERR_INVALID_ARG;
+    }
+    *out = p;
+    return CJ_OK;
+}
+
 void cj_plan_destroy(cj_plan *plan) { free_plan(plan); }
 
 cj_status cj_plan_info(const cj_plan *p, const double **w, long long *M, double *kmin,
@@ -641,7 +718,7 @@ cj_status cj_solve_to_error(cj_plan *p, const double *f, long long ldf, double *
     auto t0 = std::chrono::steady_clock::now();
     cj_result r{};
     ErrorStop es{u_exact, ld_exact, err_tol, check_every, history, cap, 0};
-    CJ_TRY(launch_import(p, f, ldf, u, ldu, p->b, p->u0, s), "import");
+    CJ_TRY(import64(p, f, ldf, u, ldu, s), "import");
     r.launches = 2;
     double *cur = nullptr;
     cj_status st = run_fp64_to_error(p, s, &es, &cur, &r);
@@ -684,10 +761,10 @@ cj_status cj_sweeps(cj_plan *p, const double *f, long long ldf, double *u, long 
     if (a != CJ_OK) return a;
     if (first < 0 || count < 0 || !p->u1) return CJ_ERR_INVALID_ARG;
     cudaStream_t s = (cudaStream_t)stream;
-    CJ_TRY(launch_import(p, f, ldf, u, ldu, p->b, p->u0, s), "import");
+    CJ_TRY(import64(p, f, ldf, u, ldu, s), "import");
     double *cur = p->u0, *nxt = p->u1;
     for (long long k = 0; k < count; ++k) {
-        CJ_TRY(launch_sweep64(p, cur, nxt, p->w[(first + k) % p->M], s), "sweep");
+        CJ_TRY(sweep64(p, cur, nxt, p->w[(first + k) % p->M], s), "sweep");
         double *t = cur;
         cur = nxt;
         nxt = t;
@@ -786,8 +863,8 @@ cj_status cj_residual(cj_plan *p, const double *f, long long ldf, const double *
     cj_status a = check_grid_args(p, f, ldf, u, ldu);
     if (a != CJ_OK) return a;
     cudaStream_t s = (cudaStream_t)stream;
-    CJ_TRY(launch_import(p, f, ldf, u, ldu, p->b, p->u0, s), "import");
-    CJ_TRY(launch_residual(p, p->u0, nullptr, nullptr, s), "residual");
+    CJ_TRY(import64(p, f, ldf, u, ldu, s), "import");
+    CJ_TRY(residual64(p, p->u0, s), "residual");
     Norms n{};
     cj_status st = fetch_norms(p, s, &n);
     if (st != CJ_OK) return st;

@@ -26,7 +26,7 @@ def lib():
 def test_header_declares_the_boundary():
     names = _declared_functions()
     for n in ("cj_plan_create", "cj_plan_destroy", "cj_plan_info", "cj_solve", "cj_solve_host",
-              "cj_solve_history", "cj_solution_lo", "cj_set_boundary", "cj_solve_to_error", "cj_autotune_depth",
+              "cj_solve_history", "cj_solution_lo", "cj_set_boundary", "cj_solve_to_error", "cj_plan_create_mask", "cj_autotune_depth",
               "cj_solve_batch", "cj_server_create", "cj_submit", "cj_poll",
               "cj_sweeps", "cj_sweeps_f32", "cj_residual", "cj_status_string", "cj_last_error"):
         assert n in names
