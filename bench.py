@@ -323,14 +323,21 @@ def mixed_paths(cj, f, stream, plain):
     import torch
     out = {"plain_fp64": {"time_s": plain["seconds"], "rel_res_l2": plain["rel_res_l2"],
                           "status": cj.cj_status_string(plain["rc"]), "sweeps": plain["sweeps"]}}
-    for name, prec in (("fp32_inner_fp64_outer", cj.CJ_FP32_INNER), ("fp32_inner_dd_outer", cj.CJ_FP32_INNER_DD)):
-        with cj.Plan(N_GRID, N_GRID, STENCIL, TOL, precision=prec) as p:
+    runs = (("fp32_inner_fp64_outer", cj.CJ_FP32_INNER, 0), ("fp32_inner_dd_outer", cj.CJ_FP32_INNER_DD, 0),
+            ("fp32_inner_dd_outer_temporal_blocking_4", cj.CJ_FP32_INNER_DD, 4))
+    for name, prec, depth in runs:
+        with cj.Plan(N_GRID, N_GRID, STENCIL, TOL, precision=prec, temporal_depth=depth) as p:
             u = torch.zeros((N_GRID, N_GRID), dtype=torch.float64, device="cuda")
             r = cj.cj_solve(p.handle, f, u, stream)
             M_in = p.info()["M_inner"]
+        upd_s = N_GRID * N_GRID * r["sweeps"] / r["sweep_seconds"]
         out[name] = {"time_s": r["seconds"], "rel_res_l2": r["rel_res_l2"], "status": cj.cj_status_string(r["rc"]),
                      "fp32_sweeps": r["sweeps"], "outer_steps": r["cycles"], "inner_cycle": M_in,
-                     "fp32_gupdates_s": N_GRID * N_GRID * r["sweeps"] / r["sweep_seconds"] / 1e9,
+                     "temporal_depth": depth if depth else "auto (1 unless cj_autotune_depth recorded another)",
+                     "fp32_gupdates_s": upd_s / 1e9,
+                     # one FP32 sweep reads e and r and writes e' (12 B per update) when it runs alone;
+                     # temporal blocking moves fewer bytes for the same updates
+                     "fp32_hbm_gbs_algorithmic": 12.0 * upd_s / 1e9,
                      "speedup_vs_plain_fp64_time": plain["seconds"] / r["seconds"]}
     return out
 

@@ -278,16 +278,6 @@ cudaError_t launch_set_ring(const cj_plan *p, const double *gdat, long long ldg,
     return cudaGetLastError();
 }
 
-cudaError_t launch_sweep32(const cj_plan *p, const float *e, const float *r, float *out, float w,
-                           cudaStream_t s) {
-    dim3 grid(p->m32.nbx, p->m32.nby);
-    switch (p->st) {
-        case 5: sweep_kernel<5, float><<<grid, kBX, 0, s>>>(e, r, out, p->g32, p->m32.ty, w, 1.0f); break;
-        case 9: sweep_kernel<9, float><<<grid, kBX, 0, s>>>(e, r, out, p->g32, p->m32.ty, w, 1.0f); break;
-        default: sweep_kernel<17, float><<<grid, kBX, 0, s>>>(e, r, out, p->g32, p->m32.ty, w, 1.0f); break;
-    }
-    return cudaGetLastError();
-}
 
 cudaError_t launch_residual(const cj_plan *p, const double *u_pad, float *rt, float *e_zero,
                             cudaStream_t s) {

@@ -551,13 +551,12 @@ cj_status cj_plan_create(int Nx, int Ny, cj_stencil st, cj_bc bc, double tol,
             p->w32.resize(p->M_in);
             for (long long k = 0; k < p->M_in; ++k) p->w32[k] = (float)wi[k];
         }
-        // default FP32 temporal depth, from measurements at 4096^2 (cj_sweeps_f32, Gupd/s at
-        // depth 1 / 4): 5-point 404 / 468, 9-point 341 / 469, 17-point 272 / 163; small
-        // grids have too few strips for the wavefront kernel, so they keep depth 1
+        // default FP32 temporal depth 1, from measurements at 4096^2 (cj_sweeps_f32, Gupd/s at
+        // depth 1 / 4): 5-point 456 / 468, 9-point 456 / 400, 17-point 385 / 185 -- the
+        // vectorised one-sweep kernel runs at ~80 % of the copy bandwidth, which the wavefront
+        // kernel does not beat; cj_autotune_depth records a deeper choice where it measures one
         const int tuned = tuned_depth(st, Nx, Ny);
-        p->depth = o.temporal_depth ? o.temporal_depth
-                   : tuned          ? tuned
-                                    : (st != CJ_ST17 && (long long)Nx * Ny >= (1LL << 20) ? 4 : 1);
+        p->depth = o.temporal_depth ? o.temporal_depth : tuned ? tuned : 1;
         long long unit = p->precision != CJ_FP64 ? p->M_in : p->M;
         p->max_sweeps = o.max_sweeps ? o.max_sweeps : 64 * unit;
         if (p->method == CJ_JACOBI && !o.max_sweeps) {

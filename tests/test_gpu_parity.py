@@ -266,6 +266,26 @@ def test_full_size_residual(cj, torch):
     assert linf == pytest.approx(m / np.abs(b).max(), rel=1e-14)
 
 
+@pytest.mark.parametrize("st", (9, 17))
+def test_full_size_mixed_dd_meets_the_tolerance_by_the_oracle(cj, torch, st):
+    """The 4096^2 FP32-inner / double-FP64-outer solve to 1e-10 (the benchmark's problem, and the
+    17-point stencil): its relative residual as the oracle evaluates it, the double-FP64 defect
+    of u_hi + u_lo, is within the tolerance and agrees with the library's own figure."""
+    N = 4096
+    f = workloads.smooth_random_rhs(N, N, 2)
+    with cj.Plan(N, N, st, 1e-10, precision=cj.CJ_FP32_INNER_DD) as p:
+        u = torch.zeros((N, N), dtype=torch.float64, device="cuda")
+        res = cj.cj_solve(p.handle, dev(torch, f), u)
+        lo = torch.zeros_like(u)
+        cj.cj_solution_lo(p.handle, lo)
+    assert res["rc"] == cj.CJ_OK
+    b = orc.scale_rhs(f)
+    R = orc.residual_dd(st, u.cpu().numpy(), lo.cpu().numpy(), b)
+    rho = np.linalg.norm(R) / np.linalg.norm(b)
+    assert rho <= 1e-10
+    assert rho == pytest.approx(res["rel_res_l2"], rel=1e-6)
+
+
 # ----------------------------------------------------------------- double-FP64 outer form
 
 @pytest.mark.parametrize("st", STENCILS)
