@@ -18,6 +18,10 @@
 
 namespace {
 
+// FP32 sweep launches per engine step, and steps per captured graph: a replay advances a slot by
+// up to 32 sweeps, as with one sweep per step and 32 steps, with half the launches per sweep.
+constexpr int kSweepsPerStep = 4;
+
 using Clock = std::chrono::steady_clock;
 
 #define ENG_TRY(call, where)                \
@@ -240,7 +244,7 @@ class Engine {
             if (st != CJ_OK) return st;
         }
         for (int k = 0; k < replays; ++k) ENG_TRY(cudaGraphLaunch(gexec_, s_), "graph launch");
-        launches_ += (long long)replays * steps_per_graph_ * 6;
+        launches_ += (long long)replays * steps_per_graph_ * (4 + 2 * kSweepsPerStep);
         ENG_TRY(cudaMemcpyAsync(h_status_, d_.status, sizeof(SlotStatus) * max_slots_,
                                 cudaMemcpyDeviceToHost, s_), "status readback");
         ENG_TRY(cudaStreamSynchronize(s_), "step sync");
@@ -290,7 +294,7 @@ class Engine {
         ENG_TRY(cudaStreamBeginCapture(s_, cudaStreamCaptureModeThreadLocal), "begin capture");
         cudaError_t err = cudaSuccess;
         for (int k = 0; k < steps_per_graph_ && err == cudaSuccess; ++k)
-            err = eng_launch_step(d_, grid_tiles_, grid_slots_, smem_, s_);
+            err = eng_launch_step(d_, grid_tiles_, grid_slots_, smem_, kSweepsPerStep, s_);
         cudaError_t e2 = cudaStreamEndCapture(s_, &g);
         if (err == cudaSuccess) err = e2;
         if (err == cudaSuccess) err = cudaGraphInstantiate(&gexec_, g, 0);
@@ -300,7 +304,7 @@ class Engine {
     }
 
     int dev_ = 0, max_slots_ = 0, max_depth_ = 1, grid_tiles_ = 0, grid_slots_ = 0;
-    int steps_per_graph_ = 32;
+    int steps_per_graph_ = 8;
     size_t smem_ = 0;
     cudaStream_t s_ = nullptr;
     EngineDev d_{};

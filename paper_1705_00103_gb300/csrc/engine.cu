@@ -9,7 +9,9 @@
 //   decide   -- per slot: reduce the partials in a fixed order, apply the stop rule on the
 //               device, start the next inner cycle or finish the slot;
 //   sweep    -- every slot in an inner cycle advances min(depth, M_in - counter) FP32
-//               sweeps over all of its tiles (one-sweep march, or temporal blocking);
+//               sweeps over all of its tiles (one-sweep march4, or temporal blocking); a step
+//               runs several sweep launches, each followed by a counter advance, so the
+//               per-step launches are spread over more sweeps;
 //   export   -- finished slots copy u into the caller's buffer;
 //   advance  -- per slot: move the cycle counter, flip the ping-pong, retire exported slots,
 //               publish a compact status record for the host.
@@ -21,6 +23,7 @@
 // single-problem solver, so a problem's result does not depend on what it is batched with.
 #include "engine.cuh"
 #include "grid_dev.cuh"
+#include "march4_dev.cuh"
 #include "stencil_dev.cuh"
 
 namespace {
@@ -202,18 +205,15 @@ __device__ __forceinline__ void sweep_tile(SlotDev &S, const TileRef &T, int k, 
     const float *ein = S.cur ? S.e1 : S.e0;
     float *eout = S.cur ? S.e0 : S.e1;
     if (k == 1) {
-        const int i = T.i0 + threadIdx.x;
-        if (i > T.i1) return;
-        struct Op {
-            float *out;
-            const Grid *g;
-            int i;
-            float w;
-            __device__ __forceinline__ void operator()(int j, float r, float uc) {
-                store_node<(ST == 17 ? 2 : 1), float>(out, *g, i, j, fmaf(w, r, uc));
-            }
-        } op{eout, &S.g32, i, S.w32[S.counter]};
-        march32<ST, true>(ein, S.rt, S.g32, i, T.j0, T.j1, op);
+        // four warps split the tile's rows; each lane takes four adjacent columns (march4)
+        constexpr int kRowsPerWarp = kEngTY / (kEngThreads / 32);
+        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+        const int c0 = T.i0 + 4 * lane;
+        const int js = T.j0 + warp * kRowsPerWarp;
+        const int je = min(js + kRowsPerWarp - 1, T.j1);
+        if (c0 > T.i1 || js > je) return;
+        M4Store<ST> op{eout, &S.g32, c0, S.w32[S.counter]};
+        march4<ST>(ein, S.rt, S.g32, c0, js, je, op);
     } else {
         float w[kTbMaxDepth];
         for (int s = 0; s < k; ++s) w[s] = S.w32[S.counter + s];
@@ -255,9 +255,12 @@ __global__ void __launch_bounds__(kEngThreads) eng_export(EngineDev E) {
     }
 }
 
-__global__ void eng_advance(EngineDev E) {
+// Per slot after a sweep launch: counters, ping-pong, end of the inner cycle.  `final` (the
+// last launch of a step) also retires exported slots and publishes the status records.
+__global__ void eng_advance(EngineDev E, int final) {
     for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < E.max_slots; q += gridDim.x * blockDim.x) {
         SlotDev &S = E.slots[q];
+        if (!final && S.phase != PHASE_SWEEP) continue;
         if (S.phase == PHASE_SWEEP) {
             const long long left = S.M_in - S.counter;
             const long long k = S.depth < left ? S.depth : left;
@@ -377,13 +380,17 @@ cudaError_t eng_prepare(size_t sweep_smem) {
 }
 
 cudaError_t eng_launch_step(const EngineDev &e, int grid_tiles, int grid_slots, size_t sweep_smem,
-                            cudaStream_t s) {
+                            int sweeps, cudaStream_t s) {
+    const int grid_adv = (e.max_slots + 127) / 128;
     eng_correct<<<grid_tiles, kEngThreads, 0, s>>>(e);
     eng_defect<<<grid_tiles, kEngThreads, 0, s>>>(e);
     eng_decide<<<grid_slots, kEngThreads, 0, s>>>(e);
-    eng_sweep<<<grid_tiles, kEngThreads, sweep_smem, s>>>(e);
+    for (int q = 0; q < sweeps; ++q) {
+        eng_sweep<<<grid_tiles, kEngThreads, sweep_smem, s>>>(e);
+        if (q + 1 < sweeps) eng_advance<<<grid_adv, 128, 0, s>>>(e, 0);
+    }
     eng_export<<<grid_tiles, kEngThreads, 0, s>>>(e);
-    eng_advance<<<(e.max_slots + 127) / 128, 128, 0, s>>>(e);
+    eng_advance<<<grid_adv, 128, 0, s>>>(e, 1);
     return cudaGetLastError();
 }
 

@@ -52,8 +52,10 @@ struct EngineDev {
 };
 
 // launchers (engine.cu)
+// one engine step: correct, defect, decide, `sweeps` sweep launches (each but the last
+// followed by a counter advance), export, advance
 cudaError_t eng_launch_step(const EngineDev &e, int grid_tiles, int grid_slots, size_t sweep_smem,
-                            cudaStream_t s);
+                            int sweeps, cudaStream_t s);
 cudaError_t eng_launch_import(const EngineDev &e, int slot, int ntiles, const double *f,
                               long long ldf, const double *u0, long long ldu, cudaStream_t s);
 size_t eng_sweep_smem(int max_depth);
