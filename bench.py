@@ -64,6 +64,8 @@ def parse_args(argv=None):
                          "right); masks: coefficient-mask sweeps and a polar solve; batch: the 512-problem batched workload; serve: a "
                          "bounded sample of the request stream")
     ap.add_argument("--serve-requests", type=int, default=48)
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="batch workload: keep the engine's default tiles (32 rows) and depth 1")
     ap.add_argument("--no-jacobi", action="store_true",
                     help="paper workload: skip the classical Jacobi solves of Table 1 (minutes)")
     return ap.parse_args(argv)
@@ -634,6 +636,21 @@ def run_batch(args):
     probs = [dict(Nx=p["Nx"], Ny=p["Ny"], st=p["st"], tol=p["tol"], precision=cj.CJ_FP32_INNER, f=f, u=u)
              for p, f, u in zip(specs, fs, us)]
     stream = torch.cuda.current_stream()
+    # engine tile rows and depth per (stencil, size class), timed on the class's median problem
+    # before the timed region
+    tuned = {}
+    if not args.no_autotune:
+        classes = {}
+        for p in specs:
+            n, c = p["Nx"] * p["Ny"], 0
+            while n > 3:
+                n >>= 2
+                c += 1
+            classes.setdefault((p["st"], c), []).append((p["Nx"] * p["Ny"], p["Nx"], p["Ny"]))
+        for (st, c), members in sorted(classes.items()):
+            _, nx, ny = sorted(members)[len(members) // 2]
+            r = cj.cj_autotune_engine(nx, ny, st)
+            tuned["%d-point class %d (%dx%d)" % (st, c, nx, ny)] = [r["tile_rows"], r["depth"]]
     for _ in range(args.warmup):
         for u in us:
             u.zero_()
@@ -667,6 +684,7 @@ def run_batch(args):
                       "points": sum(p["Nx"] * p["Ny"] for p in specs)},
            "time_to_all_converged_s": ms / args.steps * 1e-3, "statuses": stat,
            "max_rel_res_l2": max(r["rel_res_l2"] for r in res), "clocks": clk,
+           "autotuned_tile_rows_depth": tuned,
            "gpu_launches": res[0]["launches"] if res else 0}
     print(json.dumps(out), flush=True)
 

@@ -339,6 +339,22 @@ typedef struct {
 } cj_server_stats_t;
 
 /*
+ * cj_autotune_engine -- tile rows (16, 32 or 64; 128 columns) and FP32 temporal depth (1, 2 or 4)
+ * of the batched / served engine for a stencil and size class (grids within a factor 2 per side),
+ * picked by timing the engine loaded with copies of a synthetic problem of Nx x Ny nodes (as
+ * many as give the device ~8 tiles per SM, up to 256 and 2^24 nodes) at every combination, and
+ * recorded in a per-process table that cj_solve_batch and the server use for problems of that
+ * class (the server sweeps one at a time, so it takes the tile rows only; an explicit
+ * temporal_depth overrides the depth).  Not a method of the paper: a runtime choice of this
+ * library.  Synchronous; allocates an Nx x Ny FP64 grid and the engine's slots while it runs.
+ *   tile_rows, depth: the choice (may be NULL);
+ *   gupd: host array of 9 (may be NULL): measured Gupdates/s, tile rows 16/32/64 (major) x
+ *     depth 1/2/4.
+ * Returns CJ_ERR_INVALID_ARG for a bad size or stencil.
+ */
+cj_status cj_autotune_engine(int Nx, int Ny, cj_stencil st, int *tile_rows, int *depth, double *gupd);
+
+/*
  * cj_server_create -- a request loop with continuous batching on the current device: a
  * worker thread admits submitted problems, in arrival order, into free engine slots while
  * their device footprint (FP64 u, b [, u_lo], FP32 e, e', r, weights; 28-36 bytes per

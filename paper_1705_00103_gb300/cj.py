@@ -122,6 +122,9 @@ def _lib():
         L.cj_sweeps.restype = ctypes.c_int
         L.cj_sweeps_f32.argtypes = [_vp, _vp, _ll, _vp, _ll, _ll, _ll, _vp]
         L.cj_sweeps_f32.restype = ctypes.c_int
+        L.cj_autotune_engine.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
+                                         ctypes.POINTER(ctypes.c_int), _dp]
+        L.cj_autotune_engine.restype = ctypes.c_int
         L.cj_set_boundary.argtypes = [_vp, _vp, _ll, _vp]
         L.cj_set_boundary.restype = ctypes.c_int
         L.cj_autotune_depth.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, _vp,
@@ -501,3 +504,15 @@ class Plan:
             self.close()
         except Exception:
             pass
+
+
+def cj_autotune_engine(Nx: int, Ny: int, st: int) -> dict:
+    """Times the batched engine at tile rows 16/32/64 x depth 1/2/4 for this stencil and size
+    class and records the fastest for cj_solve_batch and the server (see cj.h)."""
+    ty, d = ctypes.c_int(), ctypes.c_int()
+    g = (ctypes.c_double * 9)()
+    rc = _lib().cj_autotune_engine(Nx, Ny, st, ctypes.byref(ty), ctypes.byref(d), g)
+    if rc != CJ_OK:
+        raise CJError(rc, "cj_autotune_engine")
+    return dict(tile_rows=ty.value, depth=d.value,
+                gupd={(r, k): g[i * 3 + j] for i, r in enumerate((16, 32, 64)) for j, k in enumerate((1, 2, 4))})

@@ -42,7 +42,7 @@ struct SlotMem {
 };
 
 struct Spec {
-    int Nx, Ny, st, mode, inner_cycle, depth;
+    int Nx, Ny, st, mode, inner_cycle, depth, ty;
     double tol;
     long long max_sweeps;
 };
@@ -51,7 +51,7 @@ struct Spec {
 // weights, partials).
 size_t slot_bytes(const Spec &sp, long long M_in) {
     const Grid g64 = make_grid(sp.Nx, sp.Ny, 8), g32 = make_grid(sp.Nx, sp.Ny, 4);
-    const long long ntiles = (long long)((sp.Nx + kEngTX - 1) / kEngTX) * ((sp.Ny + kEngTY - 1) / kEngTY);
+    const long long ntiles = (long long)((sp.Nx + kEngTX - 1) / kEngTX) * ((sp.Ny + sp.ty - 1) / sp.ty);
     size_t n = 0;
     n += align256(g64.elems() * 8) * (sp.mode == CJ_FP32_INNER_DD ? 3 : 2);
     n += align256(g32.elems() * 4) * 3;
@@ -149,9 +149,12 @@ class Engine {
         S.Ny = sp.Ny;
         S.st = sp.st;
         S.mode = sp.mode;
-        S.depth = sp.depth;
+        // a depth the engine has no shared memory for (an autotuned one in the server, whose
+        // engine sweeps one at a time) runs at the engine's maximum
+        S.depth = std::min(sp.depth, max_depth_);
+        S.ty = sp.ty;
         S.ntx = (sp.Nx + kEngTX - 1) / kEngTX;
-        S.ntiles = S.ntx * ((sp.Ny + kEngTY - 1) / kEngTY);
+        S.ntiles = S.ntx * ((sp.Ny + sp.ty - 1) / sp.ty);
         S.M_in = M_in;
         const long long max_sweeps = sp.max_sweeps ? sp.max_sweeps : 64 * M_in;
         S.max_outer = max_sweeps / M_in;
@@ -244,7 +247,7 @@ class Engine {
             if (st != CJ_OK) return st;
         }
         for (int k = 0; k < replays; ++k) ENG_TRY(cudaGraphLaunch(gexec_, s_), "graph launch");
-        launches_ += (long long)replays * steps_per_graph_ * (4 + 2 * kSweepsPerStep);
+        launches_ += (long long)replays * steps_per_graph_ * (4 + (smem_ > 0 ? 3 : 2) * kSweepsPerStep);
         ENG_TRY(cudaMemcpyAsync(h_status_, d_.status, sizeof(SlotStatus) * max_slots_,
                                 cudaMemcpyDeviceToHost, s_), "status readback");
         ENG_TRY(cudaStreamSynchronize(s_), "step sync");
@@ -331,6 +334,19 @@ int auto_mode(int st, int Nx, int Ny, double tol) {
     return 4.0 * fl > tol ? CJ_FP32_INNER_DD : CJ_FP32_INNER;
 }
 
+// Engine tile rows and temporal depth per (stencil, size class) recorded by
+// cj_autotune_engine; 0 = not tuned (tile rows 32, depth 1).
+struct EngineTune {
+    int ty, depth;
+};
+std::mutex g_engine_tune_mu;
+EngineTune g_engine_tune[3][32] = {};
+
+EngineTune engine_tuned(int st, int Nx, int Ny) {
+    std::lock_guard<std::mutex> lk(g_engine_tune_mu);
+    return g_engine_tune[stencil_slot(st)][size_class(Nx, Ny)];
+}
+
 cj_status check_problem(const cj_problem &pr) {
     if (pr.Nx < 1 || pr.Ny < 1 || pr.Nx > (1 << 20) || pr.Ny > (1 << 20)) return CJ_ERR_INVALID_ARG;
     if (pr.st != CJ_ST5 && pr.st != CJ_ST9 && pr.st != CJ_ST17) return CJ_ERR_INVALID_ARG;
@@ -351,7 +367,9 @@ Spec spec_of(const cj_problem &pr) {
     sp.tol = pr.tol;
     sp.mode = pr.precision ? pr.precision : auto_mode(pr.st, pr.Nx, pr.Ny, pr.tol);
     sp.inner_cycle = pr.inner_cycle;
-    sp.depth = pr.temporal_depth ? pr.temporal_depth : 1;
+    EngineTune t = engine_tuned(pr.st, pr.Nx, pr.Ny);
+    sp.depth = pr.temporal_depth ? pr.temporal_depth : (t.depth ? t.depth : 1);
+    sp.ty = t.ty ? t.ty : kEngTYDefault;
     sp.max_sweeps = pr.max_sweeps;
     return sp;
 }
@@ -540,7 +558,7 @@ cj_status cj_solve_batch(const cj_problem *problems, int n, void *stream, cj_res
     for (int k = 0; k < n; ++k) {
         cj_status st = check_problem(problems[k]);
         if (st != CJ_OK) return st;
-        max_depth = std::max(max_depth, problems[k].temporal_depth);
+        max_depth = std::max(max_depth, spec_of(problems[k]).depth);  // requested or autotuned
     }
     auto t0 = Clock::now();
     Engine eng;
@@ -594,6 +612,79 @@ cj_status cj_solve_batch(const cj_problem *problems, int n, void *stream, cj_res
     ENG_TRY(cudaStreamSynchronize(eng.stream()), "batch sync");
     cudaEventDestroy(ev);
     return all ? CJ_OK : CJ_ERR_TIMEOUT;
+}
+
+cj_status cj_autotune_engine(int Nx, int Ny, cj_stencil st, int *tile_rows, int *depth, double *gupd) {
+    if (Nx < 1 || Ny < 1 || Nx > (1 << 20) || Ny > (1 << 20)) return CJ_ERR_INVALID_ARG;
+    if (st != CJ_ST5 && st != CJ_ST9 && st != CJ_ST17) return CJ_ERR_INVALID_ARG;
+    // candidates, the default (32 rows, depth 1) first so that it wins ties
+    const int tys[9] = {32, 16, 64, 32, 16, 64, 32, 16, 64};
+    const int dps[9] = {1, 1, 1, 2, 2, 2, 4, 4, 4};
+    const int kReplays = 8;  // 8 replays x 8 steps x 4 sweep launches
+    double rate[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+    // a synthetic problem of this class: f constant (every byte 0x3F, about 4.8e-4), u0 = 0,
+    // a tolerance no slot reaches within the timed replays
+    const size_t bytes = (size_t)Nx * Ny * sizeof(double);
+    double *f = nullptr;
+    ENG_TRY(cudaMalloc((void **)&f, bytes), "autotune grid");
+    cudaError_t e = cudaMemset(f, 0x3F, bytes);
+    if (e != cudaSuccess) {
+        cudaFree(f);
+        set_cuda_error(e, "autotune grid");
+        return CJ_ERR_CUDA;
+    }
+    // as many copies of the problem as fill the device with tiles (a loaded engine, as in a
+    // batch), within 256 slots and 2^24 nodes
+    int sms = 152, dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const long long tiles32 = (long long)((Nx + kEngTX - 1) / kEngTX) * ((Ny + 31) / 32);
+    long long copies = (8LL * sms + tiles32 - 1) / tiles32;
+    copies = std::min<long long>(copies, 256);
+    copies = std::max<long long>(1, std::min<long long>(copies, (1LL << 24) / ((long long)Nx * Ny)));
+    cj_status rc = CJ_OK;
+    for (int c = 0; c < 9 && rc == CJ_OK; ++c) {
+        Engine eng;
+        rc = eng.init((int)copies, dps[c]);
+        if (rc != CJ_OK) break;
+        Spec sp{};
+        sp.Nx = Nx;
+        sp.Ny = Ny;
+        sp.st = st;
+        sp.mode = CJ_FP32_INNER_DD;
+        sp.inner_cycle = 0;
+        sp.depth = dps[c];
+        sp.ty = tys[c];
+        sp.tol = 1e-15;
+        sp.max_sweeps = 0;
+        std::vector<int> q(copies, -1);
+        for (long long k = 0; k < copies && rc == CJ_OK; ++k)
+            rc = eng.admit(sp, f, Nx, nullptr, 0, nullptr, 0, &q[k], true);  // results into own slot
+        if (rc == CJ_OK) rc = eng.run(2);  // capture and warm-up
+        if (rc != CJ_OK) break;
+        long long s0 = 0, s1 = 0;
+        for (long long k = 0; k < copies; ++k) s0 += eng.status(q[k]).sweeps;
+        const auto t0 = Clock::now();
+        rc = eng.run(kReplays);
+        const double secs = std::chrono::duration<double>(Clock::now() - t0).count();
+        if (rc != CJ_OK) break;
+        for (long long k = 0; k < copies; ++k) s1 += eng.status(q[k]).sweeps;
+        rate[c] = (double)Nx * Ny * (double)(s1 - s0) / secs / 1e9;
+    }
+    cudaFree(f);
+    if (rc != CJ_OK) return rc;
+    int best = 0;
+    for (int c = 1; c < 9; ++c)
+        if (rate[c] > rate[best]) best = c;
+    {
+        std::lock_guard<std::mutex> lk(g_engine_tune_mu);
+        g_engine_tune[stencil_slot(st)][size_class(Nx, Ny)] = EngineTune{tys[best], dps[best]};
+    }
+    if (tile_rows) *tile_rows = tys[best];
+    if (depth) *depth = dps[best];
+    if (gupd)  // tile rows 16, 32, 64 (major) x depth 1, 2, 4
+        for (int c = 0; c < 9; ++c) gupd[(tys[c] == 16 ? 0 : tys[c] == 32 ? 1 : 2) * 3 + (dps[c] == 1 ? 0 : dps[c] == 2 ? 1 : 2)] = rate[c];
+    return CJ_OK;
 }
 
 cj_status cj_server_create(size_t hbm_budget_bytes, int max_slots, cj_server **out) {

@@ -79,6 +79,10 @@ void plan_sweep_coeffs(int st, double kmin, double kmax, long long M, std::vecto
 // the same with the centre c given (c = 1: the weights omega_n of a Jacobi-normalised operator)
 void plan_sweep_coeffs_c(double c, double kmin, double kmax, long long M, std::vector<double> &w);
 
+// ---- autotuning tables (solve.cpp): stencil index 0/1/2 and size class floor(log4(Nx Ny))
+int stencil_slot(int st);
+int size_class(int Nx, int Ny);
+
 // ---- error reporting (solve.cpp)
 void set_cuda_error(cudaError_t e, const char *where);
 void set_error_text(const char *msg);

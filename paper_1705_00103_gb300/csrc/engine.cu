@@ -37,11 +37,11 @@ struct TileRef {
 __device__ __forceinline__ TileRef tile_ref(const SlotDev &S, int slot, int lt) {
     TileRef t;
     t.slot = slot;
-    const int tx = lt % S.ntx, ty = lt / S.ntx;
+    const int tx = lt % S.ntx, tyi = lt / S.ntx;
     t.i0 = tx * kEngTX + 1;
-    t.j0 = ty * kEngTY + 1;
+    t.j0 = tyi * S.ty + 1;
     t.i1 = min(t.i0 + kEngTX - 1, S.Nx);
-    t.j1 = min(t.j0 + kEngTY - 1, S.Ny);
+    t.j1 = min(t.j0 + S.ty - 1, S.Ny);
     return t;
 }
 
@@ -206,21 +206,25 @@ __device__ __forceinline__ void sweep_tile(SlotDev &S, const TileRef &T, int k, 
     float *eout = S.cur ? S.e0 : S.e1;
     if (k == 1) {
         // four warps split the tile's rows; each lane takes four adjacent columns (march4)
-        constexpr int kRowsPerWarp = kEngTY / (kEngThreads / 32);
+        const int rows_per_warp = (S.ty + kEngThreads / 32 - 1) / (kEngThreads / 32);
         const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
         const int c0 = T.i0 + 4 * lane;
-        const int js = T.j0 + warp * kRowsPerWarp;
-        const int je = min(js + kRowsPerWarp - 1, T.j1);
+        const int js = T.j0 + warp * rows_per_warp;
+        const int je = min(js + rows_per_warp - 1, T.j1);
         if (c0 > T.i1 || js > je) return;
         M4Store<ST> op{eout, &S.g32, c0, S.w32[S.counter]};
         march4<ST>(ein, S.rt, S.g32, c0, js, je, op);
     } else {
         float w[kTbMaxDepth];
         for (int s = 0; s < k; ++s) w[s] = S.w32[S.counter + s];
-        tb_tile<ST>(ein, S.rt, eout, S.g32, k, w, T.i0, T.j0, kEngTX, kEngTY, sm);
+        tb_tile<ST>(ein, S.rt, eout, S.g32, k, w, T.i0, T.j0, kEngTX, S.ty, sm);
     }
 }
 
+// Sweep launches: tiles whose slot advances one sweep now (k = 1: march4, no shared memory)
+// and tiles of temporally blocked slots (k > 1: tb_tile in dynamic shared memory) go to two
+// kernels, so that the blocked tiles' shared memory does not lower the occupancy of the rest.
+template <bool BLOCKED>
 __global__ void __launch_bounds__(kEngThreads) eng_sweep(EngineDev E) {
     extern __shared__ float sm[];
     const int n = *E.ntiles;
@@ -228,10 +232,11 @@ __global__ void __launch_bounds__(kEngThreads) eng_sweep(EngineDev E) {
         const int2 ref = E.tiles[t];
         SlotDev &S = E.slots[ref.x];
         if (S.phase != PHASE_SWEEP) continue;
-        const TileRef T = tile_ref(S, ref.x, ref.y);
         const long long left = S.M_in - S.counter;
         const int k = (int)(S.depth < left ? S.depth : left);
-        __syncthreads();  // the previous tile's shared-memory stage is finished
+        if ((k > 1) != BLOCKED) continue;
+        const TileRef T = tile_ref(S, ref.x, ref.y);
+        if (BLOCKED) __syncthreads();  // the previous tile's shared-memory stage is finished
         if (S.st == 5)
             sweep_tile<5>(S, T, k, sm);
         else if (S.st == 9)
@@ -371,11 +376,11 @@ __global__ void __launch_bounds__(kEngThreads) eng_admit(EngineDev E, int slot) 
 size_t eng_sweep_smem(int max_depth) {
     if (max_depth <= 1) return 0;
     const int H = 2 * max_depth;  // radius 2 covers every stencil
-    return (size_t)3 * (kEngTX + 2 * H) * (kEngTY + 2 * H) * sizeof(float);
+    return (size_t)3 * (kEngTX + 2 * H) * (kEngTYMax + 2 * H) * sizeof(float);
 }
 
 cudaError_t eng_prepare(size_t sweep_smem) {
-    return cudaFuncSetAttribute(eng_sweep, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    return cudaFuncSetAttribute(eng_sweep<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)(sweep_smem > 0 ? sweep_smem : 0));
 }
 
@@ -386,7 +391,8 @@ cudaError_t eng_launch_step(const EngineDev &e, int grid_tiles, int grid_slots, 
     eng_defect<<<grid_tiles, kEngThreads, 0, s>>>(e);
     eng_decide<<<grid_slots, kEngThreads, 0, s>>>(e);
     for (int q = 0; q < sweeps; ++q) {
-        eng_sweep<<<grid_tiles, kEngThreads, sweep_smem, s>>>(e);
+        eng_sweep<false><<<grid_tiles, kEngThreads, 0, s>>>(e);
+        if (sweep_smem > 0) eng_sweep<true><<<grid_tiles, kEngThreads, sweep_smem, s>>>(e);
         if (q + 1 < sweeps) eng_advance<<<grid_adv, 128, 0, s>>>(e, 0);
     }
     eng_export<<<grid_tiles, kEngThreads, 0, s>>>(e);

@@ -6,8 +6,10 @@
 
 #include "cj_internal.h"
 
-// Engine tile: the unit of work of every engine kernel (columns x rows of nodes).
-constexpr int kEngTX = 128, kEngTY = 32;
+// Engine tile: the unit of work of every engine kernel, kEngTX columns x (per slot) ty rows of
+// nodes; ty is 16, 32 (the default) or 64, chosen per stencil and size class by
+// cj_autotune_engine.
+constexpr int kEngTX = 128, kEngTYDefault = 32, kEngTYMax = 64;
 
 enum SlotPhase : int {
     PHASE_FREE = 0,     // unused
@@ -20,7 +22,7 @@ enum SlotPhase : int {
 struct SlotDev {
     // set at admission
     int Nx, Ny, st, mode;          // mode: CJ_FP32_INNER or CJ_FP32_INNER_DD
-    int depth, ntx, ntiles, pad0;
+    int depth, ntx, ntiles, ty;    // ty: tile rows
     long long M_in, max_outer;
     double tol, S, h2;
     Grid g64, g32;

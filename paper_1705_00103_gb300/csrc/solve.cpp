@@ -13,15 +13,6 @@
 
 #include "cj_internal.h"
 
-namespace {
-
-thread_local char g_err[256] = "";
-
-// Autotuned FP32 temporal depth per (stencil, size class); size class = floor(log2(Nx*Ny)/2),
-// i.e. grids within a factor 2 of each other per side share a class.  0 = not tuned.
-std::mutex g_tune_mu;
-int g_tuned_depth[3][32] = {};
-
 int stencil_slot(int st) { return st == 5 ? 0 : st == 9 ? 1 : 2; }
 
 int size_class(int Nx, int Ny) {
@@ -33,6 +24,16 @@ int size_class(int Nx, int Ny) {
     }
     return c < 32 ? c : 31;
 }
+
+namespace {
+
+thread_local char g_err[256] = "";
+
+// Autotuned FP32 temporal depth per (stencil, size class); size class = floor(log2(Nx*Ny)/2),
+// i.e. grids within a factor 2 of each other per side share a class.  0 = not tuned.
+std::mutex g_tune_mu;
+int g_tuned_depth[3][32] = {};
+
 
 int tuned_depth(int st, int Nx, int Ny) {
     std::lock_guard<std::mutex> lk(g_tune_mu);

@@ -164,3 +164,21 @@ def test_server_rejects_bad_request(cj):
             srv.submit(np.zeros((4, 4)), 6, 1e-8)
         with pytest.raises(cj.CJError):
             srv.submit(np.zeros((4, 4)), 5, 2.0)
+
+
+def test_engine_autotune_records_and_uses_its_choice(cj, torch):
+    """The engine autotuner times tile rows x depth on a problem of the size class, records the
+    fastest, and a batch of that class then runs with it -- to the oracle's bits.  (Run last in
+    this file: the choice stays in the process's table.)"""
+    Nx, Ny, st = 300, 200, 9
+    r = cj.cj_autotune_engine(Nx, Ny, st)
+    assert r["tile_rows"] in (16, 32, 64) and r["depth"] in (1, 2, 4)
+    assert all(v > 0 for v in r["gupd"].values())
+    assert r["gupd"][(r["tile_rows"], r["depth"])] == max(r["gupd"].values())
+    f, pr = _problem(torch, Nx, Ny, st, 1e-8, 1, 128, 0, 31)  # temporal_depth 0: the tuned one
+    res = cj.cj_solve_batch([pr])
+    ref = _oracle(Nx, Ny, st, 1e-8, 1, 128, f)
+    assert res[0]["sweeps"] == ref["sweeps"] and res[0]["cycles"] == ref["outer"]
+    np.testing.assert_array_equal(pr["u"].cpu().numpy(), ref["u"])
+    with pytest.raises(cj.CJError):
+        cj.cj_autotune_engine(0, 10, 9)
