@@ -111,7 +111,8 @@ class ClockSampler:
     """nvidia-smi sampled every 200 ms during the timed region."""
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
-              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap,"
+              "clocks.mem,clocks.max.mem")
 
     def __init__(self, index: int):
         self.index = index
@@ -136,7 +137,7 @@ class ClockSampler:
         except Exception:
             self.proc.kill()
         self.fh.close()
-        sm, smax, reasons, power = [], [], set(), []
+        sm, smax, reasons, power, mem, mmax = [], [], set(), [], [], []
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         for line in open(self.path):
             parts = [x.strip() for x in line.split(",")]
@@ -151,11 +152,20 @@ class ClockSampler:
             for nm, v in zip(names, parts[5:9]):
                 if v.lower().startswith("active"):
                     reasons.add(nm)
+            try:
+                mem.append(float(parts[9]))
+                mmax.append(float(parts[10]))
+            except (ValueError, IndexError):
+                pass
         os.unlink(self.path)
         if not sm:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
-        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
-                "power_w_max": max(power), "samples": len(sm)}
+        out = {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+               "power_w_max": max(power), "samples": len(sm)}
+        if mem:
+            out["mem_mhz"] = statistics.median(mem)
+            out["mem_max_mhz"] = max(mmax)
+        return out
 
 
 # ----------------------------------------------------------------- traffic record
@@ -291,7 +301,10 @@ def run_cj(args):
 
     mixed = None
     if not args.no_mixed:
+        mclk = ClockSampler(local)
+        mclk.start()
         mixed = mixed_paths(cj, rhs_dev[1], stream, results[1])
+        mixed["clocks"] = mclk.stop()
     launches = sum(r["launches"] for r in results)
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
