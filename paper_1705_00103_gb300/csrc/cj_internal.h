@@ -138,9 +138,6 @@ cudaError_t launch_defect_dd(const cj_plan *p, const double *uh, const double *u
                              float *e_zero, cudaStream_t s);
 cudaError_t launch_correct_dd(const cj_plan *p, double *uh, double *ul, const float *e,
                               cudaStream_t s);
-// temporal-blocked FP32 sweeps (tblock.cu): `depth` sweeps with weights w[0..depth-1]
-cudaError_t launch_sweep32_tb(const cj_plan *p, const float *e, const float *r, float *out,
-                              const float *w, int depth, cudaStream_t s);
 // wavefront temporal-blocked FP32 sweeps (wave.cu): k in {2, 4, 8} sweeps per launch
 int wave_depth_supported(int k);
 cudaError_t launch_sweep32_wave(const cj_plan *p, const float *e, const float *r, float *out,

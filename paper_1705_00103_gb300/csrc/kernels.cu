@@ -41,8 +41,8 @@ struct SweepOp {
     }
 };
 
-// One weighted sweep: out = u + w (L u - b).  FP64 in the pair-sum order above; FP32 in the
-// difference form (march32), which keeps the smooth modes' digits on fine grids.
+// One FP64 weighted sweep: out = u + w (L u - b) in the pair-sum order above (the FP32 inner
+// sweep, in difference form, is sweep32.cu's).
 // MIRROR: rewrite the odd-reflection ghosts of the 17-point stencil (homogeneous boundary);
 // without it the ghost ring holds fixed Dirichlet data and is left alone.
 template <int ST, typename T, bool MIRROR = true>
@@ -54,10 +54,7 @@ __global__ void __launch_bounds__(kBX) sweep_kernel(const T *__restrict__ u,
     const int j1 = min(j0 + ty - 1, g.Ny);
     if (i > g.Nx) return;
     SweepOp<ST, T, MIRROR> op{out, &g, i, w};
-    if constexpr (sizeof(T) == 4)
-        march32<ST, false>(u, b, g, i, j0, j1, op);
-    else
-        march<ST, T>(u, b, g, i, j0, j1, one, op);
+    march<ST, T>(u, b, g, i, j0, j1, one, op);
 }
 
 struct ResidOp {

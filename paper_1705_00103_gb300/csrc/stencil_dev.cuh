@@ -144,116 +144,6 @@ __device__ __forceinline__ void march(const T *__restrict__ u, const T *__restri
 }
 
 
-// march with the loads of the next row issued one iteration ahead (the padded layout
-// always has the rows they touch), so each warp keeps two rows of loads in flight.  Same
-// arithmetic as march.  It pays on short column segments (the engine's 32-row tiles: the
-// 512-problem batch runs 12 % faster); on long ones the extra registers cost more than the
-// latency they hide, so the one-problem kernels keep march.
-template <int ST, typename T, class Op>
-__device__ __forceinline__ void march_prefetch(const T *__restrict__ u, const T *__restrict__ b,
-                                      const Grid &g, int i, int j0, int j1, T one, Op &op) {
-    using A = Ar<T>;
-    using C = Co<T>;
-    const long long P = g.pitch;
-    const T *col = u + g.idx(i, 0);  // node (i, 0); row k at col + k * P
-    const T *bcol = b + g.idx(i, 0);
-    if (ST == 5) {
-        T um = ld(col + (long long)(j0 - 1) * P);
-        T uc = ld(col + (long long)j0 * P);
-        const T *row = col + (long long)j0 * P;
-        T nW = ld(row - 1), nE = ld(row + 1), nN = ld(row + P), nB = ld(bcol + (long long)j0 * P);
-        for (int j = j0; j <= j1; ++j) {
-            const T w_ = nW, e_ = nE, up = nN, bk = nB;
-            row += P;  // row j+1; rows up to Ny+1 exist
-            nW = ld(row - 1);
-            nE = ld(row + 1);
-            nN = ld(row + P);
-            nB = ld(bcol + (long long)(j + 1) * P);
-            T p0 = A::add(w_, e_, one);
-            T v1 = A::add(um, up, one);
-            T a = A::add(p0, v1, one);
-            T r = A::add(a, A::fm(C::c5(), uc, -bk), one);
-            op(j, r, uc);
-            um = uc;
-            uc = up;
-        }
-    } else if (ST == 9) {
-        const T *row = col + (long long)(j0 - 1) * P;
-        T um = ld(row);
-        T pm = A::add(ld(row - 1), ld(row + 1), one);
-        row += P;
-        T uc = ld(row);
-        T pc = A::add(ld(row - 1), ld(row + 1), one);
-        row += P;  // row j0+1
-        T nU = ld(row), nW = ld(row - 1), nE = ld(row + 1), nB = ld(bcol + (long long)j0 * P);
-        for (int j = j0; j <= j1; ++j) {
-            const T up = nU, w_ = nW, e_ = nE, bk = nB;
-            row += P;  // row j+2; rows up to Ny+2 exist
-            nU = ld(row);
-            nW = ld(row - 1);
-            nE = ld(row + 1);
-            nB = ld(bcol + (long long)(j + 1) * P);
-            T pp = A::add(w_, e_, one);
-            T v1 = A::add(um, up, one);
-            T a = A::add(pc, v1, one);
-            T d = A::add(pm, pp, one);
-            T r = A::fm(C::ax9(), a, A::fm(C::dg9(), d, A::fm(C::cc9(), uc, -bk)));
-            op(j, r, uc);
-            um = uc;
-            uc = up;
-            pm = pc;
-            pc = pp;
-        }
-    } else {
-        // rows j-2 .. j+1 in registers on entry to each iteration; row j+2 loaded one
-        // iteration ahead (row index clamped to the padded range; the clamped load is unused)
-        T u_[4], p_[4], Q_[4];
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            const T *row = col + (long long)(j0 - 2 + k) * P;
-            u_[k] = ld(row);
-            p_[k] = A::add(ld(row - 1), ld(row + 1), one);
-            Q_[k] = A::add(ld(row - 2), ld(row + 2), one);
-        }
-        const int jmax = g.Ny + 2;
-        const T *row = col + (long long)(j0 + 2) * P;
-        T n0 = ld(row), n1 = ld(row - 1), n2 = ld(row + 1), n3 = ld(row - 2), n4 = ld(row + 2);
-        T nB = ld(bcol + (long long)j0 * P);
-        for (int j = j0; j <= j1; ++j) {
-            const T u4 = n0, w1 = n1, e1 = n2, w2 = n3, e2 = n4, bk = nB;
-            const int jn = j + 3 <= jmax ? j + 3 : jmax;
-            row = col + (long long)jn * P;
-            n0 = ld(row);
-            n1 = ld(row - 1);
-            n2 = ld(row + 1);
-            n3 = ld(row - 2);
-            n4 = ld(row + 2);
-            nB = ld(bcol + (long long)(j + 1) * P);
-            T p4 = A::add(w1, e1, one);
-            T Q4 = A::add(w2, e2, one);
-            // u_[0..3] = rows j-2, j-1, j, j+1; u4 = row j+2
-            T v1 = A::add(u_[1], u_[3], one);
-            T v2 = A::add(u_[0], u4, one);
-            T a1 = A::add(p_[2], v1, one);
-            T a2 = A::add(Q_[2], v2, one);
-            T d1 = A::add(p_[1], p_[3], one);
-            T d2 = A::add(Q_[0], Q4, one);
-            T r = A::fm(C::a1(), a1,
-                        A::fm(C::a2(), a2,
-                              A::fm(C::d1(), d1, A::fm(C::d2(), d2, A::fm(C::cc17(), u_[2], -bk)))));
-            op(j, r, u_[2]);
-#pragma unroll
-            for (int k = 0; k < 3; ++k) {
-                u_[k] = u_[k + 1];
-                p_[k] = p_[k + 1];
-                Q_[k] = Q_[k + 1];
-            }
-            u_[3] = u4;
-            p_[3] = p4;
-            Q_[3] = Q4;
-        }
-    }
-}
 
 // FP32 residual in difference form, L e - rk = sum_k c_k (e_k - e_C) - rk: every neighbour
 // enters as its (for smooth e, exact) difference from the centre, so the smooth low modes
@@ -276,59 +166,6 @@ __device__ __forceinline__ float resid_diff32(F N, float uC, float rk) {
                      fmaf(16.0f / 72.0f, pm + pp, fmaf(-1.0f / 72.0f, Pm + Pp, -rk))));
 }
 
-// FP32 y-march in difference form: column i, rows j0..j1, op(j, r, e(i,j)) with
-// r = (L e - b)(i, j).  Each thread keeps the (2R+1) x (2R+1) neighbourhood of its column
-// in registers and loads one new row of 2R+1 values (and b) per step; with PF the next
-// row's loads are issued one step ahead (the padded layout always holds the rows touched).
-template <int ST, bool PF, class Op>
-__device__ __forceinline__ void march32(const float *__restrict__ u, const float *__restrict__ b,
-                                        const Grid &g, int i, int j0, int j1, Op &op) {
-    constexpr int R = ST == 17 ? 2 : 1, W = 2 * R + 1;
-    const long long P = g.pitch;
-    const float *col = u + g.idx(i, 0);  // node (i, 0); row k at col + k * P
-    const float *bcol = b + g.idx(i, 0);
-    float win[W][W];  // win[row offset + R][column offset + R] around (i, j)
-#pragma unroll
-    for (int dy = -R; dy < R; ++dy) {
-        const float *row = col + (long long)(j0 + dy) * P;
-#pragma unroll
-        for (int dx = -R; dx <= R; ++dx) win[dy + R + 1][dx + R] = __ldg(row + dx);
-    }
-    float nxt[W], nb = 0.0f;
-    if (PF) {
-        const float *row = col + (long long)(j0 + R) * P;
-#pragma unroll
-        for (int dx = -R; dx <= R; ++dx) nxt[dx + R] = __ldg(row + dx);
-        nb = __ldg(bcol + (long long)j0 * P);
-    }
-    for (int j = j0; j <= j1; ++j) {
-        // shift the window up one row and bring in row j + R
-#pragma unroll
-        for (int q = 0; q < W - 1; ++q)
-#pragma unroll
-            for (int dx = 0; dx < W; ++dx) win[q][dx] = win[q + 1][dx];
-        float bk;
-        if (PF) {
-#pragma unroll
-            for (int dx = 0; dx < W; ++dx) win[W - 1][dx] = nxt[dx];
-            bk = nb;
-            int jn = j + R + 1;
-            if (jn > g.Ny + 2) jn = g.Ny + 2;  // clamped; that load is never used
-            const float *row = col + (long long)jn * P;
-#pragma unroll
-            for (int dx = -R; dx <= R; ++dx) nxt[dx + R] = __ldg(row + dx);
-            nb = __ldg(bcol + (long long)(j + 1) * P);
-        } else {
-            const float *row = col + (long long)(j + R) * P;
-#pragma unroll
-            for (int dx = -R; dx <= R; ++dx) win[W - 1][dx + R] = __ldg(row + dx);
-            bk = __ldg(bcol + (long long)j * P);
-        }
-        const float uc = win[R][R];
-        auto N = [&](int dx, int dy) { return win[R + dy][R + dx]; };
-        op(j, resid_diff32<ST>(N, uc, bk), uc);
-    }
-}
 
 // (L u - b)(i, j) evaluated directly from a node accessor U(di, dj), in the same order as
 // march (so the two agree bit for bit).
