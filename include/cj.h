@@ -119,8 +119,9 @@ const char *cj_last_error(void);
 /*
  * cj_plan_create -- precompute everything a solve of this problem needs (Sec. 2.1:
  * the weights are "precalculated before starting the iterative algorithm").
- *   Nx, Ny >= 1 interior nodes; st in {5, 9, 17}; bc = CJ_BC_DIRICHLET0;
- *   0 < tol < 1 is the relative residual target.
+ *   1 <= Nx, Ny <= 2^20 interior nodes; st in {5, 9, 17}; bc = CJ_BC_DIRICHLET0 or
+ *   CJ_BC_DIRICHLET (data set by cj_set_boundary); 0 < tol < 1 is the relative residual
+ *   target; the cycle length may not exceed 2^24 sweeps.
  * Computes kmin, kmax, the cycle length M (smallest power of two whose Chebyshev
  * bound reaches tol), the M weights in mirror-pairing order and the sweep table
  * w_n = omega_n / c; allocates the device workspace on the current device (two padded

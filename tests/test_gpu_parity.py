@@ -250,7 +250,7 @@ def test_full_size_sweeps_bit_exact(cj, torch, st, N):
         cj.cj_sweeps(p.handle, fd, ud, 0, 2)
         got = ud.cpu().numpy()
     b = orc.scale_rhs(f)
-    ref = orc.sweep(st, orc.sweep(st, u0, b, w[0]), b, w[1])
+    ref = orc.sweep(st, orc.sweep(st, u0, b, w[0]), b, w[1 % len(w)])
     np.testing.assert_array_equal(got, ref)
 
 
@@ -556,3 +556,29 @@ def test_launch_modes_give_identical_solves(cj, torch, st, method, data):
         outs.append(ud.cpu().numpy())
     for u in outs:
         np.testing.assert_array_equal(u, ref["u"])
+
+
+# ----------------------------------------------------------------- the largest sides
+
+@pytest.mark.parametrize("Nx,Ny", [(1 << 20, 1), (1, 1 << 20)])
+def test_largest_side_sweeps_bit_exact(cj, torch, Nx, Ny):
+    """Grids at the largest side the plan accepts (2^20 nodes): FP64 and FP32 sweeps equal the
+    oracle's (a tolerance of 0.5 keeps the cycle within the 2^24-sweep limit)."""
+    st = 9
+    f, u0 = rand_problem(Nx, Ny, 4)
+    with cj.Plan(Nx, Ny, st, 0.5, launch=cj.CJ_LAUNCH_STREAM) as p:
+        w = p.info()["w"]
+        ud = dev(torch, u0)
+        cj.cj_sweeps(p.handle, dev(torch, f), ud, 0, 2)
+    b = orc.scale_rhs(f)
+    ref = orc.sweep(st, orc.sweep(st, u0, b, w[0]), b, w[1 % len(w)])
+    np.testing.assert_array_equal(ud.cpu().numpy(), ref)
+    r = np.random.default_rng(5).standard_normal((Ny, Nx)).astype(np.float32)
+    e0 = np.random.default_rng(6).standard_normal((Ny, Nx)).astype(np.float32)
+    with cj.Plan(Nx, Ny, st, 0.5, precision=cj.CJ_FP32_INNER, inner_cycle=4) as p:
+        kmin, kmax = orc.kappa_bounds(st, Nx, Ny)
+        w32 = orc.sweep_coeffs(st, kmin, kmax, 4).astype(np.float32)
+        ed = torch.from_numpy(e0).cuda()
+        cj.cj_sweeps_f32(p.handle, torch.from_numpy(r).cuda(), ed, 0, 2)
+    ref32 = orc.sweep_f32(st, orc.sweep_f32(st, e0, r, w32[0]), r, w32[1])
+    np.testing.assert_array_equal(ed.cpu().numpy(), ref32)
