@@ -80,6 +80,7 @@ class Engine {
         host_.assign(max_slots, SlotDev{});
         mem_.assign(max_slots, SlotMem{});
         used_.assign(max_slots, 0);
+        tiles_off_.assign(max_slots, 0);
         ENG_TRY(cudaMalloc(&d_.slots, sizeof(SlotDev) * max_slots), "engine slots");
         ENG_TRY(cudaMemset(d_.slots, 0, sizeof(SlotDev) * max_slots), "engine slots");
         ENG_TRY(cudaMalloc(&d_.status, sizeof(SlotStatus) * max_slots), "engine status");
@@ -210,6 +211,7 @@ class Engine {
         mem_[q].base = base;
         mem_[q].bytes = bytes;
         used_[q] = 1;
+        tiles_off_[q] = 0;
         tiles_dirty_ = true;
         *slot_out = q;
         return CJ_OK;
@@ -222,6 +224,15 @@ class Engine {
     }
 
     size_t slot_mem(int q) const { return mem_[q].bytes; }
+
+    // Takes a retired slot's tiles out of the tile list (its memory and status stay): every
+    // engine kernel scans the list, so a batch's tail runs only over the slots still working.
+    void drop_tiles(int q) {
+        if (q >= 0 && q < max_slots_ && used_[q] && !tiles_off_[q]) {
+            tiles_off_[q] = 1;
+            tiles_dirty_ = true;
+        }
+    }
 
     // Frees slot q (after its result has been read).
     cj_status release(int q) {
@@ -279,7 +290,7 @@ class Engine {
     cj_status upload_tiles() {
         tiles_.clear();
         for (int q = 0; q < max_slots_; ++q)
-            if (used_[q])
+            if (used_[q] && !tiles_off_[q])
                 for (int t = 0; t < host_[q].ntiles; ++t) tiles_.push_back(make_int2(q, t));
         cj_status st = ensure_tile_capacity((int)tiles_.size() + 1);
         if (st != CJ_OK) return st;
@@ -314,7 +325,7 @@ class Engine {
     EngineDev d_{};
     std::vector<SlotDev> host_;
     std::vector<SlotMem> mem_;
-    std::vector<char> used_;
+    std::vector<char> used_, tiles_off_;
     std::vector<int2> tiles_;
     std::vector<float> wstage_;
     int tile_cap_ = 0;
@@ -596,8 +607,12 @@ cj_status cj_solve_batch(const cj_problem *problems, int n, void *stream, cj_res
             return st;
         }
         all = true;
-        for (int k = 0; k < n; ++k)
-            if (eng.status(slot[k]).phase != PHASE_RETIRED) all = false;
+        for (int k = 0; k < n; ++k) {
+            if (eng.status(slot[k]).phase != PHASE_RETIRED)
+                all = false;
+            else
+                eng.drop_tiles(slot[k]);
+        }
     }
     const double secs = std::chrono::duration<double>(Clock::now() - t0).count();
     for (int k = 0; k < n; ++k) {
