@@ -10,8 +10,11 @@
  * Jacobi iteration matrix, whose ends the paper gives in closed form for each stencil
  * (equations after Eq. 1 and Eq. 2).  Stencils: the classical 5-point Laplacian (Table 3,
  * Cartesian row), the 9-point alpha = 2/3 Laplacian (Eq. 1) and the 17-point alpha = 2/3
- * Laplacian (Eq. 2).  Boundary: homogeneous Dirichlet (u = 0 on nodes 0 and N+1); the
- * 17-point stencil's second ghost layer is the odd reflection u[-1] = -u[1].
+ * Laplacian (Eq. 2).  Boundary: homogeneous Dirichlet (u = 0 on nodes 0 and N+1; the
+ * 17-point stencil's second ghost layer is the odd reflection u[-1] = -u[1]), or Dirichlet
+ * data on both rings (CJ_BC_DIRICHLET, the paper's test problem).  Also: classical Jacobi
+ * (CJ_JACOBI), the real-error stop (cj_solve_to_error), position-dependent coefficient
+ * masks (cj_plan_create_mask), batched solves and a request server.
  *
  * Conventions for every entry point:
  *   - Grids passed in or out are interior values only, row-major: node (i, j) is element
@@ -308,7 +311,8 @@ typedef struct {
                                FP64 floor (about 2^-53 S / (c kmin)) is within 4x of tol */
     double tol;
     int inner_cycle;        /* 0 = the planner's choice */
-    int temporal_depth;     /* FP32 sweeps per engine step, 1..8; 0 = 1 */
+    int temporal_depth;     /* FP32 sweeps per sweep launch (temporal blocking), 1..8; 0 = the
+                               cj_autotune_engine choice for the size class, else 1 */
     long long max_sweeps;   /* 0 = 64 inner cycles */
     const double *f;        /* device, Ny x ld_f, unscaled right-hand side */
     long long ld_f;
@@ -320,10 +324,12 @@ typedef struct {
  * cj_solve_batch -- solve n independent problems (any sizes, stencils, tolerances) together
  * with the mixed-precision CJM: FP32 inner cycles inside FP64 or double-FP64 defect
  * correction, every problem's residual test and stop rule evaluated on the device.  The
- * problems run as slots of one engine whose step (correct, defect, decide, sweep, export,
- * advance: six launches over persistent grids that read a device tile list) is captured
- * once in a CUDA graph and replayed until every slot has finished; a problem's arithmetic
- * does not depend on its batch-mates.  results[k] receives problem k's outcome (status per
+ * problems run as slots of one engine whose step (correct, defect, decide, eight sweep
+ * launches each followed by a counter advance, export, advance: launches over persistent
+ * grids that read a device tile list of 128-column tiles) is captured once in a CUDA graph
+ * and replayed until every slot has finished; finished problems leave the tile list; tile
+ * rows (16/32/64) and depth come from cj_autotune_engine's table for the size class when it
+ * has an entry.  A problem's arithmetic does not depend on its batch-mates.  results[k] receives problem k's outcome (status per
  * problem; seconds and launches are those of the whole batch).  Orders itself after the
  * work already on `stream` and makes `stream` wait for it; blocks until done.  Returns
  * CJ_OK, or CJ_ERR_TIMEOUT if a problem did not finish within its sweep budget's steps.

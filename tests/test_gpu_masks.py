@@ -137,3 +137,31 @@ def test_mask_argument_checks(cj, torch):
     z[0, 2, 3] = 0.0
     with pytest.raises(cj.CJError, match="centre"):
         cj.cj_plan_create_mask(6, 5, 9, z, 0.1, 1.9, 1e-6)
+
+
+def test_mask_host_solve_and_history_equal_the_device_solve(cj, torch):
+    """cj_solve_host (one copy in, one out) and cj_solve_history give the device solve's bits on
+    a mask plan, and the history ends at the reported residual."""
+    Nx, Ny = 31, 27
+    P = masks.polar(Nx, Ny, solution="harmonic")
+    G = _dev(torch, _ring(P, Nx, Ny))
+    kmin, kmax = _kappa(P, Nx, Ny)
+    outs = []
+    for how in ("device", "host", "history"):
+        with cj.Plan.mask(Nx, Ny, 5, _dev(torch, P["coef"]), 0.999 * kmin, 1.001 * kmax, 1e-9) as p:
+            cj.cj_set_boundary(p.handle, G)
+            if how == "host":
+                u = np.zeros((Ny, Nx))
+                res = cj.cj_solve_host(p.handle, np.ascontiguousarray(P["f"]), u)
+            else:
+                ud = torch.zeros((Ny, Nx), dtype=torch.float64, device="cuda")
+                if how == "device":
+                    res = cj.cj_solve(p.handle, _dev(torch, P["f"]), ud)
+                else:
+                    res = cj.cj_solve_history(p.handle, _dev(torch, P["f"]), ud)
+                    assert res["history"][-1] == res["rel_res_l2"]
+                u = ud.cpu().numpy()
+            outs.append((res["sweeps"], u))
+    for sweeps, u in outs[1:]:
+        assert sweeps == outs[0][0]
+        np.testing.assert_array_equal(u, outs[0][1])
