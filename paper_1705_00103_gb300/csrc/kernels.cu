@@ -199,7 +199,17 @@ inline dim3 copy_grid(const Grid &g) {
     return dim3(nbx, nby);
 }
 
-int g_num_sms = 0;
+// SMs of the current device, looked up once (thread-safe initialisation)
+int num_sms() {
+    static const int n = [] {
+        int dev = 0, sms = 0;
+        cudaGetDevice(&dev);
+        if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0)
+            sms = 152;
+        return sms;
+    }();
+    return n;
+}
 
 }  // namespace
 
@@ -215,18 +225,11 @@ Grid make_grid(int Nx, int Ny, int elem_bytes) {
 }
 
 March plan_march(int Nx, int Ny, int st, bool fp64) {
-    if (g_num_sms == 0) {
-        int dev = 0;
-        cudaGetDevice(&dev);
-        if (cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
-            g_num_sms <= 0)
-            g_num_sms = 152;
-    }
     // one wave of blocks: SMs x resident blocks, each block a 128-column strip of ty rows
     const int per_sm = fp64 ? 8 : 12;
     March m;
     m.nbx = (Nx + kBX - 1) / kBX;
-    long long target = (long long)g_num_sms * per_sm;
+    long long target = (long long)num_sms() * per_sm;
     long long nby = target / m.nbx;
     if (nby < 1) nby = 1;
     if (nby > Ny) nby = Ny;

@@ -28,16 +28,16 @@ __global__ void __launch_bounds__(kBX) sweep32_vec_kernel(const float *__restric
 
 template <int ST>
 cudaError_t launch_st(const Grid &g, const float *e, const float *r, float *out, float w, cudaStream_t s) {
-    static int resident = 0;  // blocks of this kernel resident on the device at once
-    if (resident == 0) {
+    // blocks of this kernel resident on the device at once (computed once, thread-safely)
+    static const int resident = [] {
         int dev = 0, sms = 152, per_sm = 1;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sweep32_vec_kernel<ST>, kBX, 0) != cudaSuccess ||
             per_sm < 1)
             per_sm = 1;
-        resident = sms * per_sm;
-    }
+        return sms * per_sm;
+    }();
     const int nbx = (g.Nx + 4 * kBX - 1) / (4 * kBX);
     long long nby = resident / nbx;
     if (nby < 1) nby = 1;

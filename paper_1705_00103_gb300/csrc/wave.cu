@@ -182,8 +182,7 @@ __global__ void __launch_bounds__(kWaveW) sweep_wave_kernel(const float *__restr
 // warm-up rows stay a minority).
 template <int ST, int K>
 int wave_rows(const Grid &g, int nstrips) {
-    static int resident = 0;
-    if (resident == 0) {
+    static const int resident = [] {  // computed once, thread-safely
         int dev = 0, sms = 152, per_sm = 1;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -191,8 +190,8 @@ int wave_rows(const Grid &g, int nstrips) {
                 cudaSuccess ||
             per_sm < 1)
             per_sm = 1;
-        resident = sms * per_sm;
-    }
+        return sms * per_sm;
+    }();
     constexpr int H = (ST == 17 ? 2 : 1) * K;
     int nby = resident / nstrips;
     if (nby < 1) nby = 1;
