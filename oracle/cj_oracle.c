@@ -386,14 +386,19 @@ void orc_sweep_f32(int st, int Nx, int Ny, const float *e, const float *r, float
         }
 }
 
+/* Dirichlet-data node access and residual (reading R15, defined with orc_solve_bc below). */
+static double at_bc(const double *u, const double *G, int Nx, int Ny, int i, int j);
+static double resid_at_bc(int st, const double *u, const double *G, int Nx, int Ny, int i, int j,
+                          double bk);
+
 /* FP64 defect r = b - L u, its square sum and max-abs, and the FP32 copy rt. */
-void orc_defect(int st, int Nx, int Ny, const double *u, const double *b, float *rt,
-                double *l2sq, double *linf) {
+static void defect_g(int st, int Nx, int Ny, const double *u, const double *G, const double *b,
+                     float *rt, double *l2sq, double *linf) {
     double s = 0.0, m = 0.0;
     for (int j = 1; j <= Ny; ++j)
         for (int i = 1; i <= Nx; ++i) {
             size_t k = (size_t)(j - 1) * Nx + (i - 1);
-            double r = resid_at(st, u, Nx, Ny, i, j, b[k]);
+            double r = G ? resid_at_bc(st, u, G, Nx, Ny, i, j, b[k]) : resid_at(st, u, Nx, Ny, i, j, b[k]);
             rt[k] = (float)(-r);
             s += r * r;
             if (fabs(r) > m) m = fabs(r);
@@ -402,13 +407,18 @@ void orc_defect(int st, int Nx, int Ny, const double *u, const double *b, float 
     *linf = m;
 }
 
+void orc_defect(int st, int Nx, int Ny, const double *u, const double *b, float *rt,
+                double *l2sq, double *linf) {
+    defect_g(st, Nx, Ny, u, NULL, b, rt, l2sq, linf);
+}
+
 /* Mixed-precision CJM (reading R10).  M_in is the inner cycle length (a power of two).
  * u: initial guess in, result out.  Returns the number of FP32 sweeps, or -1 on a bad
  * argument; *outer counts the defect-correction steps; *status as for orc_solve, with
  * an outer step in the role of a cycle. */
-long orc_solve_mixed(int st, int Nx, int Ny, const double *f, double tol, long M_in,
-                     long max_outer, double *u, double *rel_l2, double *rel_linf,
-                     long *outer, int *status) {
+static long solve_mixed_g(int st, int Nx, int Ny, const double *f, const double *G, double tol,
+                          long M_in, long max_outer, double *u, double *rel_l2, double *rel_linf,
+                          long *outer, int *status) {
     if (Nx < 1 || Ny < 1 || !(tol > 0.0 && tol < 1.0) || M_in < 1) return -1;
     size_t n = (size_t)Nx * (size_t)Ny;
     double kmin, kmax;
@@ -433,7 +443,7 @@ long orc_solve_mixed(int st, int Nx, int Ny, const double *f, double tol, long M
     double rl2 = 0.0, rinf = 0.0, prev = 0.0;
     for (;;) {
         double sq, mx, usq = 0.0;
-        orc_defect(st, Nx, Ny, u, b, rt, &sq, &mx);
+        defect_g(st, Nx, Ny, u, G, b, rt, &sq, &mx);
         for (size_t k = 0; k < n; ++k) usq += u[k] * u[k];
         rl2 = bn > 0.0 ? sqrt(sq) / bn : sqrt(sq);
         rinf = bmax > 0.0 ? mx / bmax : mx;
@@ -457,6 +467,21 @@ long orc_solve_mixed(int st, int Nx, int Ny, const double *f, double tol, long M
     *outer = out;
     *status = stat;
     return sweeps;
+}
+
+long orc_solve_mixed(int st, int Nx, int Ny, const double *f, double tol, long M_in,
+                     long max_outer, double *u, double *rel_l2, double *rel_linf,
+                     long *outer, int *status) {
+    return solve_mixed_g(st, Nx, Ny, f, NULL, tol, M_in, max_outer, u, rel_l2, rel_linf, outer, status);
+}
+
+/* Mixed precision with Dirichlet data G (R15 with R10): the FP64 defect takes the data ring,
+ * the FP32 inner cycle solves the homogeneous error equation (R6 boundary), and the correction
+ * changes the interior only. */
+long orc_solve_mixed_bc(int st, int Nx, int Ny, const double *f, const double *G, double tol,
+                        long M_in, long max_outer, double *u, double *rel_l2, double *rel_linf,
+                        long *outer, int *status) {
+    return solve_mixed_g(st, Nx, Ny, f, G, tol, M_in, max_outer, u, rel_l2, rel_linf, outer, status);
 }
 
 /* ---------------------------------------------------------------- double-FP64 outer form */
@@ -484,50 +509,55 @@ static void acc(double t, double *S, double *E) {
  *                   16 x (uSW, uSE, uNW, uNE), -(uSSWW, uSSEE, uNNWW, uNNEE),
  *                   -256uC, -32uC, -8uC, -4uC, -64bk, -8bk
  * then R = (S + (E + D * (L ul))) / D with L ul from resid_at. */
-static double resid_dd_at(int st, const double *uh, const double *ul, int Nx, int Ny, int i,
-                          int j, double bk) {
+/* u_hi at node (i, j): the data ring G when given, else the homogeneous boundary of R6. */
+static double nd(const double *uh, const double *G, int Nx, int Ny, int i, int j) {
+    return G ? at_bc(uh, G, Nx, Ny, i, j) : at(uh, Nx, Ny, i, j);
+}
+
+static double resid_dd_at(int st, const double *uh, const double *ul, const double *G,
+                          const double *G0, int Nx, int Ny, int i, int j, double bk) {
     double S = 0.0, E = 0.0, D;
-    double uC = at(uh, Nx, Ny, i, j);
+    double uC = nd(uh, G, Nx, Ny, i, j);
     if (st == 5) {
         D = 1.0;
-        acc(at(uh, Nx, Ny, i - 1, j), &S, &E);
-        acc(at(uh, Nx, Ny, i + 1, j), &S, &E);
-        acc(at(uh, Nx, Ny, i, j - 1), &S, &E);
-        acc(at(uh, Nx, Ny, i, j + 1), &S, &E);
+        acc(nd(uh, G, Nx, Ny, i - 1, j), &S, &E);
+        acc(nd(uh, G, Nx, Ny, i + 1, j), &S, &E);
+        acc(nd(uh, G, Nx, Ny, i, j - 1), &S, &E);
+        acc(nd(uh, G, Nx, Ny, i, j + 1), &S, &E);
         acc(-4.0 * uC, &S, &E);
         acc(-bk, &S, &E);
     } else if (st == 9) {
         D = 6.0;
-        acc(4.0 * at(uh, Nx, Ny, i - 1, j), &S, &E);
-        acc(4.0 * at(uh, Nx, Ny, i + 1, j), &S, &E);
-        acc(4.0 * at(uh, Nx, Ny, i, j - 1), &S, &E);
-        acc(4.0 * at(uh, Nx, Ny, i, j + 1), &S, &E);
-        acc(at(uh, Nx, Ny, i - 1, j - 1), &S, &E);
-        acc(at(uh, Nx, Ny, i + 1, j - 1), &S, &E);
-        acc(at(uh, Nx, Ny, i - 1, j + 1), &S, &E);
-        acc(at(uh, Nx, Ny, i + 1, j + 1), &S, &E);
+        acc(4.0 * nd(uh, G, Nx, Ny, i - 1, j), &S, &E);
+        acc(4.0 * nd(uh, G, Nx, Ny, i + 1, j), &S, &E);
+        acc(4.0 * nd(uh, G, Nx, Ny, i, j - 1), &S, &E);
+        acc(4.0 * nd(uh, G, Nx, Ny, i, j + 1), &S, &E);
+        acc(nd(uh, G, Nx, Ny, i - 1, j - 1), &S, &E);
+        acc(nd(uh, G, Nx, Ny, i + 1, j - 1), &S, &E);
+        acc(nd(uh, G, Nx, Ny, i - 1, j + 1), &S, &E);
+        acc(nd(uh, G, Nx, Ny, i + 1, j + 1), &S, &E);
         acc(-16.0 * uC, &S, &E);
         acc(-4.0 * uC, &S, &E);
         acc(-4.0 * bk, &S, &E);
         acc(-2.0 * bk, &S, &E);
     } else {
         D = 72.0;
-        acc(64.0 * at(uh, Nx, Ny, i - 1, j), &S, &E);
-        acc(64.0 * at(uh, Nx, Ny, i + 1, j), &S, &E);
-        acc(64.0 * at(uh, Nx, Ny, i, j - 1), &S, &E);
-        acc(64.0 * at(uh, Nx, Ny, i, j + 1), &S, &E);
-        acc(-4.0 * at(uh, Nx, Ny, i - 2, j), &S, &E);
-        acc(-4.0 * at(uh, Nx, Ny, i + 2, j), &S, &E);
-        acc(-4.0 * at(uh, Nx, Ny, i, j - 2), &S, &E);
-        acc(-4.0 * at(uh, Nx, Ny, i, j + 2), &S, &E);
-        acc(16.0 * at(uh, Nx, Ny, i - 1, j - 1), &S, &E);
-        acc(16.0 * at(uh, Nx, Ny, i + 1, j - 1), &S, &E);
-        acc(16.0 * at(uh, Nx, Ny, i - 1, j + 1), &S, &E);
-        acc(16.0 * at(uh, Nx, Ny, i + 1, j + 1), &S, &E);
-        acc(-at(uh, Nx, Ny, i - 2, j - 2), &S, &E);
-        acc(-at(uh, Nx, Ny, i + 2, j - 2), &S, &E);
-        acc(-at(uh, Nx, Ny, i - 2, j + 2), &S, &E);
-        acc(-at(uh, Nx, Ny, i + 2, j + 2), &S, &E);
+        acc(64.0 * nd(uh, G, Nx, Ny, i - 1, j), &S, &E);
+        acc(64.0 * nd(uh, G, Nx, Ny, i + 1, j), &S, &E);
+        acc(64.0 * nd(uh, G, Nx, Ny, i, j - 1), &S, &E);
+        acc(64.0 * nd(uh, G, Nx, Ny, i, j + 1), &S, &E);
+        acc(-4.0 * nd(uh, G, Nx, Ny, i - 2, j), &S, &E);
+        acc(-4.0 * nd(uh, G, Nx, Ny, i + 2, j), &S, &E);
+        acc(-4.0 * nd(uh, G, Nx, Ny, i, j - 2), &S, &E);
+        acc(-4.0 * nd(uh, G, Nx, Ny, i, j + 2), &S, &E);
+        acc(16.0 * nd(uh, G, Nx, Ny, i - 1, j - 1), &S, &E);
+        acc(16.0 * nd(uh, G, Nx, Ny, i + 1, j - 1), &S, &E);
+        acc(16.0 * nd(uh, G, Nx, Ny, i - 1, j + 1), &S, &E);
+        acc(16.0 * nd(uh, G, Nx, Ny, i + 1, j + 1), &S, &E);
+        acc(-nd(uh, G, Nx, Ny, i - 2, j - 2), &S, &E);
+        acc(-nd(uh, G, Nx, Ny, i + 2, j - 2), &S, &E);
+        acc(-nd(uh, G, Nx, Ny, i - 2, j + 2), &S, &E);
+        acc(-nd(uh, G, Nx, Ny, i + 2, j + 2), &S, &E);
         acc(-256.0 * uC, &S, &E);
         acc(-32.0 * uC, &S, &E);
         acc(-8.0 * uC, &S, &E);
@@ -535,33 +565,40 @@ static double resid_dd_at(int st, const double *uh, const double *ul, int Nx, in
         acc(-64.0 * bk, &S, &E);
         acc(-8.0 * bk, &S, &E);
     }
-    double Llo = resid_at(st, ul, Nx, Ny, i, j, 0.0);
+    /* u_lo has zero data: the zero ring G0 with data, else the R6 boundary */
+    double Llo = G ? resid_at_bc(st, ul, G0, Nx, Ny, i, j, 0.0) : resid_at(st, ul, Nx, Ny, i, j, 0.0);
     return (S + (E + D * Llo)) / D;
 }
 
 /* Residual R = L (uh + ul) - b of the double-FP64 form at every node (reading R11). */
-void orc_residual_dd(int st, int Nx, int Ny, const double *uh, const double *ul,
-                     const double *b, double *R) {
+static void residual_dd_g(int st, int Nx, int Ny, const double *uh, const double *ul, const double *G,
+                          const double *G0, const double *b, double *R) {
     for (int j = 1; j <= Ny; ++j)
         for (int i = 1; i <= Nx; ++i) {
             size_t k = (size_t)(j - 1) * Nx + (i - 1);
-            R[k] = resid_dd_at(st, uh, ul, Nx, Ny, i, j, b[k]);
+            R[k] = resid_dd_at(st, uh, ul, G, G0, Nx, Ny, i, j, b[k]);
         }
+}
+
+void orc_residual_dd(int st, int Nx, int Ny, const double *uh, const double *ul,
+                     const double *b, double *R) {
+    residual_dd_g(st, Nx, Ny, uh, ul, NULL, NULL, b, R);
 }
 
 /* Mixed-precision CJM with the double-FP64 outer loop (reading R11).  u: initial guess in
  * (taken as u_hi, u_lo = 0), u_hi + u_lo rounded to FP64 out; u_lo_out (may be NULL)
  * receives u_lo.  Returns the FP32 sweeps done or -1; *outer, *status as orc_solve_mixed;
  * the floor estimate uses 2^-106 in place of 2^-53. */
-long orc_solve_mixed_dd(int st, int Nx, int Ny, const double *f, double tol, long M_in,
-                        long max_outer, double *u, double *u_lo_out, double *rel_l2,
-                        double *rel_linf, long *outer, int *status) {
+static long solve_mixed_dd_g(int st, int Nx, int Ny, const double *f, const double *G, double tol,
+                             long M_in, long max_outer, double *u, double *u_lo_out, double *rel_l2,
+                             double *rel_linf, long *outer, int *status) {
     if (Nx < 1 || Ny < 1 || !(tol > 0.0 && tol < 1.0) || M_in < 1) return -1;
     size_t n = (size_t)Nx * (size_t)Ny;
+    double *G0 = G ? (double *)calloc((size_t)(Nx + 4) * (size_t)(Ny + 4), sizeof(double)) : NULL;
     double kmin, kmax;
     orc_kappa_bounds(st, Nx, Ny, &kmin, &kmax);
     double *w = (double *)malloc(sizeof(double) * (size_t)M_in);
-    if (orc_sweep_coeffs(st, kmin, kmax, M_in, w) != 0) { free(w); return -1; }
+    if (orc_sweep_coeffs(st, kmin, kmax, M_in, w) != 0) { free(w); free(G0); return -1; }
     float *w32 = (float *)malloc(sizeof(float) * (size_t)M_in);
     for (long s = 0; s < M_in; ++s) w32[s] = (float)w[s];
     double *b = (double *)malloc(sizeof(double) * n);
@@ -582,7 +619,7 @@ long orc_solve_mixed_dd(int st, int Nx, int Ny, const double *f, double tol, lon
     double rl2 = 0.0, rinf = 0.0, prev = 0.0;
     for (;;) {
         double sq = 0.0, mx = 0.0, usq = 0.0;
-        orc_residual_dd(st, Nx, Ny, u, ul, b, R);
+        residual_dd_g(st, Nx, Ny, u, ul, G, G0, b, R);
         for (size_t k = 0; k < n; ++k) {
             sq += R[k] * R[k];
             if (fabs(R[k]) > mx) mx = fabs(R[k]);
@@ -611,12 +648,28 @@ long orc_solve_mixed_dd(int st, int Nx, int Ny, const double *f, double tol, lon
         out += 1;
     }
     if (u_lo_out) memcpy(u_lo_out, ul, sizeof(double) * n);
-    free(w); free(w32); free(b); free(ul); free(R); free(rt); free(e); free(e2);
+    free(w); free(w32); free(b); free(ul); free(R); free(rt); free(e); free(e2); free(G0);
     *rel_l2 = rl2;
     *rel_linf = rinf;
     *outer = out;
     *status = stat;
     return sweeps;
+}
+
+long orc_solve_mixed_dd(int st, int Nx, int Ny, const double *f, double tol, long M_in,
+                        long max_outer, double *u, double *u_lo_out, double *rel_l2,
+                        double *rel_linf, long *outer, int *status) {
+    return solve_mixed_dd_g(st, Nx, Ny, f, NULL, tol, M_in, max_outer, u, u_lo_out, rel_l2, rel_linf,
+                            outer, status);
+}
+
+/* The double-FP64 form with Dirichlet data G (R15 with R11): u_hi's ghosts are the data, u_lo's
+ * are zero; the inner cycle and correction as in orc_solve_mixed_bc. */
+long orc_solve_mixed_dd_bc(int st, int Nx, int Ny, const double *f, const double *G, double tol,
+                           long M_in, long max_outer, double *u, double *u_lo_out, double *rel_l2,
+                           double *rel_linf, long *outer, int *status) {
+    return solve_mixed_dd_g(st, Nx, Ny, f, G, tol, M_in, max_outer, u, u_lo_out, rel_l2, rel_linf,
+                            outer, status);
 }
 
 /* ---------------------------------------------------------------- non-homogeneous Dirichlet */

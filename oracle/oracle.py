@@ -107,6 +107,12 @@ def lib():
         L.orc_solve_mixed_dd.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, _dp, ctypes.c_double,
                                          ctypes.c_long, ctypes.c_long, _dp, _dp, _dp, _dp, _lp, _ip]
         L.orc_solve_mixed_dd.restype = ctypes.c_long
+        L.orc_solve_mixed_bc.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, _dp, _dp, ctypes.c_double,
+                                         ctypes.c_long, ctypes.c_long, _dp, _dp, _dp, _lp, _ip]
+        L.orc_solve_mixed_bc.restype = ctypes.c_long
+        L.orc_solve_mixed_dd_bc.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, _dp, _dp, ctypes.c_double,
+                                            ctypes.c_long, ctypes.c_long, _dp, _dp, _dp, _dp, _lp, _ip]
+        L.orc_solve_mixed_dd_bc.restype = ctypes.c_long
         _lib = L
     return _lib
 
@@ -247,15 +253,20 @@ def defect(st: int, u: np.ndarray, b: np.ndarray):
 
 
 def solve_mixed(st: int, f: np.ndarray, tol: float, M_in: int, u0: np.ndarray | None = None,
-                max_outer: int = 1000) -> dict:
-    """FP32-inner / FP64-outer defect-correction CJM."""
+                max_outer: int = 1000, G: np.ndarray | None = None) -> dict:
+    """FP32-inner / FP64-outer defect-correction CJM (with Dirichlet data G, see ghost_ring)."""
     f = _grid(f)
     u = np.zeros_like(f) if u0 is None else _grid(u0).copy()
     rl2, rinf = ctypes.c_double(), ctypes.c_double()
     outer, stat = ctypes.c_long(), ctypes.c_int()
-    n = lib().orc_solve_mixed(st, f.shape[1], f.shape[0], _d(f), tol, M_in, max_outer, _d(u),
-                              ctypes.byref(rl2), ctypes.byref(rinf), ctypes.byref(outer),
-                              ctypes.byref(stat))
+    if G is None:
+        n = lib().orc_solve_mixed(st, f.shape[1], f.shape[0], _d(f), tol, M_in, max_outer, _d(u),
+                                  ctypes.byref(rl2), ctypes.byref(rinf), ctypes.byref(outer),
+                                  ctypes.byref(stat))
+    else:
+        n = lib().orc_solve_mixed_bc(st, f.shape[1], f.shape[0], _d(f), _d(_grid(G)), tol, M_in, max_outer,
+                                     _d(u), ctypes.byref(rl2), ctypes.byref(rinf), ctypes.byref(outer),
+                                     ctypes.byref(stat))
     if n < 0:
         raise ValueError("bad argument")
     return dict(u=u, sweeps=n, outer=outer.value, rel_l2=rl2.value, rel_linf=rinf.value,
@@ -271,17 +282,22 @@ def residual_dd(st: int, uh: np.ndarray, ul: np.ndarray, b: np.ndarray) -> np.nd
 
 
 def solve_mixed_dd(st: int, f: np.ndarray, tol: float, M_in: int, u0: np.ndarray | None = None,
-                   max_outer: int = 1000) -> dict:
-    """FP32-inner CJM cycles inside a double-FP64 defect-correction loop; returns
-    u = fl(u_hi + u_lo) and u_lo."""
+                   max_outer: int = 1000, G: np.ndarray | None = None) -> dict:
+    """FP32-inner CJM cycles inside a double-FP64 defect-correction loop (with Dirichlet data
+    G, see ghost_ring); returns u = fl(u_hi + u_lo) and u_lo."""
     f = _grid(f)
     u = np.zeros_like(f) if u0 is None else _grid(u0).copy()
     ulo = np.zeros_like(f)
     rl2, rinf = ctypes.c_double(), ctypes.c_double()
     outer, stat = ctypes.c_long(), ctypes.c_int()
-    n = lib().orc_solve_mixed_dd(st, f.shape[1], f.shape[0], _d(f), tol, M_in, max_outer, _d(u),
-                                 _d(ulo), ctypes.byref(rl2), ctypes.byref(rinf),
-                                 ctypes.byref(outer), ctypes.byref(stat))
+    if G is None:
+        n = lib().orc_solve_mixed_dd(st, f.shape[1], f.shape[0], _d(f), tol, M_in, max_outer, _d(u),
+                                     _d(ulo), ctypes.byref(rl2), ctypes.byref(rinf),
+                                     ctypes.byref(outer), ctypes.byref(stat))
+    else:
+        n = lib().orc_solve_mixed_dd_bc(st, f.shape[1], f.shape[0], _d(f), _d(_grid(G)), tol, M_in,
+                                        max_outer, _d(u), _d(ulo), ctypes.byref(rl2), ctypes.byref(rinf),
+                                        ctypes.byref(outer), ctypes.byref(stat))
     if n < 0:
         raise ValueError("bad argument")
     return dict(u=u, u_lo=ulo, sweeps=n, outer=outer.value, rel_l2=rl2.value, rel_linf=rinf.value,

@@ -781,3 +781,46 @@ def test_jacobi_budget_and_argument_checks():
     assert out["status"] == "max_sweeps" and out["sweeps"] <= 100
     with pytest.raises(ValueError):
         orc.solve_jacobi(5, f, 0.0)
+
+
+# ----------------------------------------------------------------- mixed precision with Dirichlet data
+
+@pytest.mark.parametrize("st", STENCILS)
+@pytest.mark.parametrize("dd", [False, True])
+def test_mixed_with_data_reaches_the_dense_solution(st, dd):
+    """FP32 inner cycles in FP64 (or double-FP64) defect correction with Dirichlet data converge
+    to the dense solution of the zero-ghost system with the data moved to the right-hand side."""
+    Nx, Ny = 11, 9
+    f, _, g = workloads.paper_problem(Nx, Ny)
+    G = orc.ghost_ring(Nx, Ny, g)
+    solve = orc.solve_mixed_dd if dd else orc.solve_mixed
+    out = solve(st, f, 1e-12, 16, G=G, max_outer=200)
+    assert out["status"] in ("converged", "floor") and out["rel_l2"] < 1e-11
+    h = 1.0 / (Nx + 1)
+    rhs = (h * h * f - _ghost_term(st, Nx, Ny, G)).ravel()
+    ref = np.linalg.solve(_dense_zero_ghost(st, Nx, Ny), rhs).reshape(Ny, Nx)
+    np.testing.assert_allclose(out["u"], ref, rtol=0, atol=1e-10 * np.abs(ref).max())
+
+
+def test_mixed_with_zero_data_equals_homogeneous_for_radius_one():
+    f = workloads.smooth_random_rhs(20, 17, 3)
+    G = np.zeros((21, 24))
+    for st in (5, 9):
+        for solve in (orc.solve_mixed, orc.solve_mixed_dd):
+            a = solve(st, f, 1e-10, 32, G=G)
+            b = solve(st, f, 1e-10, 32)
+            assert a["sweeps"] == b["sweeps"] and a["outer"] == b["outer"]
+            np.testing.assert_array_equal(a["u"], b["u"])
+
+
+def test_mixed_dd_with_data_meets_the_paper_problem_to_its_discretisation_error():
+    N, st = 63, 17
+    f, ue, g = workloads.paper_problem(N, N)
+    G = orc.ghost_ring(N, N, g)
+    out = orc.solve_mixed_dd(st, f, 1e-12, 64, G=G, max_outer=300)
+    ref = orc.solve_bc(st, f, G, 1e-13)
+    assert out["status"] in ("converged", "floor")
+    # both are the discrete solution: their real errors agree to a few percent of it
+    e_mixed = np.abs(out["u"] - ue).max()
+    e_fp64 = np.abs(ref["u"] - ue).max()
+    assert e_mixed == pytest.approx(e_fp64, rel=1e-2)
