@@ -421,7 +421,7 @@ def run_highorder(args):
     print(json.dumps(out), flush=True)
 
 
-def paper_solve(cj, torch, N, st, tol, stream, err_goal=None, check_every=0, method=0):
+def paper_solve(cj, torch, N, st, tol, stream, err_goal=None, check_every=0, method=0, precision=0):
     """One solve of the paper's test problem (Sec. 3.3) with its Dirichlet data: to the
     relative residual tol, or, with err_goal, to that real error (Sec. 3.4); method 1 is
     classical Jacobi."""
@@ -429,7 +429,7 @@ def paper_solve(cj, torch, N, st, tol, stream, err_goal=None, check_every=0, met
     f, ue, g = workloads.paper_problem(N, N)
     fd, ued, Gd = f_to(torch, f), f_to(torch, ue), f_to(torch, cj.dirichlet_ring(N, N, g))
     u = torch.zeros_like(fd)
-    with cj.Plan(N, N, st, tol, bc=cj.CJ_BC_DIRICHLET, method=method) as p:
+    with cj.Plan(N, N, st, tol, bc=cj.CJ_BC_DIRICHLET, method=method, precision=precision) as p:
         cj.cj_set_boundary(p.handle, Gd, stream)
         M = p.info()["M"]
         every = max(1, M // 64) if check_every else 0
@@ -529,6 +529,13 @@ def run_paper(args):
         return d
 
     t3 = [brief(r, k, st, N) for (k, st, N, _, _), r in zip(runs, res) if k == "table1"]
+    # the same problem by FP32 inner cycles in double-FP64 defect correction, to 1e-10
+    mixed = []
+    for st, N in ((5, 2048), (17, 1024), (17, 2048)):
+        r = paper_solve(cj, torch, N, st, 1e-10, stream, precision=cj.CJ_FP32_INNER_DD)
+        mixed.append({"stencil": st, "N": N, "fp32_sweeps": r["sweeps"], "outer_steps": r["cycles"],
+                      "time_s": r["time_s"], "status": cj.cj_status_string(r["rc"]),
+                      "rel_res_l2": r["rel_res_l2"], "real_error": r["real_error_final"]})
     if not args.no_jacobi:
         table1_ratios(cj, torch, stream, t3, N3, tol3)
     f4 = [brief(r, k, st, N) for (k, st, N, _, _), r in zip(runs, res) if k == "fig4"]
@@ -540,7 +547,7 @@ def run_paper(args):
                       "table1": "N = 1024, stencils 5/9/17, tol = N^-2",
                       "fig4_right": "17-point N = 128 vs 5-point N = 2048, real error goal 1e-8",
                       "l2_flush": "none: the 2048^2 arrays (34 MB) fit in L2; the timing is of whole solves"},
-           "table1": t3, "fig4_right": f4,
+           "table1": t3, "fig4_right": f4, "mixed_dd_to_1e-10": mixed,
            "fig4_sweep_ratio_5pt_over_17pt": f4[1]["sweeps"] / max(1, f4[0]["sweeps"]),
            "fig4_time_ratio_5pt_over_17pt": f4[1]["time_s"] / max(1e-12, f4[0]["time_s"]),
            "clocks": clk}

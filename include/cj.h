@@ -55,7 +55,9 @@ typedef enum { CJ_ST5 = 5, CJ_ST9 = 9, CJ_ST17 = 17 } cj_stencil;
 typedef enum {
     CJ_BC_DIRICHLET0 = 0,  /* homogeneous Dirichlet; 17-point: odd reflection for the 2nd ring */
     CJ_BC_DIRICHLET = 1    /* Dirichlet data given at both rings around the interior (the paper's
-                              test problem, Sec. 3.3), set by cj_set_boundary; CJ_FP64 only */
+                              test problem, Sec. 3.3), set by cj_set_boundary; in the mixed
+                              precisions the FP64 defect reads the data and the FP32 inner
+                              cycles solve the homogeneous error equation */
 } cj_bc;
 
 typedef enum {

@@ -75,7 +75,7 @@ cudaError_t launch_defect_dd(const cj_plan *p, const double *uh, const double *u
 
 cudaError_t launch_correct_dd(const cj_plan *p, double *uh, double *ul, const float *e,
                               cudaStream_t s) {
-    if (p->r == 2)
+    if (p->r == 2 && p->bc == CJ_BC_DIRICHLET0)  // with Dirichlet data the ring stays as set
         correct_dd_kernel<2><<<node_grid(p->g64), kBX, 0, s>>>(uh, ul, e, p->g64, p->g32);
     else
         correct_dd_kernel<1><<<node_grid(p->g64), kBX, 0, s>>>(uh, ul, e, p->g64, p->g32);

@@ -313,7 +313,7 @@ cudaError_t launch_export(const cj_plan *p, const double *u_pad, double *u, long
 }
 
 cudaError_t launch_correct(const cj_plan *p, double *u_pad, const float *e, cudaStream_t s) {
-    if (p->r == 2)
+    if (p->r == 2 && p->bc == CJ_BC_DIRICHLET0)  // with Dirichlet data the ring stays as set
         correct_kernel<2><<<copy_grid(p->g64), kBX, 0, s>>>(u_pad, e, p->g64, p->g32, 1.0);
     else
         correct_kernel<1><<<copy_grid(p->g64), kBX, 0, s>>>(u_pad, e, p->g64, p->g32, 1.0);

@@ -508,7 +508,6 @@ cj_status cj_plan_create(int Nx, int Ny, cj_stencil st, cj_bc bc, double tol,
     if (o.inner_cycle != 0 && !is_pow2(o.inner_cycle)) return CJ_ERR_INVALID_ARG;
     if (o.max_sweeps < 0) return CJ_ERR_INVALID_ARG;
     if (o.temporal_depth < 0 || o.temporal_depth > kTbMaxDepth) return CJ_ERR_INVALID_ARG;
-    if (bc == CJ_BC_DIRICHLET && o.precision != CJ_FP64) return CJ_ERR_INVALID_ARG;
     if (o.method != CJ_CJM && o.method != CJ_JACOBI) return CJ_ERR_INVALID_ARG;
     if (o.method == CJ_JACOBI && o.precision != CJ_FP64) return CJ_ERR_INVALID_ARG;
     if (o.launch < 0 || o.launch > 2) return CJ_ERR_INVALID_ARG;

@@ -425,8 +425,6 @@ def test_dirichlet_data_solve_matches_oracle(cj, torch, st, N, tol):
 
 
 def test_dirichlet_data_argument_checks(cj, torch):
-    with pytest.raises(cj.CJError):
-        cj.cj_plan_create(16, 16, 9, 1e-8, bc=cj.CJ_BC_DIRICHLET, precision=cj.CJ_FP32_INNER)
     g = torch.zeros((20, 20), dtype=torch.float64, device="cuda")
     with cj.Plan(16, 16, 9, 1e-8) as p:
         with pytest.raises(cj.CJError):
@@ -582,3 +580,26 @@ def test_largest_side_sweeps_bit_exact(cj, torch, Nx, Ny):
         cj.cj_sweeps_f32(p.handle, torch.from_numpy(r).cuda(), ed, 0, 2)
     ref32 = orc.sweep_f32(st, orc.sweep_f32(st, e0, r, w32[0]), r, w32[1])
     np.testing.assert_array_equal(ed.cpu().numpy(), ref32)
+
+
+@pytest.mark.parametrize("st", STENCILS)
+@pytest.mark.parametrize("prec", [1, 2])
+@pytest.mark.parametrize("Nx,Ny,M_in", [(40, 33, 32), (130, 70, 64)])
+def test_mixed_with_dirichlet_data_matches_oracle(cj, torch, st, prec, Nx, Ny, M_in):
+    """FP32 inner cycles in FP64 / double-FP64 defect correction on the paper's problem with its
+    data ring: every bit of u (and u_lo) and the sweep count equal the oracle's."""
+    f, _, g = workloads.paper_problem(Nx, Ny)
+    G, Gd = _ring(torch, Nx, Ny, g)
+    tol = 1e-10
+    ref = (orc.solve_mixed_dd if prec == 2 else orc.solve_mixed)(st, f, tol, M_in, G=G, max_outer=64)
+    with cj.Plan(Nx, Ny, st, tol, precision=prec, inner_cycle=M_in, bc=cj.CJ_BC_DIRICHLET) as p:
+        cj.cj_set_boundary(p.handle, Gd)
+        ud = torch.zeros((Ny, Nx), dtype=torch.float64, device="cuda")
+        res = cj.cj_solve(p.handle, dev(torch, f), ud)
+        if prec == 2:
+            lo = torch.zeros_like(ud)
+            cj.cj_solution_lo(p.handle, lo)
+            np.testing.assert_array_equal(lo.cpu().numpy(), ref["u_lo"])
+    assert res["sweeps"] == ref["sweeps"] and res["cycles"] == ref["outer"]
+    assert {0: "converged", 1: "floor"}[res["status"]] == ref["status"]
+    np.testing.assert_array_equal(ud.cpu().numpy(), ref["u"])
