@@ -78,3 +78,32 @@ def test_dirichlet_ring_layout_matches_the_oracle():
     for Nx, Ny in [(1, 1), (5, 3), (17, 9)]:
         _, _, g = workloads.paper_problem(Nx, Ny)
         np.testing.assert_array_equal(cj.dirichlet_ring(Nx, Ny, g), orc.ghost_ring(Nx, Ny, g))
+
+
+def test_batch_server_and_mask_arguments_rejected_without_gpu(lib):
+    """Entry points check their arguments before any CUDA call: no GPU is needed to see the
+    rejections."""
+    I = ctypes.c_int
+    lib.cj_solve_batch.restype = I
+    assert lib.cj_solve_batch(None, 0, None, None) == -1
+    lib.cj_server_create.restype = I
+    out = ctypes.c_void_p()
+    assert lib.cj_server_create(ctypes.c_size_t(0), 4, ctypes.byref(out)) == -1
+    assert lib.cj_server_create(ctypes.c_size_t(1 << 30), 0, ctypes.byref(out)) == -1
+    lib.cj_submit.restype = I
+    t = ctypes.c_uint64()
+    assert lib.cj_submit(None, 8, 8, 5, ctypes.c_double(1e-6), None, ctypes.byref(t)) == -1
+    lib.cj_poll.restype = I
+    assert lib.cj_poll(None, ctypes.c_uint64(1), None, None) == -1
+    lib.cj_plan_create_mask.restype = I
+    h = ctypes.c_void_p()
+    assert lib.cj_plan_create_mask(8, 8, None, ctypes.c_double(1e-6), None, ctypes.byref(h)) == -1
+    lib.cj_autotune_engine.restype = I
+    assert lib.cj_autotune_engine(0, 8, 5, None, None, None) == -1
+    assert lib.cj_autotune_engine(8, 8, 7, None, None, None) == -1
+    lib.cj_set_boundary.restype = I
+    assert lib.cj_set_boundary(None, None, ctypes.c_longlong(0), None) == -1
+    lib.cj_solve_to_error.restype = I
+    assert lib.cj_solve_to_error(None, None, ctypes.c_longlong(0), None, ctypes.c_longlong(0), None,
+                                 ctypes.c_longlong(0), ctypes.c_double(0.0), ctypes.c_longlong(0), None,
+                                 None, None, None, 0, None) == -1
