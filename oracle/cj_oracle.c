@@ -416,9 +416,39 @@ void orc_defect(int st, int Nx, int Ny, const double *u, const double *b, float 
  * u: initial guess in, result out.  Returns the number of FP32 sweeps, or -1 on a bad
  * argument; *outer counts the defect-correction steps; *status as for orc_solve, with
  * an outer step in the role of a cycle. */
+/* Real-error stop of a defect-correction solve (R16 with R10/R11): u_hi - u_exact tested at
+ * every outer step, after the defect; NULL = the residual stop of R8. */
+typedef struct {
+    const double *ue;
+    double goal;
+    double *hist;
+    long cap, count;
+    double err;
+} err_stop;
+
+double orc_real_error(int Nx, int Ny, const double *u, const double *u_exact);
+
+/* The mixed loops' stop test at an outer step: with es, the real error first (recorded in
+ * es->hist as (sweeps, E)), then the floor part of R8; else R8 with tol. */
+static int mixed_stop(err_stop *es, int Nx, int Ny, const double *u, long sweeps, double rl2, double fl,
+                      double prev, long out, double tol, int *stall) {
+    if (!es) return stop_rule(rl2, fl, prev, out, tol, 2, stall);
+    double E = orc_real_error(Nx, Ny, u, es->ue);
+    if (es->count < es->cap) {
+        es->hist[2 * es->count] = (double)sweeps;
+        es->hist[2 * es->count + 1] = E;
+    }
+    es->count += 1;
+    es->err = E;
+    if (!(E == E) || E > 1e300) return ORC_DIVERGED;
+    if (E <= es->goal) return ORC_CONVERGED;
+    int st = stop_rule(rl2, fl, prev, out, 0.0, 2, stall);
+    return st == ORC_CONVERGED ? ORC_FLOOR : st;
+}
+
 static long solve_mixed_g(int st, int Nx, int Ny, const double *f, const double *G, double tol,
                           long M_in, long max_outer, double *u, double *rel_l2, double *rel_linf,
-                          long *outer, int *status) {
+                          long *outer, int *status, err_stop *es) {
     if (Nx < 1 || Ny < 1 || !(tol > 0.0 && tol < 1.0) || M_in < 1) return -1;
     size_t n = (size_t)Nx * (size_t)Ny;
     double kmin, kmax;
@@ -448,7 +478,7 @@ static long solve_mixed_g(int st, int Nx, int Ny, const double *f, const double 
         rl2 = bn > 0.0 ? sqrt(sq) / bn : sqrt(sq);
         rinf = bmax > 0.0 ? mx / bmax : mx;
         double fl = bn > 0.0 ? eps * S * sqrt(usq) / bn : eps * S * sqrt(usq);
-        stat = stop_rule(rl2, fl, prev, out, tol, 2, &stall);
+        stat = mixed_stop(es, Nx, Ny, u, sweeps, rl2, fl, prev, out, tol, &stall);
         if (stat >= 0) break;
         if (out >= max_outer) { stat = ORC_MAX_SWEEPS; break; }
         prev = rl2;
@@ -472,7 +502,7 @@ static long solve_mixed_g(int st, int Nx, int Ny, const double *f, const double 
 long orc_solve_mixed(int st, int Nx, int Ny, const double *f, double tol, long M_in,
                      long max_outer, double *u, double *rel_l2, double *rel_linf,
                      long *outer, int *status) {
-    return solve_mixed_g(st, Nx, Ny, f, NULL, tol, M_in, max_outer, u, rel_l2, rel_linf, outer, status);
+    return solve_mixed_g(st, Nx, Ny, f, NULL, tol, M_in, max_outer, u, rel_l2, rel_linf, outer, status, NULL);
 }
 
 /* Mixed precision with Dirichlet data G (R15 with R10): the FP64 defect takes the data ring,
@@ -481,7 +511,7 @@ long orc_solve_mixed(int st, int Nx, int Ny, const double *f, double tol, long M
 long orc_solve_mixed_bc(int st, int Nx, int Ny, const double *f, const double *G, double tol,
                         long M_in, long max_outer, double *u, double *rel_l2, double *rel_linf,
                         long *outer, int *status) {
-    return solve_mixed_g(st, Nx, Ny, f, G, tol, M_in, max_outer, u, rel_l2, rel_linf, outer, status);
+    return solve_mixed_g(st, Nx, Ny, f, G, tol, M_in, max_outer, u, rel_l2, rel_linf, outer, status, NULL);
 }
 
 /* ---------------------------------------------------------------- double-FP64 outer form */
@@ -591,7 +621,7 @@ void orc_residual_dd(int st, int Nx, int Ny, const double *uh, const double *ul,
  * the floor estimate uses 2^-106 in place of 2^-53. */
 static long solve_mixed_dd_g(int st, int Nx, int Ny, const double *f, const double *G, double tol,
                              long M_in, long max_outer, double *u, double *u_lo_out, double *rel_l2,
-                             double *rel_linf, long *outer, int *status) {
+                             double *rel_linf, long *outer, int *status, err_stop *es) {
     if (Nx < 1 || Ny < 1 || !(tol > 0.0 && tol < 1.0) || M_in < 1) return -1;
     size_t n = (size_t)Nx * (size_t)Ny;
     double *G0 = G ? (double *)calloc((size_t)(Nx + 4) * (size_t)(Ny + 4), sizeof(double)) : NULL;
@@ -629,7 +659,7 @@ static long solve_mixed_dd_g(int st, int Nx, int Ny, const double *f, const doub
         rl2 = bn > 0.0 ? sqrt(sq) / bn : sqrt(sq);
         rinf = bmax > 0.0 ? mx / bmax : mx;
         double fl = bn > 0.0 ? eps2 * S * sqrt(usq) / bn : eps2 * S * sqrt(usq);
-        stat = stop_rule(rl2, fl, prev, out, tol, 2, &stall);
+        stat = mixed_stop(es, Nx, Ny, u, sweeps, rl2, fl, prev, out, tol, &stall);
         if (stat >= 0) break;
         if (out >= max_outer) { stat = ORC_MAX_SWEEPS; break; }
         prev = rl2;
@@ -660,7 +690,7 @@ long orc_solve_mixed_dd(int st, int Nx, int Ny, const double *f, double tol, lon
                         long max_outer, double *u, double *u_lo_out, double *rel_l2,
                         double *rel_linf, long *outer, int *status) {
     return solve_mixed_dd_g(st, Nx, Ny, f, NULL, tol, M_in, max_outer, u, u_lo_out, rel_l2, rel_linf,
-                            outer, status);
+                            outer, status, NULL);
 }
 
 /* The double-FP64 form with Dirichlet data G (R15 with R11): u_hi's ghosts are the data, u_lo's
@@ -669,7 +699,7 @@ long orc_solve_mixed_dd_bc(int st, int Nx, int Ny, const double *f, const double
                            long M_in, long max_outer, double *u, double *u_lo_out, double *rel_l2,
                            double *rel_linf, long *outer, int *status) {
     return solve_mixed_dd_g(st, Nx, Ny, f, G, tol, M_in, max_outer, u, u_lo_out, rel_l2, rel_linf,
-                            outer, status);
+                            outer, status, NULL);
 }
 
 /* ---------------------------------------------------------------- non-homogeneous Dirichlet */
@@ -1108,4 +1138,23 @@ long orc_solve_mask(int pat, int Nx, int Ny, const double *f, const double *coef
     *cycles = cyc;
     *status = stat;
     return sweeps;
+}
+
+/* Defect correction (R10, or R11 with dd) stopped by the real error (R16): u_hi - u_exact in the
+ * infinity norm, tested at every outer step after the defect, stops the solve at <= err_goal;
+ * the residual's floor and stall parts of R8 still end it ("floor").  G: Dirichlet data (R15) or
+ * NULL.  hist[2k], hist[2k+1] = FP32 sweeps done and E at the k-th test (cap tests; *count = all). */
+long orc_solve_mixed_to_error(int st, int Nx, int Ny, const double *f, const double *G,
+                              const double *u_exact, double err_goal, long M_in, int dd, long max_outer,
+                              double *u, double *u_lo_out, double *hist, long cap, long *count,
+                              double *err, double *rel_l2, long *outer, int *status) {
+    if (!(err_goal >= 0.0)) return -1;
+    err_stop es = {u_exact, err_goal, hist, cap, 0, 0.0};
+    double rinf;
+    long n = dd ? solve_mixed_dd_g(st, Nx, Ny, f, G, 0.5, M_in, max_outer, u, u_lo_out, rel_l2, &rinf, outer,
+                                   status, &es)
+                : solve_mixed_g(st, Nx, Ny, f, G, 0.5, M_in, max_outer, u, rel_l2, &rinf, outer, status, &es);
+    *count = es.count;
+    *err = es.err;
+    return n;
 }

@@ -96,6 +96,11 @@ def lib():
                                      ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_int, _dp,
                                      ctypes.c_long, _dp, _dp, _dp, _lp, ctypes.POINTER(ctypes.c_int)]
         L.orc_solve_mask.restype = ctypes.c_long
+        L.orc_solve_mixed_to_error.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, _dp, _dp, _dp,
+                                               ctypes.c_double, ctypes.c_long, ctypes.c_int, ctypes.c_long,
+                                               _dp, _dp, _dp, ctypes.c_long, _lp, _dp, _dp, _lp,
+                                               ctypes.POINTER(ctypes.c_int)]
+        L.orc_solve_mixed_to_error.restype = ctypes.c_long
         L.orc_real_error.argtypes = [ctypes.c_int, ctypes.c_int, _dp, _dp]
         L.orc_real_error.restype = ctypes.c_double
         L.orc_solve_to_error.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, _dp, _dp, _dp,
@@ -471,3 +476,24 @@ def solve_mask(pat: int, f: np.ndarray, coef: np.ndarray, kmin: float, kmax: flo
         raise ValueError("bad argument")
     return dict(u=u, sweeps=n, cycles=cyc.value, rel_l2=rl2.value, rel_linf=rinf.value,
                 status=STATUS[stat.value], converged=stat.value == 0)
+
+
+def solve_mixed_to_error(st: int, f: np.ndarray, u_exact: np.ndarray, err_goal: float, M_in: int,
+                         dd: bool = False, G: np.ndarray | None = None, max_outer: int = 1000,
+                         cap: int = 4096) -> dict:
+    """Defect correction (FP32 inner cycles, FP64 or double-FP64 outer) stopped by the real error
+    at the outer steps (orc_solve_mixed_to_error)."""
+    f, ue = _grid(f), _grid(u_exact)
+    u, ulo = np.zeros_like(f), np.zeros_like(f)
+    hist = np.zeros(2 * cap)
+    cnt, outer, stat = ctypes.c_long(), ctypes.c_long(), ctypes.c_int()
+    err, rl2 = ctypes.c_double(), ctypes.c_double()
+    n = lib().orc_solve_mixed_to_error(st, f.shape[1], f.shape[0], _d(f), None if G is None else _d(_grid(G)),
+                                       _d(ue), err_goal, M_in, int(dd), max_outer, _d(u), _d(ulo), _d(hist),
+                                       cap, ctypes.byref(cnt), ctypes.byref(err), ctypes.byref(rl2),
+                                       ctypes.byref(outer), ctypes.byref(stat))
+    if n < 0:
+        raise ValueError("bad argument")
+    k = min(cnt.value, cap)
+    return dict(u=u, u_lo=ulo, sweeps=n, outer=outer.value, err=err.value, rel_l2=rl2.value,
+                status=STATUS[stat.value], tests=cnt.value, history=hist[:2 * k].reshape(k, 2).copy())

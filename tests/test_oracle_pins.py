@@ -824,3 +824,67 @@ def test_mixed_dd_with_data_meets_the_paper_problem_to_its_discretisation_error(
     e_mixed = np.abs(out["u"] - ue).max()
     e_fp64 = np.abs(ref["u"] - ue).max()
     assert e_mixed == pytest.approx(e_fp64, rel=1e-2)
+
+
+# ----------------------------------------------------------------- real-error stop of defect correction
+
+def _mixed_to_error_by_hand(st, f, ue, goal, M_in):
+    """The FP64-outer defect correction stopped by the real error, written out with the pinned
+    defect and FP32 sweep primitives (homogeneous boundary)."""
+    Ny, Nx = f.shape
+    kmin, kmax = orc.kappa_bounds(st, Nx, Ny)
+    w32 = orc.sweep_coeffs(st, kmin, kmax, M_in).astype(np.float32)
+    b = orc.scale_rhs(f)
+    u = np.zeros_like(f)
+    hist, sweeps = [], 0
+    while True:
+        rt, _, _ = orc.defect(st, u, b)
+        E = float(np.max(np.abs(u - ue)))
+        hist.append((sweeps, E))
+        if E <= goal:
+            return u, sweeps, hist
+        e = np.zeros(f.shape, np.float32)
+        for k in range(M_in):
+            e = orc.sweep_f32(st, e, rt, w32[k])
+        u = u + e.astype(np.float64)
+        sweeps += M_in
+
+
+@pytest.mark.parametrize("st", STENCILS)
+def test_mixed_to_error_follows_its_definition(st):
+    N, M_in = 23, 32
+    f, ue = workloads.manufactured_rhs(N, N), workloads.manufactured_solution(N, N)
+    disc = orc.real_error(orc.solve(st, f, 1e-13)["u"], ue)
+    goal = disc * 1.05 + 1e-9
+    u, sweeps, hist = _mixed_to_error_by_hand(st, f, ue, goal, M_in)
+    out = orc.solve_mixed_to_error(st, f, ue, goal, M_in)
+    assert out["status"] == "converged" and out["sweeps"] == sweeps
+    np.testing.assert_array_equal(out["history"], np.array(hist))
+    np.testing.assert_array_equal(out["u"], u)
+
+
+@pytest.mark.parametrize("st", STENCILS)
+def test_mixed_dd_to_error_stops_at_the_iterate_of_the_plain_loop(st):
+    """With data and the double-FP64 outer steps: the real-error stop ends at the same iterate as
+    the residual-stopped loop run for that many outer steps, with its real error at most the goal."""
+    N, M_in = 31, 64
+    f, ue, g = workloads.paper_problem(N, N)
+    G = orc.ghost_ring(N, N, g)
+    disc = orc.real_error(orc.solve_bc(st, f, G, 1e-13)["u"], ue)
+    goal = disc * 1.5 + 1e-12
+    out = orc.solve_mixed_to_error(st, f, ue, goal, M_in, dd=True, G=G)
+    assert out["status"] == "converged" and out["err"] <= goal
+    assert out["history"][-1, 1] == out["err"] == orc.real_error(out["u"], ue)
+    ref = orc.solve_mixed_dd(st, f, 1e-15, M_in, G=G, max_outer=out["outer"])
+    np.testing.assert_array_equal(out["u"], ref["u"])
+    np.testing.assert_array_equal(out["u_lo"], ref["u_lo"])
+
+
+def test_mixed_to_error_goal_below_discretisation_ends_at_the_floor():
+    N, st = 23, 9
+    f, ue, g = workloads.paper_problem(N, N)
+    G = orc.ghost_ring(N, N, g)
+    disc = orc.real_error(orc.solve_bc(st, f, G, 1e-13)["u"], ue)
+    out = orc.solve_mixed_to_error(st, f, ue, disc / 2, 32, dd=True, G=G, max_outer=400)
+    assert out["status"] == "floor"
+    assert out["err"] == pytest.approx(disc, rel=1e-6)
