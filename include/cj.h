@@ -223,14 +223,17 @@ cj_status cj_solve_history(cj_plan *plan, const double *f, long long ld_f, doubl
  *   err_tol: the real-error goal (>= 0).
  *   check_every: the real error is tested before every cycle and, when > 0, after every
  *     check_every sweeps inside a cycle (0: at cycle ends only); the plan's tolerance sets
- *     only the cycle length M.
+ *     only the cycle length M.  For CJ_FP32_INNER and CJ_FP32_INNER_DD plans the error of u
+ *     (u_hi) is tested at every outer step, after its defect; check_every must be 0 and
+ *     history counts FP32 sweeps.
  *   history: host array of 2*cap doubles (may be NULL when cap = 0) receiving (sweeps done,
  *     real error) at every test; *count (may be NULL) = number of tests made (may exceed cap).
  *   *real_error (may be NULL): the real error at the last test.
  * Returns CJ_OK when the goal is met; CJ_FLOOR when the residual, still evaluated before every
  * cycle, stalls first (a goal below the discretisation error); CJ_ERR_NOT_CONVERGED when the
- * sweep budget is spent; CJ_ERR_DIVERGED on a non-finite error; CJ_ERR_INVALID_ARG for a plan
- * that is not CJ_FP64, a NULL u_exact, ld_exact < Nx, err_tol < 0 or check_every < 0.
+ * sweep budget is spent; CJ_ERR_DIVERGED on a non-finite error; CJ_ERR_INVALID_ARG for a
+ * classical-Jacobi plan, a NULL u_exact, ld_exact < Nx, err_tol < 0, check_every < 0, or a
+ * nonzero check_every on a defect-correction plan.
  * Works with either boundary type (cj_set_boundary data for CJ_BC_DIRICHLET plans).
  */
 cj_status cj_solve_to_error(cj_plan *plan, const double *f, long long ld_f, double *u,

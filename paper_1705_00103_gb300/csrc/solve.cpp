@@ -329,6 +329,17 @@ cj_status run_fp64_to_error(cj_plan *p, cudaStream_t s, ErrorStop *es, double **
     return (cj_status)stat;
 }
 
+// The real-error stop at an outer step of a defect-correction solve (after the defect and the
+// real-error launches have been read): the error first, then the floor part of the stop rule.
+int mixed_error_stop(ErrorStop *es, long long sweeps, const Norms &n, double prev, long long outer,
+                     int *stall) {
+    es->add(sweeps, n.err);
+    if (!(n.err_sq == n.err_sq) || n.err > 1e300) return CJ_ERR_DIVERGED;
+    if (n.err <= es->tol) return CJ_OK;
+    const int st = stop_rule(n.l2, n.fl, prev, outer, 0.0, 2, stall);
+    return st == CJ_OK ? CJ_FLOOR : st;
+}
+
 // One inner cycle of FP32 sweeps with weights w32[first .. first+count-1], `depth` per
 // launch; *cur holds the input on entry and the result on exit (ping-pong with *nxt).
 cudaError_t fp32_sweeps(cj_plan *p, float **cur, float **nxt, const float *r, long long first,
@@ -358,7 +369,8 @@ cudaError_t fp32_sweeps(cj_plan *p, float **cur, float **nxt, const float *r, lo
 
 // Mixed precision: FP64 defect r = b - L u -> FP32 rt; one FP32 CJM cycle of length M_in
 // on L e = rt from e = 0; u += e in FP64; repeat until the FP64 stop rule ends it.
-cj_status run_mixed(cj_plan *p, cudaStream_t s, double **cur_out, cj_result *res, History *h) {
+cj_status run_mixed(cj_plan *p, cudaStream_t s, double **cur_out, cj_result *res, History *h,
+                    ErrorStop *es = nullptr) {
     long long sweeps = 0, outer = 0;
     const long long max_outer = p->max_sweeps / p->M_in;
     double prev = 0.0, sweep_ms = 0.0;
@@ -368,11 +380,16 @@ cj_status run_mixed(cj_plan *p, cudaStream_t s, double **cur_out, cj_result *res
     for (;;) {
         CJ_TRY(launch_residual(p, p->u0, p->rt, p->e0, s), "defect");
         res->launches += 2;
+        if (es) {
+            CJ_TRY(launch_real_error(p, p->u0, es->ue, es->lde, s), "real error");
+            res->launches += 2;
+        }
         cj_status st = fetch_norms(p, s, &n);
         if (st != CJ_OK) return st;
         if (timed) sweep_ms += elapsed_ms(p);
         h->add(n.l2);
-        stat = stop_rule(n.l2, n.fl, prev, outer, p->tol, 2, &stall);
+        stat = es ? mixed_error_stop(es, sweeps, n, prev, outer, &stall)
+                  : stop_rule(n.l2, n.fl, prev, outer, p->tol, 2, &stall);
         if (stat != -1) break;
         if (outer >= max_outer) {
             stat = CJ_ERR_NOT_CONVERGED;
@@ -402,7 +419,8 @@ cj_status run_mixed(cj_plan *p, cudaStream_t s, double **cur_out, cj_result *res
 
 // Mixed precision with the double-FP64 outer loop: the solution is u0 + u1 (hi + lo), the
 // defect is evaluated to about twice FP64 precision and the correction added by TwoSum.
-cj_status run_mixed_dd(cj_plan *p, cudaStream_t s, double **cur_out, cj_result *res, History *h) {
+cj_status run_mixed_dd(cj_plan *p, cudaStream_t s, double **cur_out, cj_result *res, History *h,
+                       ErrorStop *es = nullptr) {
     long long sweeps = 0, outer = 0;
     const long long max_outer = p->max_sweeps / p->M_in;
     const double eps2 = 1.2325951644078309e-32;  // 2^-106
@@ -414,11 +432,16 @@ cj_status run_mixed_dd(cj_plan *p, cudaStream_t s, double **cur_out, cj_result *
     for (;;) {
         CJ_TRY(launch_defect_dd(p, p->u0, p->u1, p->rt, p->e0, s), "defect dd");
         res->launches += 2;
+        if (es) {  // the real error of u_hi
+            CJ_TRY(launch_real_error(p, p->u0, es->ue, es->lde, s), "real error");
+            res->launches += 2;
+        }
         cj_status st = fetch_norms(p, s, &n, eps2);
         if (st != CJ_OK) return st;
         if (timed) sweep_ms += elapsed_ms(p);
         h->add(n.l2);
-        stat = stop_rule(n.l2, n.fl, prev, outer, p->tol, 2, &stall);
+        stat = es ? mixed_error_stop(es, sweeps, n, prev, outer, &stall)
+                  : stop_rule(n.l2, n.fl, prev, outer, p->tol, 2, &stall);
         if (stat != -1) break;
         if (outer >= max_outer) {
             stat = CJ_ERR_NOT_CONVERGED;
@@ -711,8 +734,10 @@ cj_status cj_solve_to_error(cj_plan *p, const double *f, long long ldf, double *
     cj_status a = check_grid_args(p, f, ldf, u, ldu);
     if (a != CJ_OK) return a;
     if (!u_exact || ld_exact < p->Nx || !(err_tol >= 0.0) || check_every < 0 || cap < 0 ||
-        (cap > 0 && !history) || p->precision != CJ_FP64 || p->method != CJ_CJM)
+        (cap > 0 && !history) || p->method != CJ_CJM)
         return CJ_ERR_INVALID_ARG;
+    // defect-correction plans test the real error at their outer steps
+    if (p->precision != CJ_FP64 && check_every != 0) return CJ_ERR_INVALID_ARG;
     cudaStream_t s = (cudaStream_t)stream;
     auto t0 = std::chrono::steady_clock::now();
     cj_result r{};
@@ -720,7 +745,10 @@ cj_status cj_solve_to_error(cj_plan *p, const double *f, long long ldf, double *
     CJ_TRY(import64(p, f, ldf, u, ldu, s), "import");
     r.launches = 2;
     double *cur = nullptr;
-    cj_status st = run_fp64_to_error(p, s, &es, &cur, &r);
+    History h;
+    cj_status st = p->precision == CJ_FP32_INNER      ? run_mixed(p, s, &cur, &r, &h, &es)
+                   : p->precision == CJ_FP32_INNER_DD ? run_mixed_dd(p, s, &cur, &r, &h, &es)
+                                                      : run_fp64_to_error(p, s, &es, &cur, &r);
     if (count) *count = es.n;
     if (st < 0 && st != CJ_ERR_NOT_CONVERGED && st != CJ_ERR_DIVERGED) return st;
     CJ_TRY(launch_export(p, cur, u, ldu, s), "export");

@@ -481,7 +481,7 @@ def test_solve_to_error_argument_checks(cj, torch):
     z = torch.zeros((8, 8), dtype=torch.float64, device="cuda")
     with cj.Plan(8, 8, 9, 1e-6, precision=cj.CJ_FP32_INNER) as p:
         with pytest.raises(cj.CJError):
-            cj.cj_solve_to_error(p.handle, z, z.clone(), z, 1e-3)
+            cj.cj_solve_to_error(p.handle, z, z.clone(), z, 1e-3, check_every=4)
     with cj.Plan(8, 8, 9, 1e-6) as p:
         with pytest.raises(cj.CJError):
             cj.cj_solve_to_error(p.handle, z, z.clone(), z, -1.0)
@@ -603,3 +603,31 @@ def test_mixed_with_dirichlet_data_matches_oracle(cj, torch, st, prec, Nx, Ny, M
     assert res["sweeps"] == ref["sweeps"] and res["cycles"] == ref["outer"]
     assert {0: "converged", 1: "floor"}[res["status"]] == ref["status"]
     np.testing.assert_array_equal(ud.cpu().numpy(), ref["u"])
+
+
+@pytest.mark.parametrize("st", STENCILS)
+@pytest.mark.parametrize("prec,data", [(1, True), (2, True), (1, False), (2, False)])
+def test_mixed_solve_to_error_matches_oracle(cj, torch, st, prec, data):
+    """The real-error stop on the defect-correction plans (tested at every outer step): sweeps,
+    outer steps, every (sweeps, error) test and the bits of u equal the oracle's."""
+    N, M_in = 37, 32
+    if data:
+        f, ue, g = workloads.paper_problem(N, N)
+        G, Gd = _ring(torch, N, N, g)
+        disc = orc.real_error(orc.solve_bc(st, f, G, 1e-13)["u"], ue)
+    else:
+        f, ue, G = workloads.manufactured_rhs(N, N), workloads.manufactured_solution(N, N), None
+        disc = orc.real_error(orc.solve(st, f, 1e-13)["u"], ue)
+    goal = disc * 1.5 + 1e-12
+    ref = orc.solve_mixed_to_error(st, f, ue, goal, M_in, dd=prec == 2, G=G, max_outer=64)
+    with cj.Plan(N, N, st, 1e-10, precision=prec, inner_cycle=M_in,
+                 bc=cj.CJ_BC_DIRICHLET if data else cj.CJ_BC_DIRICHLET0) as p:
+        if data:
+            cj.cj_set_boundary(p.handle, Gd)
+        ud = torch.zeros((N, N), dtype=torch.float64, device="cuda")
+        res = cj.cj_solve_to_error(p.handle, dev(torch, f), ud, dev(torch, ue), goal)
+    assert ref["status"] == "converged" and res["rc"] == cj.CJ_OK
+    assert res["sweeps"] == ref["sweeps"] and res["cycles"] == ref["outer"] and res["tests"] == ref["tests"]
+    np.testing.assert_array_equal(res["history"], ref["history"])
+    np.testing.assert_array_equal(ud.cpu().numpy(), ref["u"])
+    assert res["real_error"] == ref["err"]
