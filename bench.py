@@ -536,6 +536,13 @@ def run_paper(args):
         mixed.append({"stencil": st, "N": N, "fp32_sweeps": r["sweeps"], "outer_steps": r["cycles"],
                       "time_s": r["time_s"], "status": cj.cj_status_string(r["rc"]),
                       "rel_res_l2": r["rel_res_l2"], "real_error": r["real_error_final"]})
+    # Fig. 4 right by the same defect correction: the real error is tested at every outer step
+    mixed_f4 = []
+    for st, N in ((17, 128), (5, 2048)):
+        r = paper_solve(cj, torch, N, st, 1e-8, stream, 1e-8, precision=cj.CJ_FP32_INNER_DD)
+        mixed_f4.append({"stencil": st, "N": N, "fp32_sweeps": r["sweeps"], "outer_steps": r["cycles"],
+                         "time_s": r["time_s"], "status": cj.cj_status_string(r["rc"]),
+                         "real_error": r["real_error_final"]})
     if not args.no_jacobi:
         table1_ratios(cj, torch, stream, t3, N3, tol3)
     f4 = [brief(r, k, st, N) for (k, st, N, _, _), r in zip(runs, res) if k == "fig4"]
@@ -548,6 +555,7 @@ def run_paper(args):
                       "fig4_right": "17-point N = 128 vs 5-point N = 2048, real error goal 1e-8",
                       "l2_flush": "none: the 2048^2 arrays (34 MB) fit in L2; the timing is of whole solves"},
            "table1": t3, "fig4_right": f4, "mixed_dd_to_1e-10": mixed,
+           "fig4_right_mixed_dd": mixed_f4,
            "fig4_sweep_ratio_5pt_over_17pt": f4[1]["sweeps"] / max(1, f4[0]["sweeps"]),
            "fig4_time_ratio_5pt_over_17pt": f4[1]["time_s"] / max(1e-12, f4[0]["time_s"]),
            "clocks": clk}
