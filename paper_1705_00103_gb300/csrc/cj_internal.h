@@ -138,6 +138,11 @@ cudaError_t launch_defect_dd(const cj_plan *p, const double *uh, const double *u
                              float *e_zero, cudaStream_t s);
 cudaError_t launch_correct_dd(const cj_plan *p, double *uh, double *ul, const float *e,
                               cudaStream_t s);
+// register wavefront temporal-blocked FP32 sweeps (wave_reg.cu): k = 2 sweeps per launch, or
+// 4 for the 5- and 9-point stencils
+int wave_reg_supported(int st, int k);
+cudaError_t launch_sweep32_wave_reg(const cj_plan *p, const float *e, const float *r, float *out,
+                                    const float *w, int k, cudaStream_t s);
 // wavefront temporal-blocked FP32 sweeps (wave.cu): k in {2, 4, 8} sweeps per launch
 int wave_depth_supported(int k);
 cudaError_t launch_sweep32_wave(const cj_plan *p, const float *e, const float *r, float *out,

@@ -355,7 +355,8 @@ cudaError_t fp32_sweeps(cj_plan *p, float **cur, float **nxt, const float *r, lo
         } else {
             float w[kTbMaxDepth];
             for (long long q = 0; q < k; ++q) w[q] = p->w32[(first + n + q) % p->M_in];
-            e = launch_sweep32_wave(p, *cur, r, *nxt, w, (int)k, s);
+            e = wave_reg_supported(p->st, (int)k) ? launch_sweep32_wave_reg(p, *cur, r, *nxt, w, (int)k, s)
+                                                   : launch_sweep32_wave(p, *cur, r, *nxt, w, (int)k, s);
         }
         if (e != cudaSuccess) return e;
         float *t = *cur;
@@ -574,12 +575,14 @@ cj_status cj_plan_create(int Nx, int Ny, cj_stencil st, cj_bc bc, double tol,
             p->w32.resize(p->M_in);
             for (long long k = 0; k < p->M_in; ++k) p->w32[k] = (float)wi[k];
         }
-        // default FP32 temporal depth 1, from measurements at 4096^2 (cj_sweeps_f32, Gupd/s at
-        // depth 1 / 4): 5-point 456 / 468, 9-point 456 / 400, 17-point 385 / 185 -- the
-        // vectorised one-sweep kernel runs at ~80 % of the copy bandwidth, which the wavefront
-        // kernel does not beat; cj_autotune_depth records a deeper choice where it measures one
+        // default FP32 temporal depth, from measurements (cj_sweeps_f32, 9-point Gupd/s at depth
+        // 1 / 4): 179 / 226 at 1024^2, 510 / 545 at 2048^2, 480 / 862 at 4096^2, 539 / 990 at
+        // 8192^2 (5-point: 4 is as fast or faster from 256^2 up; below 1024^2 both are
+        // launch-bound); the 17-point stencil keeps depth 1 (380 against 250 at depth 2).
+        // cj_autotune_depth records a measured choice per size class, which takes precedence.
         const int tuned = tuned_depth(st, Nx, Ny);
-        p->depth = o.temporal_depth ? o.temporal_depth : tuned ? tuned : 1;
+        const int dflt = st != 17 && (long long)Nx * Ny >= (1LL << 20) ? 4 : 1;
+        p->depth = o.temporal_depth ? o.temporal_depth : tuned ? tuned : dflt;
         long long unit = p->precision != CJ_FP64 ? p->M_in : p->M;
         p->max_sweeps = o.max_sweeps ? o.max_sweeps : 64 * unit;
         if (p->method == CJ_JACOBI && !o.max_sweeps) {

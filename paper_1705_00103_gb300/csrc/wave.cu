@@ -25,6 +25,7 @@
 // one-sweep FP32 kernel.  HBM traffic per update: about (4 e + 4 r + 4 e') / K bytes plus
 // the halo.
 #include "cj_internal.h"
+#include "fold_dev.cuh"
 #include "grid_dev.cuh"
 #include "stencil_dev.cuh"
 
@@ -35,27 +36,6 @@ constexpr int kWaveW = 128;   // threads = staged columns per block (measured be
 struct WaveWeights {
     float w[kTbMaxDepth];
 };
-
-// Index and sign of node k of the odd extension of 1..N (nodes 0 and N+1 are zero: sign 0).
-__device__ __forceinline__ int fold(int k, int N, float &sign) {
-    if (k >= 1 && k <= N) {
-        sign = 1.0f;
-        return k;
-    }
-    const int P = 2 * (N + 1);
-    int m = k % P;
-    if (m < 0) m += P;
-    if (m == 0 || m == N + 1) {
-        sign = 0.0f;
-        return 1;
-    }
-    if (m <= N) {
-        sign = 1.0f;
-        return m;
-    }
-    sign = -1.0f;
-    return P - m;
-}
 
 // True when row y of the odd extension is a Dirichlet row (a node 0 or N+1 image).
 __device__ __forceinline__ bool boundary_row(int y, int N) {

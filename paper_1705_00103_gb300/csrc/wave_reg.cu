@@ -1,0 +1,309 @@
+// Register wavefront temporal blocking of the FP32 inner sweep (sm_103a): K consecutive
+// weighted sweeps e <- e + w_n (L e - r) per HBM round trip, each with its own weight, with
+// no shared-memory exchange and no barrier.
+//
+// Every warp owns a strip of 128 staged columns (four adjacent columns per lane, loaded and
+// stored as 16-byte vectors) and streams down a block of rows.  Each iteration brings in one
+// input row and advances all K stages by one row: stage s computes row y_in - s (R + 1) from
+// rows y - R .. y + R of stage s-1, which sit in a register window of 2R + 2 rows per stage.
+// The one row of skew beyond the stencil radius makes the K stages of an iteration
+// independent of one another (stage s never reads the row stage s-1 produces in the same
+// iteration), so a warp carries 4K independent node updates per iteration.  The R columns on
+// either side of a lane's four come from the neighbouring lanes by warp shuffles when a row
+// is produced.  The strip's edge columns are garbage after each stage; with H = R K <= 4,
+// lanes 1 .. 30 (120 columns) hold valid results after K stages and are stored.  In y the
+// block's first H output rows are preceded by H warm-up input rows and followed by H more.
+//
+// Boundaries: the stages run on the odd extension of the grid (fold_dev.cuh), so no per-stage
+// ghost refresh is needed and interior results equal one-sweep launches bit for bit; the
+// residual is evaluated in difference form (resid_diff32) with the same operation order.
+//
+// r(y) is needed by every stage at a different iteration: each lane keeps its own four
+// columns of the last 16 rows of r in a private shared-memory ring (written once, read by each
+// stage; no other lane reads them, so no synchronisation is needed).
+//
+// HBM traffic per update: about (8 B in + 4 B out) / K, plus the strip's 8-column and the row
+// block's 2H-row overlap with its neighbours.
+#include "cj_internal.h"
+#include "fold_dev.cuh"
+#include "grid_dev.cuh"
+#include "stencil_dev.cuh"
+
+namespace {
+
+constexpr int kWrWarps = 4;              // warps per block; each warp is an independent strip
+constexpr int kWrThreads = 32 * kWrWarps;
+constexpr int kWrERing = 8;              // rows of e in each lane's ring (a power of 2)
+constexpr int kWrRRing = 16;             // rows of r in each lane's ring (a power of 2)
+constexpr int kWrAhead = 6;              // input rows in flight ahead of the one consumed
+
+struct WrWeights {
+    float w[4];
+};
+
+__device__ __forceinline__ void cp_async16(void *dst, const void *src) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src) : "memory");
+}
+
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+// Folded index and sign of row y (warp-uniform).
+__device__ __forceinline__ int wr_row(int y, int Ny, float &sy) {
+    if (y >= 1 && y <= Ny) {
+        sy = 1.0f;
+        return y;
+    }
+    return fold(y, Ny, sy);
+}
+
+// Starts the copies of row y of e and r (this lane's four columns) into ring rows de, dr;
+// a Dirichlet row (sign 0) is stored as 0 at once, and a mirrored row is copied from the row
+// it mirrors (its sign is applied when it is consumed).
+__device__ __forceinline__ void wr_issue(const float *__restrict__ e, const float *__restrict__ r, const Grid &g,
+                                         int c0, int y, float4 *de, float4 *dr) {
+    float sy;
+    const int fy = wr_row(y, g.Ny, sy);
+    if (sy == 0.0f) {
+        *de = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        *dr = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        return;
+    }
+    const long long k = g.idx(c0, fy);
+    cp_async16(de, e + k);
+    cp_async16(dr, r + k);
+}
+
+// Dirichlet columns of a new row.  Every row of every stage keeps column Nx + 1 at 0 and, for
+// the 5-wide stencil, column Nx + 2 at -u(Nx) (the values the odd extension gives them
+// exactly), and on the left column 0 at 0 and column -1 at -u(1).  Columns past Nx + R are
+// never read by a node in 1 .. Nx.
+struct WrEdge {
+    bool left;       // this lane holds column 1 (its left side columns are 0 and -1)
+    unsigned zero;   // bit m: column c0 + m is Nx + 1;   bit 4 + q: side column c0 + 3 + q is
+    unsigned neg;    // bit m: column c0 + m is Nx + 2;   bit 4 + q: side column c0 + 3 + q is
+};
+
+// The lane's own four values, before they are shared with the neighbouring lanes.
+template <int R>
+__device__ __forceinline__ float4 wr_edge_own(const WrEdge &ed, float4 v) {
+    float a[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+        if (ed.zero >> m & 1u) a[m] = 0.0f;
+        if (R == 2 && m >= 2 && (ed.neg >> m & 1u)) a[m] = -a[m - 2];
+    }
+    return make_float4(a[0], a[1], a[2], a[3]);
+}
+
+// The side columns after the shuffles.
+template <int R, int WC>
+__device__ __forceinline__ void wr_edge_side(const WrEdge &ed, float (&row)[WC]) {
+    if (ed.left) {
+        row[R - 1] = 0.0f;
+        if (R == 2) row[0] = -row[R];
+    }
+#pragma unroll
+    for (int q = 1; q <= R; ++q) {
+        if (ed.zero >> (3 + q) & 1u) row[R + 3 + q] = 0.0f;
+        if (R == 2 && (ed.neg >> (3 + q) & 1u)) row[R + 3 + q] = -row[R + 1 + q];
+    }
+}
+
+// Puts the four values v of a new row into window row `row` (columns c0 - R .. c0 + 3 + R),
+// with the side columns from the neighbouring lanes; `edge`: this warp's strip touches a
+// Dirichlet column (warp-uniform).
+template <int R, int WC>
+__device__ __forceinline__ void wr_put(float (&row)[WC], float4 v, bool edge, const WrEdge &ed) {
+    if (edge) v = wr_edge_own<R>(ed, v);
+    row[R] = v.x;
+    row[R + 1] = v.y;
+    row[R + 2] = v.z;
+    row[R + 3] = v.w;
+    const float vs[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+    for (int q = 1; q <= R; ++q) {
+        row[R - q] = __shfl_up_sync(0xffffffffu, vs[4 - q], 1);
+        row[R + 3 + q] = __shfl_down_sync(0xffffffffu, vs[q - 1], 1);
+    }
+    if (edge) wr_edge_side<R, WC>(ed, row);
+}
+
+// First staged column of strip x: strip 0 starts at column 1 and stores lanes 0 .. 30, the
+// others start 4 columns before their first output column and store lanes 1 .. 30.
+__host__ __device__ __forceinline__ int wr_strip_x0(int x) { return x == 0 ? 1 : 121 + 120 * (x - 1); }
+
+__host__ __device__ __forceinline__ int wr_strips(int Nx) { return Nx <= 124 ? 1 : 1 + (Nx - 124 + 119) / 120; }
+
+template <int ST, int K>
+__global__ void __launch_bounds__(kWrThreads, ST == 17 ? 2 : 3)
+    sweep_wave_reg_kernel(const float *__restrict__ e, const float *__restrict__ r, float *__restrict__ out,
+                          Grid g, WrWeights wt, int rows, int nrb, int nstrips) {
+    constexpr int R = ST == 17 ? 2 : 1;
+    constexpr int H = R * K;
+    static_assert(H <= 4, "the valid strip after K stages is lanes 1 .. 30");
+    constexpr int SK = R + 1;      // rows between consecutive stages
+    constexpr int W = 2 * R + 2;   // window rows per stage input
+    constexpr int WC = 4 + 2 * R;  // window columns
+    constexpr int D = kWrAhead;
+    static_assert(D < kWrERing && K * SK + D < kWrRRing, "ring rows still in use would be overwritten");
+    __shared__ float4 ering[kWrWarps][kWrERing][32];
+    __shared__ float4 rring[kWrWarps][kWrRRing][32];
+
+    const int lane = (int)threadIdx.x & 31, wid = (int)threadIdx.x >> 5;
+    const int gw = (int)blockIdx.x * kWrWarps + wid;  // (strip, row block) of this warp
+    if (gw >= nstrips * nrb) return;                   // whole warp: no block barrier is used
+    const int strip = gw % nstrips, rb = gw / nstrips;
+    const int Nx = g.Nx, Ny = g.Ny;
+    const int c0 = wr_strip_x0(strip) + 4 * lane;  // first of this lane's columns
+    const bool live = c0 <= Nx;                    // lanes past Nx hold nothing that is read
+    const int y0 = rb * rows + 1;
+    const int y1 = min(y0 + rows - 1, Ny);  // last output row
+    const int ystart = y0 - H, ylast = y1 + H;
+    const int T = (y1 - y0 + 1) + H + K * SK;  // output row y1 leaves at iteration T - 1
+    const bool out_lane = live && lane <= 30 && (lane >= 1 || strip == 0);
+    // warp-uniform: the strip holds column 1, or one of its 128 columns lies past Nx (then
+    // the lane holding Nx keeps the Dirichlet columns; the last strip, and the one before it
+    // when Nx falls in its side lane)
+    const bool edge = strip == 0 || wr_strip_x0(strip) + 127 > Nx;
+    WrEdge ed;
+    ed.left = strip == 0 && lane == 0;
+    ed.zero = ed.neg = 0u;
+#pragma unroll
+    for (int m = 0; m < 4 + R; ++m) {  // own columns m < 4, side columns c0 + 3 + q at bit 3 + q
+        const int c = c0 + m;
+        if (c == Nx + 1) ed.zero |= 1u << m;
+        if (R == 2 && c == Nx + 2) ed.neg |= 1u << m;
+    }
+
+    float4 *er = ering[wid][0], *rr = rring[wid][0];
+    const float4 z4 = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+#pragma unroll
+    for (int q = 0; q < kWrERing; ++q) er[q * 32 + lane] = z4;
+#pragma unroll
+    for (int q = 0; q < kWrRRing; ++q) rr[q * 32 + lane] = z4;
+
+    // win[s][q][c]: input of stage s+1 as a ring of W rows (the row produced at iteration t
+    // sits at q = t mod W), columns c0 - R .. c0 + 3 + R
+    float win[K][W][WC];
+#pragma unroll
+    for (int s = 0; s < K; ++s)
+#pragma unroll
+        for (int q = 0; q < W; ++q)
+#pragma unroll
+            for (int c = 0; c < WC; ++c) win[s][q][c] = 0.0f;
+
+#pragma unroll
+    for (int d = 0; d < D; ++d) {
+        if (live && ystart + d <= ylast) wr_issue(e, r, g, c0, ystart + d, &er[d * 32 + lane], &rr[d * 32 + lane]);
+        cp_async_commit();
+    }
+
+    for (int t0 = 0; t0 < T; t0 += W) {
+#pragma unroll
+        for (int k = 0; k < W; ++k) {  // k = t mod W: the windows' ring positions are constants
+            const int t = t0 + k;
+            if (t >= T) break;
+            const int yin = ystart + t;
+            if (live && yin + D <= ylast)
+                wr_issue(e, r, g, c0, yin + D, &er[((t + D) & (kWrERing - 1)) * 32 + lane],
+                         &rr[((t + D) & (kWrRRing - 1)) * 32 + lane]);
+            cp_async_commit();
+            cp_async_wait<D>();  // row yin has landed
+            float4 ve = er[(t & (kWrERing - 1)) * 32 + lane];
+            if (yin < 1 || yin > Ny) {  // a mirrored row: apply its sign once, for every stage
+                float sy;
+                wr_row(yin, Ny, sy);
+                float4 *pr = &rr[(t & (kWrRRing - 1)) * 32 + lane];
+                const float4 vr = *pr;
+                ve = make_float4(sy * ve.x, sy * ve.y, sy * ve.z, sy * ve.w);
+                *pr = make_float4(sy * vr.x, sy * vr.y, sy * vr.z, sy * vr.w);
+            }
+            wr_put<R, WC>(win[0][k], ve, edge, ed);
+            // stage s: row yin - s SK from the rows of ages SK - R .. SK + R of its window (the
+            // row of age 0 is the one stage s - 1 produces in this same iteration)
+#pragma unroll
+            for (int s = 1; s <= K; ++s) {
+                const float4 rq = rr[((t - s * SK) & (kWrRRing - 1)) * 32 + lane];
+                const float rk[4] = {rq.x, rq.y, rq.z, rq.w};
+                float nv[4];
+#pragma unroll
+                for (int m = 0; m < 4; ++m) {
+                    auto N = [&](int dx, int dy) { return win[s - 1][(k - SK + dy + 2 * W) % W][R + m + dx]; };
+                    const float uc = win[s - 1][(k - SK + 2 * W) % W][R + m];
+                    nv[m] = fmaf(wt.w[s - 1], resid_diff32<ST>(N, uc, rk[m]), uc);
+                }
+                if (s < K) {
+                    wr_put<R, WC>(win[s][k], make_float4(nv[0], nv[1], nv[2], nv[3]), edge, ed);
+                } else {
+                    const int yo = yin - K * SK;
+                    if (out_lane && yo >= y0 && yo <= y1) {
+                        const bool bnd = ST == 17 && (c0 == 1 || c0 + 3 >= Nx || yo == 1 || yo == Ny);
+                        if (c0 + 3 <= Nx && !bnd) {
+                            *reinterpret_cast<float4 *>(out + g.idx(c0, yo)) =
+                                make_float4(nv[0], nv[1], nv[2], nv[3]);
+                        } else {
+#pragma unroll
+                            for (int m = 0; m < 4; ++m)
+                                if (c0 + m <= Nx) store_node<R, float>(out, g, c0 + m, yo, nv[m]);
+                        }
+                    }
+                }
+            }
+        }
+    }
+    cp_async_wait<0>();
+}
+
+// Warps of this kernel resident on the device at once (computed once, thread-safely).
+template <int ST, int K>
+int wr_resident_warps() {
+    static const int n = [] {
+        int dev = 0, sms = 152, per_sm = 1;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sweep_wave_reg_kernel<ST, K>, kWrThreads, 0) !=
+                cudaSuccess ||
+            per_sm < 1)
+            per_sm = 1;
+        return sms * per_sm * kWrWarps;
+    }();
+    return n;
+}
+
+template <int ST, int K>
+cudaError_t launch_k(const Grid &g, const float *e, const float *r, float *out, const float *w, cudaStream_t s) {
+    constexpr int H = (ST == 17 ? 2 : 1) * K;
+    WrWeights wt{};
+    for (int k = 0; k < K; ++k) wt.w[k] = w[k];
+    const int nstrips = wr_strips(g.Nx);
+    // at most one wave of warps; row blocks of at least 4H rows so the warm-up stays a minority
+    int nrb = wr_resident_warps<ST, K>() / nstrips;
+    if (nrb < 1) nrb = 1;
+    int rows = (g.Ny + nrb - 1) / nrb;
+    if (rows < 4 * H) rows = 4 * H;
+    nrb = (g.Ny + rows - 1) / rows;
+    const long long warps = (long long)nstrips * nrb;
+    const int blocks = (int)((warps + kWrWarps - 1) / kWrWarps);
+    sweep_wave_reg_kernel<ST, K><<<blocks, kWrThreads, 0, s>>>(e, r, out, g, wt, rows, nrb, nstrips);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+int wave_reg_supported(int st, int k) { return k == 2 || (k == 4 && st != 17); }
+
+cudaError_t launch_sweep32_wave_reg(const cj_plan *p, const float *e, const float *r, float *out,
+                                    const float *w, int k, cudaStream_t s) {
+    if (!wave_reg_supported(p->st, k)) return cudaErrorInvalidValue;
+    switch (p->st) {
+        case 5: return k == 2 ? launch_k<5, 2>(p->g32, e, r, out, w, s) : launch_k<5, 4>(p->g32, e, r, out, w, s);
+        case 9: return k == 2 ? launch_k<9, 2>(p->g32, e, r, out, w, s) : launch_k<9, 4>(p->g32, e, r, out, w, s);
+        default: return launch_k<17, 2>(p->g32, e, r, out, w, s);
+    }
+}

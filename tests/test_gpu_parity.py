@@ -348,6 +348,28 @@ def test_fp32_temporal_blocking_bit_exact(cj, torch, st, depth, Nx, Ny):
     np.testing.assert_array_equal(ed.cpu().numpy(), ref)
 
 
+@pytest.mark.parametrize("st,depth", [(5, 2), (5, 4), (9, 2), (9, 4), (17, 2)])
+@pytest.mark.parametrize("Nx,Ny", [(124, 9), (125, 40), (244, 17), (245, 3), (246, 66), (247, 33), (248, 129),
+                                   (369, 250)])
+def test_register_wavefront_strip_edges_bit_exact(cj, torch, st, depth, Nx, Ny):
+    """The register wavefront kernel's 120-column strips (124 for the first) with the last
+    column Nx at every position within a lane's four, one and several strips and row blocks:
+    depth sweeps per launch equal the oracle's one-sweep-at-a-time FP32 result bit for bit."""
+    rng = np.random.default_rng(3 * Nx + Ny + 11 * st + depth)
+    r = rng.standard_normal((Ny, Nx)).astype(np.float32)
+    e = rng.standard_normal((Ny, Nx)).astype(np.float32)
+    count = 3 * depth
+    with cj.Plan(Nx, Ny, st, 1e-8, precision=cj.CJ_FP32_INNER, inner_cycle=64, temporal_depth=depth) as p:
+        kmin, kmax = orc.kappa_bounds(st, Nx, Ny)
+        w32 = orc.sweep_coeffs(st, kmin, kmax, 64).astype(np.float32)
+        ed = dev(torch, e)
+        cj.cj_sweeps_f32(p.handle, dev(torch, r), ed, 5, count)
+    ref = e.copy()
+    for k in range(count):
+        ref = orc.sweep_f32(st, ref, r, w32[(5 + k) % 64])
+    np.testing.assert_array_equal(ed.cpu().numpy(), ref)
+
+
 @pytest.mark.parametrize("st", STENCILS)
 def test_mixed_solve_with_temporal_blocking_matches_oracle(cj, torch, st):
     Nx, Ny, M_in = 200, 150, 128
