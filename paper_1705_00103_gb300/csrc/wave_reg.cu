@@ -134,6 +134,34 @@ __device__ __forceinline__ void wr_put(float (&row)[WC], float4 v, bool edge, co
     if (edge) wr_edge_side<R, WC>(ed, row);
 }
 
+// (L e - r) at this lane's four nodes of the centre row c of a window (rows n below and s
+// above it; columns c0 - R .. c0 + 3 + R), in the operation order of resid_diff32.  For the
+// 5- and 9-point stencils (the only ones it serves) the horizontal differences are shared between neighbouring nodes:
+// e(i-1) - e(i) is computed as -(e(i) - e(i-1)), which round-to-nearest makes exact, so each
+// node's result is bit-identical to resid_diff32's.
+template <int ST, int R, int WC>
+__device__ __forceinline__ void wr_resid(const float (&rs)[WC], const float (&rc)[WC], const float (&rn)[WC],
+                                         const float (&rk)[4], float (&res)[4]) {
+    if (ST != 17) {
+        float dE[5];  // dE[j] = e(c0 - 1 + j + 1) - e(c0 - 1 + j), j = 0 .. 4
+#pragma unroll
+        for (int j = 0; j < 5; ++j) dE[j] = rc[R + j] - rc[R + j - 1];
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+            const float uc = rc[R + m];
+            const float v1 = (rs[R + m] - uc) + (rn[R + m] - uc);
+            const float p0 = -dE[m] + dE[m + 1];
+            if (ST == 5) {
+                res[m] = (p0 + v1) - rk[m];
+            } else {
+                const float pm = (rs[R + m - 1] - uc) + (rs[R + m + 1] - uc);
+                const float pp = (rn[R + m - 1] - uc) + (rn[R + m + 1] - uc);
+                res[m] = fmaf(4.0f / 6.0f, p0 + v1, fmaf(1.0f / 6.0f, pm + pp, -rk[m]));
+            }
+        }
+    }
+}
+
 // First staged column of strip x: strip 0 starts at column 1 and stores lanes 0 .. 30, the
 // others start 4 columns before their first output column and store lanes 1 .. 30.
 __host__ __device__ __forceinline__ int wr_strip_x0(int x) { return x == 0 ? 1 : 121 + 120 * (x - 1); }
@@ -232,11 +260,22 @@ __global__ void __launch_bounds__(kWrThreads, ST == 17 ? 2 : 3)
                 const float4 rq = rr[((t - s * SK) & (kWrRRing - 1)) * 32 + lane];
                 const float rk[4] = {rq.x, rq.y, rq.z, rq.w};
                 float nv[4];
+                if (ST == 17) {
 #pragma unroll
-                for (int m = 0; m < 4; ++m) {
-                    auto N = [&](int dx, int dy) { return win[s - 1][(k - SK + dy + 2 * W) % W][R + m + dx]; };
-                    const float uc = win[s - 1][(k - SK + 2 * W) % W][R + m];
-                    nv[m] = fmaf(wt.w[s - 1], resid_diff32<ST>(N, uc, rk[m]), uc);
+                    for (int m = 0; m < 4; ++m) {
+                        auto N = [&](int dx, int dy) { return win[s - 1][(k - SK + dy + 2 * W) % W][R + m + dx]; };
+                        const float uc = win[s - 1][(k - SK + 2 * W) % W][R + m];
+                        nv[m] = fmaf(wt.w[s - 1], resid_diff32<ST>(N, uc, rk[m]), uc);
+                    }
+                } else {
+                    float res[4];
+                    wr_resid<ST, R, WC>(win[s - 1][(k - SK - 1 + 2 * W) % W], win[s - 1][(k - SK + 2 * W) % W],
+                                        win[s - 1][(k - SK + 1 + 2 * W) % W], rk, res);
+#pragma unroll
+                    for (int m = 0; m < 4; ++m) {
+                        const float uc = win[s - 1][(k - SK + 2 * W) % W][R + m];
+                        nv[m] = fmaf(wt.w[s - 1], res[m], uc);
+                    }
                 }
                 if (s < K) {
                     wr_put<R, WC>(win[s][k], make_float4(nv[0], nv[1], nv[2], nv[3]), edge, ed);
