@@ -134,30 +134,44 @@ __device__ __forceinline__ void wr_put(float (&row)[WC], float4 v, bool edge, co
     if (edge) wr_edge_side<R, WC>(ed, row);
 }
 
-// (L e - r) at this lane's four nodes of the centre row c of a window (rows n below and s
-// above it; columns c0 - R .. c0 + 3 + R), in the operation order of resid_diff32.  For the
-// 5- and 9-point stencils (the only ones it serves) the horizontal differences are shared between neighbouring nodes:
-// e(i-1) - e(i) is computed as -(e(i) - e(i-1)), which round-to-nearest makes exact, so each
-// node's result is bit-identical to resid_diff32's.
+// Differences of the row pair (y, y+1) of one stage's input at this lane's columns:
+// dN[m] = e(c0+m, y+1) - e(c0+m, y); dNE[j] = e(c0+j, y+1) - e(c0-1+j, y);
+// dNW[j] = e(c0-1+j, y+1) - e(c0+j, y).  Node (i, y) uses them for its upper neighbours and
+// node (i, y+1), one iteration later, for its lower ones, negated: e(a) - e(b) is computed
+// as -(e(b) - e(a)), which round-to-nearest makes exact.
+struct WrPair {
+    float dN[4], dNE[5], dNW[5];
+};
+
+// (L e - r) at this lane's four nodes of the centre row rc (upper row rn; lo: the pair
+// (y-1, y) from the previous iteration; hi: filled here with the pair (y, y+1)), in the
+// operation order of resid_diff32, so each node's result is bit-identical to it.  The
+// horizontal differences are shared the same way: e(i-1) - e(i) = -(e(i) - e(i-1)).
 template <int ST, int R, int WC>
-__device__ __forceinline__ void wr_resid(const float (&rs)[WC], const float (&rc)[WC], const float (&rn)[WC],
-                                         const float (&rk)[4], float (&res)[4]) {
-    if (ST != 17) {
-        float dE[5];  // dE[j] = e(c0 - 1 + j + 1) - e(c0 - 1 + j), j = 0 .. 4
+__device__ __forceinline__ void wr_resid(const float (&rc)[WC], const float (&rn)[WC], const WrPair &lo,
+                                         WrPair &hi, const float (&rk)[4], float (&res)[4]) {
+    float dE[5];  // dE[j] = e(c0 + j) - e(c0 - 1 + j)
 #pragma unroll
-        for (int j = 0; j < 5; ++j) dE[j] = rc[R + j] - rc[R + j - 1];
+    for (int j = 0; j < 5; ++j) dE[j] = rc[R + j] - rc[R + j - 1];
 #pragma unroll
-        for (int m = 0; m < 4; ++m) {
-            const float uc = rc[R + m];
-            const float v1 = (rs[R + m] - uc) + (rn[R + m] - uc);
-            const float p0 = -dE[m] + dE[m + 1];
-            if (ST == 5) {
-                res[m] = (p0 + v1) - rk[m];
-            } else {
-                const float pm = (rs[R + m - 1] - uc) + (rs[R + m + 1] - uc);
-                const float pp = (rn[R + m - 1] - uc) + (rn[R + m + 1] - uc);
-                res[m] = fmaf(4.0f / 6.0f, p0 + v1, fmaf(1.0f / 6.0f, pm + pp, -rk[m]));
-            }
+    for (int m = 0; m < 4; ++m) hi.dN[m] = rn[R + m] - rc[R + m];
+    if (ST == 9) {
+#pragma unroll
+        for (int j = 0; j < 5; ++j) {
+            hi.dNE[j] = rn[R + j] - rc[R + j - 1];
+            hi.dNW[j] = rn[R + j - 1] - rc[R + j];
+        }
+    }
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+        const float v1 = -lo.dN[m] + hi.dN[m];
+        const float p0 = -dE[m] + dE[m + 1];
+        if (ST == 5) {
+            res[m] = (p0 + v1) - rk[m];
+        } else {
+            const float pm = -lo.dNE[m] + -lo.dNW[m + 1];
+            const float pp = hi.dNW[m] + hi.dNE[m + 1];
+            res[m] = fmaf(4.0f / 6.0f, p0 + v1, fmaf(1.0f / 6.0f, pm + pp, -rk[m]));
         }
     }
 }
@@ -168,8 +182,11 @@ __host__ __device__ __forceinline__ int wr_strip_x0(int x) { return x == 0 ? 1 :
 
 __host__ __device__ __forceinline__ int wr_strips(int Nx) { return Nx <= 124 ? 1 : 1 + (Nx - 124 + 119) / 120; }
 
+// Registers: the 9-point depth-4 kernel carries 237 (windows and pair differences of four
+// stages), so it runs 2 blocks per SM; 3 blocks (12 warps, 168 registers each, as the register
+// file is split between the SM's four schedulers) would spill.
 template <int ST, int K>
-__global__ void __launch_bounds__(kWrThreads, ST == 17 ? 2 : 3)
+__global__ void __launch_bounds__(kWrThreads, ST == 17 || (ST == 9 && K == 4) ? 2 : 3)
     sweep_wave_reg_kernel(const float *__restrict__ e, const float *__restrict__ r, float *__restrict__ out,
                           Grid g, WrWeights wt, int rows, int nrb, int nstrips) {
     constexpr int R = ST == 17 ? 2 : 1;
@@ -179,6 +196,7 @@ __global__ void __launch_bounds__(kWrThreads, ST == 17 ? 2 : 3)
     constexpr int W = 2 * R + 2;   // window rows per stage input
     constexpr int WC = 4 + 2 * R;  // window columns
     constexpr int D = kWrAhead;
+    static_assert(W % 2 == 0, "the pair differences alternate with the iteration's parity");
     static_assert(D < kWrERing && K * SK + D < kWrRRing, "ring rows still in use would be overwritten");
     __shared__ float4 ering[kWrWarps][kWrERing][32];
     __shared__ float4 rring[kWrWarps][kWrRRing][32];
@@ -219,6 +237,18 @@ __global__ void __launch_bounds__(kWrThreads, ST == 17 ? 2 : 3)
     // win[s][q][c]: input of stage s+1 as a ring of W rows (the row produced at iteration t
     // sits at q = t mod W), columns c0 - R .. c0 + 3 + R
     float win[K][W][WC];
+    // pair differences of each stage's input, alternating between iterations (k & 1): the
+    // pair computed at one iteration is the lower pair of the next
+    WrPair pr2[K][2];
+#pragma unroll
+    for (int s = 0; s < K; ++s)
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+#pragma unroll
+            for (int m = 0; m < 4; ++m) pr2[s][h].dN[m] = 0.0f;
+#pragma unroll
+            for (int j = 0; j < 5; ++j) pr2[s][h].dNE[j] = pr2[s][h].dNW[j] = 0.0f;
+        }
 #pragma unroll
     for (int s = 0; s < K; ++s)
 #pragma unroll
@@ -269,8 +299,8 @@ __global__ void __launch_bounds__(kWrThreads, ST == 17 ? 2 : 3)
                     }
                 } else {
                     float res[4];
-                    wr_resid<ST, R, WC>(win[s - 1][(k - SK - 1 + 2 * W) % W], win[s - 1][(k - SK + 2 * W) % W],
-                                        win[s - 1][(k - SK + 1 + 2 * W) % W], rk, res);
+                    wr_resid<ST, R, WC>(win[s - 1][(k - SK + 2 * W) % W], win[s - 1][(k - SK + 1 + 2 * W) % W],
+                                        pr2[s - 1][(k + 1) & 1], pr2[s - 1][k & 1], rk, res);
 #pragma unroll
                     for (int m = 0; m < 4; ++m) {
                         const float uc = win[s - 1][(k - SK + 2 * W) % W][R + m];
