@@ -139,7 +139,7 @@ cudaError_t launch_defect_dd(const cj_plan *p, const double *uh, const double *u
 cudaError_t launch_correct_dd(const cj_plan *p, double *uh, double *ul, const float *e,
                               cudaStream_t s);
 // register wavefront temporal-blocked FP32 sweeps (wave_reg.cu): k = 2 sweeps per launch, or
-// 4 for the 5- and 9-point stencils
+// 3 or 4 for the 5- and 9-point stencils
 int wave_reg_supported(int st, int k);
 cudaError_t launch_sweep32_wave_reg(const cj_plan *p, const float *e, const float *r, float *out,
                                     const float *w, int k, cudaStream_t s);

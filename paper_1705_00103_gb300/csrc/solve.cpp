@@ -347,8 +347,9 @@ cudaError_t fp32_sweeps(cj_plan *p, float **cur, float **nxt, const float *r, lo
     long long n = 0;
     while (n < count) {
         long long k = p->depth < count - n ? p->depth : count - n;
-        // the wavefront kernel exists for depths 2, 4 and 8: use the largest that fits
-        while (k > 1 && !wave_depth_supported((int)k)) --k;
+        // the temporal-blocking kernels exist for depths 2, 3 and 4 (register wavefront; 17
+        // points: 2) and 2, 4 and 8 (wavefront strips): use the largest that fits
+        while (k > 1 && !wave_reg_supported(p->st, (int)k) && !wave_depth_supported((int)k)) --k;
         cudaError_t e;
         if (k == 1) {
             e = launch_sweep32(p, *cur, r, *nxt, p->w32[(first + n) % p->M_in], s);

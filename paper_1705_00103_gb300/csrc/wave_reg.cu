@@ -365,14 +365,20 @@ cudaError_t launch_k(const Grid &g, const float *e, const float *r, float *out, 
 
 }  // namespace
 
-int wave_reg_supported(int st, int k) { return k == 2 || (k == 4 && st != 17); }
+int wave_reg_supported(int st, int k) { return k == 2 || ((k == 3 || k == 4) && st != 17); }
 
 cudaError_t launch_sweep32_wave_reg(const cj_plan *p, const float *e, const float *r, float *out,
                                     const float *w, int k, cudaStream_t s) {
     if (!wave_reg_supported(p->st, k)) return cudaErrorInvalidValue;
     switch (p->st) {
-        case 5: return k == 2 ? launch_k<5, 2>(p->g32, e, r, out, w, s) : launch_k<5, 4>(p->g32, e, r, out, w, s);
-        case 9: return k == 2 ? launch_k<9, 2>(p->g32, e, r, out, w, s) : launch_k<9, 4>(p->g32, e, r, out, w, s);
+        case 5:
+            return k == 2 ? launch_k<5, 2>(p->g32, e, r, out, w, s)
+                   : k == 3 ? launch_k<5, 3>(p->g32, e, r, out, w, s)
+                            : launch_k<5, 4>(p->g32, e, r, out, w, s);
+        case 9:
+            return k == 2 ? launch_k<9, 2>(p->g32, e, r, out, w, s)
+                   : k == 3 ? launch_k<9, 3>(p->g32, e, r, out, w, s)
+                            : launch_k<9, 4>(p->g32, e, r, out, w, s);
         default: return launch_k<17, 2>(p->g32, e, r, out, w, s);
     }
 }
