@@ -171,23 +171,31 @@ class ClockSampler:
 # ----------------------------------------------------------------- traffic record
 
 KERNEL_SOURCES = ("kernels.cu", "stencil_dev.cuh", "grid_dev.cuh")
+# sources of the FP32 register wavefront kernel (temporal blocking)
+WAVE_REG_SOURCES = ("wave_reg.cu", "fold_dev.cuh", "grid_dev.cuh", "stencil_dev.cuh", "cj_internal.h")
+# FP32 instructions per 9-point update of the register wavefront kernel: 4.75 differences
+# (shared between neighbours), 4 pair sums, 2 group sums, 2 coefficient fmas, 1 update fma
+FP32_OPS_PER_UPDATE_WAVE_REG_9 = 13.75
+# FP32 issue peak: 4 schedulers x 32 lanes per SM x 152 SMs x 2.07 GHz (FFMA/FADD issue at one
+# warp instruction per scheduler per clock)
+FP32_ISSUE_PEAK_TOPS = 4 * 32 * 152 * 2.07e9 / 1e12
 
 
-def kernel_digest() -> str:
-    """Digest of the sources the sweep kernel is compiled from."""
+def kernel_digest(sources=KERNEL_SOURCES) -> str:
+    """Digest of the sources a kernel is compiled from."""
     h = hashlib.sha256()
-    for name in KERNEL_SOURCES:
+    for name in sources:
         h.update(open(os.path.join(ROOT, "paper_1705_00103_gb300", "csrc", name), "rb").read())
     return h.hexdigest()[:16]
 
 
-def traffic_per_launch(kernel_key: str):
+def traffic_per_launch(kernel_key: str, sources=KERNEL_SOURCES):
     """DRAM bytes per launch of a kernel from the committed ncu summary, or None when the
     kernel's sources changed since the counters were taken."""
     path = os.path.join(ROOT, "profiles", "traffic_per_launch.txt")
     if not os.path.exists(path):
         return None
-    digest = kernel_digest()
+    digest = kernel_digest(sources)
     for line in open(path):
         parts = line.split()
         if len(parts) >= 3 and not line.startswith("#") and parts[0] == kernel_key:
@@ -354,7 +362,39 @@ def mixed_paths(cj, f, stream, plain):
                      # temporal blocking moves fewer bytes for the same updates
                      "fp32_hbm_gbs_algorithmic": 12.0 * upd_s / 1e9,
                      "speedup_vs_plain_fp64_time": plain["seconds"] / r["seconds"]}
+    out["fp32_sweep_roofline"] = fp32_sweep_roofline(cj, stream)
     return out
+
+
+def fp32_sweep_roofline(cj, stream, launches: int = 64) -> dict:
+    """The dominant kernel of the FP32-inner paths, the register wavefront at its default depth
+    (4 sweeps per launch), timed alone with CUDA events on the launching stream over `launches`
+    launches on the 4096^2 grid (three 64 MB FP32 grids, more than the L2), against the FP32
+    issue peak: it is bound by instruction issue, not by HBM."""
+    import torch
+    with cj.Plan(N_GRID, N_GRID, STENCIL, TOL, precision=cj.CJ_FP32_INNER) as p:
+        r = torch.zeros((N_GRID, N_GRID), dtype=torch.float32, device="cuda")
+        e = torch.zeros_like(r)
+        depth = 4
+        cj.cj_sweeps_f32(p.handle, r, e, 0, 4 * depth, stream)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        cj.cj_sweeps_f32(p.handle, r, e, 0, launches * depth, stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+    per_launch = e0.elapsed_time(e1) * 1e-3 / launches
+    upd = depth * N_GRID * N_GRID
+    achieved = FP32_OPS_PER_UPDATE_WAVE_REG_9 * upd / per_launch / 1e12
+    return {"kernel": "sweep_wave_reg_kernel<9,4>", "bound": "alu", "achieved": achieved,
+            "peak": FP32_ISSUE_PEAK_TOPS, "unit": "TFP32op/s", "frac": achieved / FP32_ISSUE_PEAK_TOPS,
+            "traffic": traffic_per_launch("sweep_wave_reg_9_d4_4096", WAVE_REG_SOURCES),
+            "avg_launch_us": per_launch * 1e6, "sweeps_per_launch": depth,
+            "gupdates_s": upd / per_launch / 1e9,
+            "hbm_gbs_algorithmic": 12.0 * N_GRID * N_GRID / per_launch / 1e9,
+            "peak_note": "FP32 issue peak: 4 schedulers x 32 lanes x 152 SMs x 2.07 GHz; 13.75 FP32 "
+                         "instructions per 9-point update in the kernel's shared-difference form"}
 
 
 def run_highorder(args):
