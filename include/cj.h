@@ -86,8 +86,9 @@ typedef struct {
     int inner_cycle;        /* FP32-inner modes: inner cycle length (a power of two); 0 = auto */
     int temporal_depth;     /* FP32-inner modes: sweeps fused per HBM round trip (temporal
                                blocking), 1..8; 0 = auto: the depth cj_autotune_depth
-                               recorded for this stencil and size class, else 4 for the 5-
-                               and 9-point stencils on grids of 2^20 nodes or more, else 1 */
+                               recorded for this stencil and size class, else 4 for the
+                               5-point stencil on grids of 2^16 nodes or more and the
+                               9-point one on grids of 2^20 or more, else 1 */
     long long max_sweeps;   /* sweep budget of one solve; 0 = 64 cycles (CJ_JACOBI: the larger
                                of 64 intervals and 4 ln(1/tol) / kmin sweeps) */
     int method;             /* cj_method (default CJ_CJM) */
