@@ -15,6 +15,9 @@ e2e    = the same metric through cj_solve_host (host arrays, one H2D copy of f a
          initial guess, one D2H copy of u inside every step);
 roofline: the FP64 sweep kernel against the FP64 instruction-issue peak (it is bound by
          FP64 arithmetic on GB300, not by HBM);
+vs_plain_fp64: the same problem by FP32 inner cycles in FP64 / double-FP64 defect correction
+         (time to 1e-10), with fp32_sweep_roofline: the FP32 register wavefront kernel (4 sweeps
+         per launch) timed alone against the FP32 instruction-issue peak;
 cpu_baseline / --impl reference: the FP64 C oracle (test infrastructure) timed on the
          host on a bounded sample of the same workload.
 N > 1 runs independent replicas, one per GPU (the solve does not shard across GPUs).
@@ -347,7 +350,7 @@ def mixed_paths(cj, f, stream, plain):
     out = {"plain_fp64": {"time_s": plain["seconds"], "rel_res_l2": plain["rel_res_l2"],
                           "status": cj.cj_status_string(plain["rc"]), "sweeps": plain["sweeps"]}}
     runs = (("fp32_inner_fp64_outer", cj.CJ_FP32_INNER, 0), ("fp32_inner_dd_outer", cj.CJ_FP32_INNER_DD, 0),
-            ("fp32_inner_dd_outer_temporal_blocking_4", cj.CJ_FP32_INNER_DD, 4))
+            ("fp32_inner_dd_outer_one_sweep_per_launch", cj.CJ_FP32_INNER_DD, 1))
     for name, prec, depth in runs:
         with cj.Plan(N_GRID, N_GRID, STENCIL, TOL, precision=prec, temporal_depth=depth) as p:
             u = torch.zeros((N_GRID, N_GRID), dtype=torch.float64, device="cuda")
@@ -356,7 +359,8 @@ def mixed_paths(cj, f, stream, plain):
         upd_s = N_GRID * N_GRID * r["sweeps"] / r["sweep_seconds"]
         out[name] = {"time_s": r["seconds"], "rel_res_l2": r["rel_res_l2"], "status": cj.cj_status_string(r["rc"]),
                      "fp32_sweeps": r["sweeps"], "outer_steps": r["cycles"], "inner_cycle": M_in,
-                     "temporal_depth": depth if depth else "auto (1 unless cj_autotune_depth recorded another)",
+                     "temporal_depth": depth if depth else "auto (4 for this stencil and size unless "
+                                                           "cj_autotune_depth recorded another)",
                      "fp32_gupdates_s": upd_s / 1e9,
                      # one FP32 sweep reads e and r and writes e' (12 B per update) when it runs alone;
                      # temporal blocking moves fewer bytes for the same updates
