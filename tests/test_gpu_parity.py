@@ -254,6 +254,27 @@ def test_full_size_sweeps_bit_exact(cj, torch, st, N):
     np.testing.assert_array_equal(got, ref)
 
 
+@pytest.mark.parametrize("st", (5, 9))
+def test_full_size_fp32_temporal_sweeps_bit_exact(cj, torch, st):
+    """Nine FP32 inner sweeps of the 4096^2 grid at the solver's default depth for this size (the
+    register wavefront, four sweeps per launch, then one), against the oracle's one-sweep-at-a-
+    time FP32 sweeps on the whole grid."""
+    N = 4096
+    rng = np.random.default_rng(17 + st)
+    r = rng.standard_normal((N, N)).astype(np.float32)
+    e = rng.standard_normal((N, N)).astype(np.float32)
+    with cj.Plan(N, N, st, 1e-10, precision=cj.CJ_FP32_INNER, inner_cycle=64) as p:
+        kmin, kmax = orc.kappa_bounds(st, N, N)
+        w32 = orc.sweep_coeffs(st, kmin, kmax, 64).astype(np.float32)
+        ed = dev(torch, e)
+        cj.cj_sweeps_f32(p.handle, dev(torch, r), ed, 7, 9)
+        got = ed.cpu().numpy()
+    ref = e
+    for k in range(9):
+        ref = orc.sweep_f32(st, ref, r, w32[(7 + k) % 64])
+    np.testing.assert_array_equal(got, ref)
+
+
 def test_full_size_residual(cj, torch):
     N, st = 4096, 9
     f = workloads.smooth_random_rhs(N, N, 1)
