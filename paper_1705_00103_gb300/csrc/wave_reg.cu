@@ -282,9 +282,12 @@ __global__ void __launch_bounds__(kWrThreads, ST == 17 || (ST == 9 && K == 4) ? 
                 ve = make_float4(sy * ve.x, sy * ve.y, sy * ve.z, sy * ve.w);
                 *pr = make_float4(sy * vr.x, sy * vr.y, sy * vr.z, sy * vr.w);
             }
-            wr_put<R, WC>(win[0][k], ve, edge, ed);
-            // stage s: row yin - s SK from the rows of ages SK - R .. SK + R of its window (the
-            // row of age 0 is the one stage s - 1 produces in this same iteration)
+            // stage s: row yin - s SK from the rows of ages SK - R .. SK + R of its window; the
+            // row of age 0 is the one this iteration produces, so the K stages are computed
+            // first and the new rows (ve and the stages' outputs) enter the windows afterwards
+            float4 nr[K];  // new row of each window: nr[0] = ve, nr[s] = stage s's output
+            nr[0] = ve;
+            float4 ov;     // stage K's output
 #pragma unroll
             for (int s = 1; s <= K; ++s) {
                 const float4 rq = rr[((t - s * SK) & (kWrRRing - 1)) * 32 + lane];
@@ -307,21 +310,32 @@ __global__ void __launch_bounds__(kWrThreads, ST == 17 || (ST == 9 && K == 4) ? 
                         nv[m] = fmaf(wt.w[s - 1], res[m], uc);
                     }
                 }
-                if (s < K) {
-                    wr_put<R, WC>(win[s][k], make_float4(nv[0], nv[1], nv[2], nv[3]), edge, ed);
-                } else {
-                    const int yo = yin - K * SK;
-                    if (out_lane && yo >= y0 && yo <= y1) {
-                        const bool bnd = ST == 17 && (c0 == 1 || c0 + 3 >= Nx || yo == 1 || yo == Ny);
-                        if (c0 + 3 <= Nx && !bnd) {
-                            *reinterpret_cast<float4 *>(out + g.idx(c0, yo)) =
-                                make_float4(nv[0], nv[1], nv[2], nv[3]);
-                        } else {
+                if (s < K)
+                    nr[s] = make_float4(nv[0], nv[1], nv[2], nv[3]);
+                else
+                    ov = make_float4(nv[0], nv[1], nv[2], nv[3]);
+            }
+            // the new rows enter the windows, with the Dirichlet columns under one branch
+            if (edge) {
 #pragma unroll
-                            for (int m = 0; m < 4; ++m)
-                                if (c0 + m <= Nx) store_node<R, float>(out, g, c0 + m, yo, nv[m]);
-                        }
-                    }
+                for (int s = 0; s < K; ++s) nr[s] = wr_edge_own<R>(ed, nr[s]);
+            }
+#pragma unroll
+            for (int s = 0; s < K; ++s) wr_put<R, WC>(win[s][k], nr[s], false, ed);
+            if (edge) {
+#pragma unroll
+                for (int s = 0; s < K; ++s) wr_edge_side<R, WC>(ed, win[s][k]);
+            }
+            const int yo = yin - K * SK;
+            if (out_lane && yo >= y0 && yo <= y1) {
+                const bool bnd = ST == 17 && (c0 == 1 || c0 + 3 >= Nx || yo == 1 || yo == Ny);
+                if (c0 + 3 <= Nx && !bnd) {
+                    *reinterpret_cast<float4 *>(out + g.idx(c0, yo)) = ov;
+                } else {
+                    const float o4[4] = {ov.x, ov.y, ov.z, ov.w};
+#pragma unroll
+                    for (int m = 0; m < 4; ++m)
+                        if (c0 + m <= Nx) store_node<R, float>(out, g, c0 + m, yo, o4[m]);
                 }
             }
         }
