@@ -601,11 +601,12 @@ def test_launch_modes_give_identical_solves(cj, torch, st, method, data):
 
 # ----------------------------------------------------------------- the largest sides
 
+@pytest.mark.parametrize("st", (5, 9))
 @pytest.mark.parametrize("Nx,Ny", [(1 << 20, 1), (1, 1 << 20)])
-def test_largest_side_sweeps_bit_exact(cj, torch, Nx, Ny):
-    """Grids at the largest side the plan accepts (2^20 nodes): FP64 and FP32 sweeps equal the
-    oracle's (a tolerance of 0.5 keeps the cycle within the 2^24-sweep limit)."""
-    st = 9
+def test_largest_side_sweeps_bit_exact(cj, torch, st, Nx, Ny):
+    """Grids at the largest side the plan accepts (2^20 nodes): FP64 sweeps and FP32 sweeps (four
+    per launch by the register wavefront, then one) equal the oracle's (a tolerance of 0.5 keeps
+    the cycle within the 2^24-sweep limit)."""
     f, u0 = rand_problem(Nx, Ny, 4)
     with cj.Plan(Nx, Ny, st, 0.5, launch=cj.CJ_LAUNCH_STREAM) as p:
         w = p.info()["w"]
@@ -616,12 +617,14 @@ def test_largest_side_sweeps_bit_exact(cj, torch, Nx, Ny):
     np.testing.assert_array_equal(ud.cpu().numpy(), ref)
     r = np.random.default_rng(5).standard_normal((Ny, Nx)).astype(np.float32)
     e0 = np.random.default_rng(6).standard_normal((Ny, Nx)).astype(np.float32)
-    with cj.Plan(Nx, Ny, st, 0.5, precision=cj.CJ_FP32_INNER, inner_cycle=4) as p:
+    with cj.Plan(Nx, Ny, st, 0.5, precision=cj.CJ_FP32_INNER, inner_cycle=4, temporal_depth=4) as p:
         kmin, kmax = orc.kappa_bounds(st, Nx, Ny)
         w32 = orc.sweep_coeffs(st, kmin, kmax, 4).astype(np.float32)
         ed = torch.from_numpy(e0).cuda()
-        cj.cj_sweeps_f32(p.handle, torch.from_numpy(r).cuda(), ed, 0, 2)
-    ref32 = orc.sweep_f32(st, orc.sweep_f32(st, e0, r, w32[0]), r, w32[1])
+        cj.cj_sweeps_f32(p.handle, torch.from_numpy(r).cuda(), ed, 0, 5)
+    ref32 = e0
+    for k in range(5):
+        ref32 = orc.sweep_f32(st, ref32, r, w32[k % 4])
     np.testing.assert_array_equal(ed.cpu().numpy(), ref32)
 
 
