@@ -391,11 +391,16 @@ def fp32_sweep_roofline(cj, stream, launches: int = 64) -> dict:
     per_launch = e0.elapsed_time(e1) * 1e-3 / launches
     upd = depth * N_GRID * N_GRID
     achieved = FP32_OPS_PER_UPDATE_WAVE_REG_9 * upd / per_launch / 1e12
+    traffic = traffic_per_launch("sweep_wave_reg_9_d4_4096", WAVE_REG_SOURCES)
     return {"kernel": "sweep_wave_reg_kernel<9,4>", "bound": "alu", "achieved": achieved,
             "peak": FP32_ISSUE_PEAK_TOPS, "unit": "TFP32op/s", "frac": achieved / FP32_ISSUE_PEAK_TOPS,
-            "traffic": traffic_per_launch("sweep_wave_reg_9_d4_4096", WAVE_REG_SOURCES),
+            "traffic": traffic,
             "avg_launch_us": per_launch * 1e6, "sweeps_per_launch": depth,
             "gupdates_s": upd / per_launch / 1e9,
+            # with temporal blocking: DRAM bytes actually moved (ncu traffic per launch) per second
+            # and per update; without it, one sweep per launch moves 12 B per update
+            "dram_gbs_with_temporal_blocking": None if traffic is None else traffic / per_launch / 1e9,
+            "dram_bytes_per_update": None if traffic is None else traffic / upd,
             "hbm_gbs_algorithmic": 12.0 * N_GRID * N_GRID / per_launch / 1e9,
             "peak_note": "FP32 issue peak: 4 schedulers x 32 lanes x 152 SMs x 2.07 GHz; 13.75 FP32 "
                          "instructions per 9-point update in the kernel's shared-difference form"}
