@@ -5,22 +5,27 @@
 // Every warp owns a strip of 128 staged columns (four adjacent columns per lane, loaded and
 // stored as 16-byte vectors) and streams down a block of rows.  Each iteration brings in one
 // input row and advances all K stages by one row: stage s computes row y_in - s (R + 1) from
-// rows y - R .. y + R of stage s-1, which sit in a register window of 2R + 2 rows per stage.
-// The one row of skew beyond the stencil radius makes the K stages of an iteration
-// independent of one another (stage s never reads the row stage s-1 produces in the same
-// iteration), so a warp carries 4K independent node updates per iteration.  The R columns on
-// either side of a lane's four come from the neighbouring lanes by warp shuffles when a row
-// is produced.  The strip's edge columns are garbage after each stage; with H = R K <= 4,
-// lanes 1 .. 30 (120 columns) hold valid results after K stages and are stored.  In y the
-// block's first H output rows are preceded by H warm-up input rows and followed by H more.
+// rows y - R .. y + R of stage s-1, which sit in a register ring of 2R + 2 rows per stage
+// (the loop is unrolled by the ring length, so every ring index is a constant).  The one row
+// of skew beyond the stencil radius makes the K stages of an iteration independent of one
+// another (stage s never reads the row stage s-1 produces in the same iteration): all K are
+// computed first, and their new rows then enter the rings together.  The R columns on either
+// side of a lane's four come from the neighbouring lanes by warp shuffles when a row enters.
+// A strip's two side lanes are garbage after K stages (H = R K <= 4 columns from the edge), so
+// lanes 1 .. 30 (120 columns) are stored; strip 0 starts at column 1 and stores lanes 0 .. 30.
+// In y, a row block's outputs need H input rows before and after it.
 //
-// Boundaries: the stages run on the odd extension of the grid (fold_dev.cuh), so no per-stage
-// ghost refresh is needed and interior results equal one-sweep launches bit for bit; the
-// residual is evaluated in difference form (resid_diff32) with the same operation order.
+// Boundaries: in x, the lanes next to the Dirichlet columns keep them in registers at every
+// stage (column 0 and Nx + 1 at 0; for the 17-point stencil column -1 at -u(1) and Nx + 2 at
+// -u(Nx)), the values the homogeneous boundary gives; lanes past Nx are never read.  In y, the
+// stages run on the odd extension of the grid (fold_dev.cuh): every operation of the sweep is
+// an odd function of its inputs under round-to-nearest, so values on reflected rows stay the
+// exact negatives of their mirrors.  Interior results equal one-sweep launches bit for bit;
+// the residual is evaluated in difference form with resid_diff32's operation order.
 //
-// r(y) is needed by every stage at a different iteration: each lane keeps its own four
-// columns of the last 16 rows of r in a private shared-memory ring (written once, read by each
-// stage; no other lane reads them, so no synchronisation is needed).
+// e and r arrive by cp.async, kWrAhead rows ahead, into lane-private shared-memory rings (each
+// lane reads back only what it copied, so no synchronisation is needed); r(y) is needed by
+// every stage at a different iteration and stays in its ring for 16 rows.
 //
 // HBM traffic per update: about (8 B in + 4 B out) / K, plus the strip's 8-column and the row
 // block's 2H-row overlap with its neighbours.
