@@ -262,8 +262,11 @@ cj_status cj_sweeps(cj_plan *plan, const double *f, long long ld_f, double *u, l
 /*
  * cj_sweeps_f32 -- apply `count` weighted FP32 sweeps e <- e + w32_n (L e - r) in place,
  * w32_n = (float) w_n of the plan's inner cycle (FP32-inner plans only), fused
- * temporal_depth at a time per launch as the solve does (bit-identical to one at a time).
- * r, e: device, Ny x ld floats.  Asynchronous on `stream`.
+ * temporal_depth at a time per launch as the solve does (bit-identical to one at a time):
+ * depths 2-4 (5 and 9 points) and 2 (17 points) by the register wavefront kernel, 8 (and
+ * 17-point 4) by the shared-memory wavefront kernel, 1 by the one-sweep kernel; a remainder
+ * shorter than the depth, or a depth no kernel serves, runs at the largest served depth that
+ * fits.  r, e: device, Ny x ld floats.  Asynchronous on `stream`.
  */
 cj_status cj_sweeps_f32(cj_plan *plan, const float *r, long long ld_r, float *e, long long ld_e,
                         long long first, long long count, void *stream);
