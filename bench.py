@@ -316,6 +316,7 @@ def run_cj(args):
         mclk.start()
         mixed = mixed_paths(cj, rhs_dev[1], stream, results[1])
         mixed["clocks"] = mclk.stop()
+    small = None if args.no_mixed else small_solve(cj, stream)
     launches = sum(r["launches"] for r in results)
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -332,6 +333,7 @@ def run_cj(args):
                     "time_s": r["seconds"]} for r in results[:2]],
         "roofline": roofline, "clocks": clk, "gpu_launches": launches, "e2e": e2e,
         "vs_plain_fp64": mixed,
+        "small_5pt_64": small,
     }
     if rank == 0 and not args.no_cpu:
         out["cpu_baseline"] = cpu_oracle_sample()
@@ -368,6 +370,29 @@ def mixed_paths(cj, f, stream, plain):
                      "speedup_vs_plain_fp64_time": plain["seconds"] / r["seconds"]}
     out["fp32_sweep_roofline"] = fp32_sweep_roofline(cj, stream)
     return out
+
+
+def small_solve(cj, stream, runs: int = 5) -> dict:
+    """The small case (5-point, 64 x 64, FP64, tol 1e-10, the sin*sin right-hand side): time to
+    tolerance of whole cj_solve calls (graph-launched cycles), median of `runs` after 3 warm-up
+    solves; the call blocks until the solve ends, so host time is the time to tolerance."""
+    import torch
+    import workloads
+    N = 64
+    f = torch.from_numpy(workloads.manufactured_rhs(N, N)).cuda()
+    times, res = [], None
+    with cj.Plan(N, N, 5, TOL) as p:
+        u = torch.zeros_like(f)
+        for k in range(3 + runs):
+            u.zero_()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            res = cj.cj_solve(p.handle, f, u, stream)
+            torch.cuda.synchronize()
+            if k >= 3:
+                times.append(time.perf_counter() - t0)
+    return {"us_to_tol_median": statistics.median(times) * 1e6, "sweeps": res["sweeps"],
+            "rel_res_l2": res["rel_res_l2"], "status": cj.cj_status_string(res["rc"]), "runs": runs}
 
 
 def fp32_sweep_roofline(cj, stream, launches: int = 64) -> dict:
