@@ -187,8 +187,8 @@ __host__ __device__ __forceinline__ int wr_strip_x0(int x) { return x == 0 ? 1 :
 
 __host__ __device__ __forceinline__ int wr_strips(int Nx) { return Nx <= 124 ? 1 : 1 + (Nx - 124 + 119) / 120; }
 
-// Registers: the 9-point depth-4 kernel carries 237 (windows and pair differences of four
-// stages), so it runs 2 blocks per SM; 3 blocks (12 warps, 168 registers each, as the register
+// Registers: the 9-point depth-4 kernel carries about 240 (windows and pair differences of
+// four stages), so it runs 2 blocks per SM; 3 blocks (12 warps, 168 registers each, as the register
 // file is split between the SM's four schedulers) would spill.
 template <int ST, int K>
 __global__ void __launch_bounds__(kWrThreads, ST == 17 || (ST == 9 && K == 4) ? 2 : 3)
