@@ -2,6 +2,7 @@
 
     python -m paper_1705_00103_gb300.profile_sweeps --stencil 9 --n 4096 --precision fp64 --count 3
     python -m paper_1705_00103_gb300.profile_sweeps --stencil 9 --precision fp32 --depth 8 --count 16
+    python -m paper_1705_00103_gb300.profile_sweeps --stencil 9 --n 4096 --solve fp32_inner_dd
 
 Inputs are zero grids of the given size (the sweep's cost does not depend on the values);
 three FP64 grids of 4096^2 (400 MB) exceed the 129 MB L2.
@@ -24,8 +25,23 @@ def main(argv=None):
     ap.add_argument("--depth", type=int, default=1, help="FP32 sweeps per launch (temporal blocking)")
     ap.add_argument("--time", type=int, default=0,
                     help="also time this many sweeps with CUDA events and print us per sweep")
+    ap.add_argument("--solve", default="", choices=["", "fp32_inner", "fp32_inner_dd"],
+                    help="instead of sweeps, one mixed-precision solve of the smooth random RHS "
+                         "(seed 2) to a relative residual of 1e-10, at the default temporal depth")
     a = ap.parse_args(argv)
     build.build()
+    if a.solve:
+        import workloads
+        prec = cj.CJ_FP32_INNER if a.solve == "fp32_inner" else cj.CJ_FP32_INNER_DD
+        f = torch.from_numpy(workloads.smooth_random_rhs(a.n, a.n, 2)).cuda()
+        with cj.Plan(a.n, a.n, a.stencil, 1e-10, precision=prec) as p:
+            u = torch.zeros_like(f)
+            res = cj.cj_solve(p.handle, f, u)
+        torch.cuda.synchronize()
+        print("%s solve %dx%d stencil %d: %d FP32 sweeps, %d outer steps, rel residual %.3e, %.3f s"
+              % (a.solve, a.n, a.n, a.stencil, res["sweeps"], res["cycles"], res["rel_res_l2"], res["seconds"]))
+        print("ok")
+        return
 
     def run(fn):
         fn(a.count)
