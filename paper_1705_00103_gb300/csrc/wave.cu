@@ -1,5 +1,7 @@
 // Wavefront temporal blocking of the FP32 inner sweep (sm_103a): K consecutive weighted
-// sweeps e <- e + w_n (L e - r) per HBM round trip, each with its own weight.
+// sweeps e <- e + w_n (L e - r) per HBM round trip, each with its own weight.  The register
+// wavefront (wave_reg.cu) serves depths 2-4 of the 5- and 9-point stencils and depth 2 of the
+// 17-point one; this kernel serves depth 8 and the 17-point depth 4.
 //
 // A block of kWaveW threads owns a strip of kWaveW staged columns (one per thread: kWaveW - 2H output
 // columns plus an x-halo of H = r K on each side, r = stencil radius) and streams down a
