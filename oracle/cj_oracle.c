@@ -35,10 +35,11 @@
  *      before every cycle; u0 = 0 unless given.  If ||b|| = 0 the absolute norm is used.
  *      rho cannot fall below the rounding floor of an FP64 u, about
  *      fl = eps * S * ||u||_2 / ||b||_2 (eps = 2^-53, S = sum of |coefficients|), which is
- *      ~5e-10 for the 9-point stencil on 4096^2; so the solve also stops, with the status
- *      "floor", once rho <= 4 fl, or once `patience` consecutive cycles each failed to
- *      halve rho (patience 1 for plain CJM cycles; 2 for the defect-correction loop of
- *      R10, whose residual may jump up once before contracting).
+ *      ~5e-10 for the 9-point stencil on 4096^2; so the solve also stops: with the status
+ *      "floor" once rho <= 4 fl, and with the status "stalled" once `patience`
+ *      consecutive cycles each failed to halve rho while it is still above 4 fl
+ *      (patience 1 for plain CJM cycles; 2 for the defect-correction loop of R10, whose
+ *      residual may jump up once before contracting).
  *   R9 evaluation order of the residual L u - b (any order is exact in real arithmetic):
  *      horizontal pair sums p = u(i-1,.) + u(i+1,.), P = u(i-2,.) + u(i+2,.), vertical
  *      pair sums v1 = u(i,j-1) + u(i,j+1), v2 = u(i,j-2) + u(i,j+2); axis groups
@@ -66,6 +67,9 @@
  *      M sweeps (see orc_solve_jacobi).
  *   R19 position-dependent coefficient masks (Sec. 3.2): the Jacobi-normalised sweep with the
  *      caller's eigenvalue bounds (see orc_solve_mask).
+ *   R20 FP64 inner cycles (not in the paper): R11's double-FP64 outer loop with the inner
+ *      cycle run by the plain FP64 sweep of R9 on L e = r, r = -R in FP64 (see
+ *      orc_solve_fp64_dd) -- the all-FP64 way to a residual below one array's FP64 floor.
  *
  * Array convention: interior values only, row-major [Ny][Nx], value of node (i, j) at
  * u[(j-1)*Nx + (i-1)].  Compiled with -ffp-contract=off so that every rounding is the
@@ -271,8 +275,11 @@ double orc_abs_coeff_sum(int st) {
     return 640.0 / 72.0;
 }
 
-/* Stop statuses of the solves (reading R8). */
-enum { ORC_CONVERGED = 0, ORC_FLOOR = 1, ORC_MAX_SWEEPS = 2, ORC_DIVERGED = 3 };
+/* Stop statuses of the solves (reading R8).  "floor" means the residual reached the FP64
+ * rounding floor of the solution array (rho <= 4 fl); "stalled" means it stopped falling while
+ * still above that floor (a cycle's own rounding, amplified by its partial products, or a goal
+ * the iteration cannot reach), so the two are told apart. */
+enum { ORC_CONVERGED = 0, ORC_FLOOR = 1, ORC_MAX_SWEEPS = 2, ORC_DIVERGED = 3, ORC_STALLED = 4 };
 
 /* Decide after a residual evaluation whether to stop; returns -1 to continue.  *stall
  * counts consecutive cycles that failed to halve rho. */
@@ -283,7 +290,7 @@ static int stop_rule(double rho, double floor_est, double rho_prev, long done_cy
     if (rho <= 4.0 * floor_est) return ORC_FLOOR;
     if (done_cycles > 0) {
         *stall = rho > 0.5 * rho_prev ? *stall + 1 : 0;
-        if (*stall >= patience) return ORC_FLOOR;
+        if (*stall >= patience) return ORC_STALLED;
     }
     return -1;
 }
@@ -292,7 +299,7 @@ static int stop_rule(double rho, double floor_est, double rho_prev, long done_cy
  * and the result on exit.  The residual is tested before every cycle; a cycle is M
  * sweeps with the weights in the order of R3.  Returns the number of sweeps done, or
  * -1 on a bad argument.  *cycles, *rel_l2, *rel_linf describe the returned u; *status
- * is one of ORC_CONVERGED, ORC_FLOOR, ORC_MAX_SWEEPS, ORC_DIVERGED. */
+ * is one of ORC_CONVERGED, ORC_FLOOR, ORC_MAX_SWEEPS, ORC_DIVERGED, ORC_STALLED. */
 long orc_solve(int st, int Nx, int Ny, const double *f, double tol, long max_sweeps,
                double *u, double *rel_l2, double *rel_linf, long *cycles, int *status) {
     if (Nx < 1 || Ny < 1 || !(tol > 0.0 && tol < 1.0)) return -1;
@@ -617,11 +624,17 @@ void orc_residual_dd(int st, int Nx, int Ny, const double *uh, const double *ul,
 
 /* Mixed-precision CJM with the double-FP64 outer loop (reading R11).  u: initial guess in
  * (taken as u_hi, u_lo = 0), u_hi + u_lo rounded to FP64 out; u_lo_out (may be NULL)
- * receives u_lo.  Returns the FP32 sweeps done or -1; *outer, *status as orc_solve_mixed;
- * the floor estimate uses 2^-106 in place of 2^-53. */
+ * receives u_lo.  Returns the inner sweeps done or -1; *outer, *status as orc_solve_mixed;
+ * the floor estimate uses 2^-106 in place of 2^-53.
+ * inner64 = 0: the inner cycle runs in FP32 (R10's cycle on rt = (float)(-R)).
+ * inner64 = 1 (reading R20): the inner cycle runs in FP64 -- orc_sweep, the plain FP64 sweep
+ * of R9 with the homogeneous boundary of R6, on L e = r with r = -R kept in FP64 and the FP64
+ * weights of a cycle of length M_in -- so every operation of the solve is FP64 or the
+ * error-free double-FP64 defect and correction: the FP64-arithmetic path to a residual below
+ * the FP64 floor of one solution array. */
 static long solve_mixed_dd_g(int st, int Nx, int Ny, const double *f, const double *G, double tol,
                              long M_in, long max_outer, double *u, double *u_lo_out, double *rel_l2,
-                             double *rel_linf, long *outer, int *status, err_stop *es) {
+                             double *rel_linf, long *outer, int *status, err_stop *es, int inner64) {
     if (Nx < 1 || Ny < 1 || !(tol > 0.0 && tol < 1.0) || M_in < 1) return -1;
     size_t n = (size_t)Nx * (size_t)Ny;
     double *G0 = G ? (double *)calloc((size_t)(Nx + 4) * (size_t)(Ny + 4), sizeof(double)) : NULL;
@@ -637,6 +650,9 @@ static long solve_mixed_dd_g(int st, int Nx, int Ny, const double *f, const doub
     float *rt = (float *)malloc(sizeof(float) * n);
     float *e = (float *)malloc(sizeof(float) * n);
     float *e2 = (float *)malloc(sizeof(float) * n);
+    double *r64 = inner64 ? (double *)malloc(sizeof(double) * n) : NULL;
+    double *e64 = inner64 ? (double *)malloc(sizeof(double) * n) : NULL;
+    double *e64b = inner64 ? (double *)malloc(sizeof(double) * n) : NULL;
     orc_scale_rhs(Nx, Ny, f, b);
     double bsq = 0.0, bmax = 0.0;
     for (size_t k = 0; k < n; ++k) {
@@ -655,6 +671,7 @@ static long solve_mixed_dd_g(int st, int Nx, int Ny, const double *f, const doub
             if (fabs(R[k]) > mx) mx = fabs(R[k]);
             usq += u[k] * u[k];
             rt[k] = (float)(-R[k]);
+            if (inner64) r64[k] = -R[k];
         }
         rl2 = bn > 0.0 ? sqrt(sq) / bn : sqrt(sq);
         rinf = bmax > 0.0 ? mx / bmax : mx;
@@ -663,14 +680,22 @@ static long solve_mixed_dd_g(int st, int Nx, int Ny, const double *f, const doub
         if (stat >= 0) break;
         if (out >= max_outer) { stat = ORC_MAX_SWEEPS; break; }
         prev = rl2;
-        memset(e, 0, sizeof(float) * n);
-        for (long s = 0; s < M_in; ++s) {
-            orc_sweep_f32(st, Nx, Ny, e, rt, w32[s], e2);
-            memcpy(e, e2, sizeof(float) * n);
+        if (inner64) {
+            memset(e64, 0, sizeof(double) * n);
+            for (long s = 0; s < M_in; ++s) {
+                orc_sweep(st, Nx, Ny, e64, r64, w[s], e64b);
+                memcpy(e64, e64b, sizeof(double) * n);
+            }
+        } else {
+            memset(e, 0, sizeof(float) * n);
+            for (long s = 0; s < M_in; ++s) {
+                orc_sweep_f32(st, Nx, Ny, e, rt, w32[s], e2);
+                memcpy(e, e2, sizeof(float) * n);
+            }
         }
         for (size_t k = 0; k < n; ++k) {
             double hi, err;
-            two_sum(u[k], (double)e[k], &hi, &err);
+            two_sum(u[k], inner64 ? e64[k] : (double)e[k], &hi, &err);
             double lo = ul[k] + err;
             two_sum(hi, lo, &u[k], &ul[k]);
         }
@@ -679,6 +704,7 @@ static long solve_mixed_dd_g(int st, int Nx, int Ny, const double *f, const doub
     }
     if (u_lo_out) memcpy(u_lo_out, ul, sizeof(double) * n);
     free(w); free(w32); free(b); free(ul); free(R); free(rt); free(e); free(e2); free(G0);
+    free(r64); free(e64); free(e64b);
     *rel_l2 = rl2;
     *rel_linf = rinf;
     *outer = out;
@@ -690,7 +716,16 @@ long orc_solve_mixed_dd(int st, int Nx, int Ny, const double *f, double tol, lon
                         long max_outer, double *u, double *u_lo_out, double *rel_l2,
                         double *rel_linf, long *outer, int *status) {
     return solve_mixed_dd_g(st, Nx, Ny, f, NULL, tol, M_in, max_outer, u, u_lo_out, rel_l2, rel_linf,
-                            outer, status, NULL);
+                            outer, status, NULL, 0);
+}
+
+/* FP64 inner cycles in the double-FP64 outer loop (reading R20); G: Dirichlet data (R15) or
+ * NULL (R6).  Arguments and results as orc_solve_mixed_dd; the count returned is FP64 sweeps. */
+long orc_solve_fp64_dd(int st, int Nx, int Ny, const double *f, const double *G, double tol, long M_in,
+                       long max_outer, double *u, double *u_lo_out, double *rel_l2, double *rel_linf,
+                       long *outer, int *status) {
+    return solve_mixed_dd_g(st, Nx, Ny, f, G, tol, M_in, max_outer, u, u_lo_out, rel_l2, rel_linf,
+                            outer, status, NULL, 1);
 }
 
 /* The double-FP64 form with Dirichlet data G (R15 with R11): u_hi's ghosts are the data, u_lo's
@@ -699,7 +734,7 @@ long orc_solve_mixed_dd_bc(int st, int Nx, int Ny, const double *f, const double
                            long M_in, long max_outer, double *u, double *u_lo_out, double *rel_l2,
                            double *rel_linf, long *outer, int *status) {
     return solve_mixed_dd_g(st, Nx, Ny, f, G, tol, M_in, max_outer, u, u_lo_out, rel_l2, rel_linf,
-                            outer, status, NULL);
+                            outer, status, NULL, 0);
 }
 
 /* ---------------------------------------------------------------- non-homogeneous Dirichlet */
@@ -826,9 +861,9 @@ double orc_real_error(int Nx, int Ny, const double *u, const double *u_exact) {
  * the cycle length comes from `tol` as in orc_solve; the real error E is tested before every
  * cycle and, when check_every > 0, after every check_every sweeps inside a cycle.  Stops with
  * converged at the first test where E <= err_tol.  The residual of R8 is still evaluated before
- * every cycle, only for the floor part of the stop rule (a residual at the FP64 floor, or a
- * cycle that failed to halve it, ends the solve with "floor": the real error cannot fall
- * further, e.g. when err_tol is below the discretisation error).  E = NaN ends it with
+ * every cycle, only for the floor and stall parts of the stop rule (a residual at the FP64
+ * floor ends the solve with "floor", a cycle that failed to halve it with "stalled": the real
+ * error cannot fall further, e.g. when err_tol is below the discretisation error).  E = NaN ends it with
  * "diverged".  G = NULL: homogeneous Dirichlet (R6); else the Dirichlet data of R15.
  * hist[2k], hist[2k+1] = sweeps done and E at the k-th test (up to cap tests; *count = all). */
 long orc_solve_to_error(int st, int Nx, int Ny, const double *f, const double *G,
@@ -910,9 +945,9 @@ long orc_solve_to_error(int st, int Nx, int Ny, const double *f, const double *G
 
 /* Classical Jacobi (omega = 1, the paper's comparison method, Sec. 3.4 and Table 1), reading
  * R18: every sweep uses w = 1/c; the residual of R8 is tested every M sweeps, M the CJM cycle
- * length of the same tolerance (R2); stops converged at rho <= tol, "floor" at rho <= 4 fl or
- * when an interval of M sweeps did not lower rho (Jacobi's residual falls monotonically in
- * exact arithmetic), "diverged" on a non-finite rho.  G = NULL: homogeneous Dirichlet (R6);
+ * length of the same tolerance (R2); stops converged at rho <= tol, "floor" at rho <= 4 fl,
+ * "stalled" when an interval of M sweeps did not lower rho (Jacobi's residual falls
+ * monotonically in exact arithmetic), "diverged" on a non-finite rho.  G = NULL: homogeneous Dirichlet (R6);
  * else the Dirichlet data of R15.  *intervals = the M-sweep intervals done. */
 long orc_solve_jacobi(int st, int Nx, int Ny, const double *f, const double *G, double tol,
                       long max_sweeps, double *u, double *rel_l2, double *rel_linf,
@@ -945,7 +980,8 @@ long orc_solve_jacobi(int st, int Nx, int Ny, const double *f, const double *G, 
         double fl = bn > 0.0 ? eps * S * sqrt(usq) / bn : eps * S * sqrt(usq);
         if (rl2 <= tol) { stat = ORC_CONVERGED; break; }
         if (!(rl2 == rl2) || rl2 > 1e300) { stat = ORC_DIVERGED; break; }
-        if (rl2 <= 4.0 * fl || (done > 0 && rl2 >= prev)) { stat = ORC_FLOOR; break; }
+        if (rl2 <= 4.0 * fl) { stat = ORC_FLOOR; break; }
+        if (done > 0 && rl2 >= prev) { stat = ORC_STALLED; break; }
         if (sweeps + M > max_sweeps) { stat = ORC_MAX_SWEEPS; break; }
         for (long s = 0; s < M; ++s) {
             if (G) orc_sweep_bc(st, Nx, Ny, u, G, b, w, v);
@@ -1117,7 +1153,8 @@ long orc_solve_mask(int pat, int Nx, int Ny, const double *f, const double *coef
         if (method == 1) {
             if (rl2 <= tol) stat = ORC_CONVERGED;
             else if (!(rl2 == rl2) || rl2 > 1e300) stat = ORC_DIVERGED;
-            else if (rl2 <= 4.0 * fl || (cyc > 0 && rl2 >= prev)) stat = ORC_FLOOR;
+            else if (rl2 <= 4.0 * fl) stat = ORC_FLOOR;
+            else if (cyc > 0 && rl2 >= prev) stat = ORC_STALLED;
             else stat = -1;
         } else {
             stat = stop_rule(rl2, fl, prev, cyc, tol, 1, &stall);
@@ -1140,10 +1177,11 @@ long orc_solve_mask(int pat, int Nx, int Ny, const double *f, const double *coef
     return sweeps;
 }
 
-/* Defect correction (R10, or R11 with dd) stopped by the real error (R16): u_hi - u_exact in the
- * infinity norm, tested at every outer step after the defect, stops the solve at <= err_goal;
- * the residual's floor and stall parts of R8 still end it ("floor").  G: Dirichlet data (R15) or
- * NULL.  hist[2k], hist[2k+1] = FP32 sweeps done and E at the k-th test (cap tests; *count = all). */
+/* Defect correction (R10; R11 with dd = 1; R20, FP64 inner cycles, with dd = 2) stopped by the
+ * real error (R16): u_hi - u_exact in the infinity norm, tested at every outer step after the
+ * defect, stops the solve at <= err_goal; the residual's floor and stall parts of R8 still end it
+ * ("floor" / "stalled").  G: Dirichlet data (R15) or NULL.  hist[2k], hist[2k+1] = inner sweeps
+ * done and E at the k-th test (cap tests; *count = all). */
 long orc_solve_mixed_to_error(int st, int Nx, int Ny, const double *f, const double *G,
                               const double *u_exact, double err_goal, long M_in, int dd, long max_outer,
                               double *u, double *u_lo_out, double *hist, long cap, long *count,
@@ -1152,7 +1190,7 @@ long orc_solve_mixed_to_error(int st, int Nx, int Ny, const double *f, const dou
     err_stop es = {u_exact, err_goal, hist, cap, 0, 0.0};
     double rinf;
     long n = dd ? solve_mixed_dd_g(st, Nx, Ny, f, G, 0.5, M_in, max_outer, u, u_lo_out, rel_l2, &rinf, outer,
-                                   status, &es)
+                                   status, &es, dd == 2)
                 : solve_mixed_g(st, Nx, Ny, f, G, 0.5, M_in, max_outer, u, rel_l2, &rinf, outer, status, &es);
     *count = es.count;
     *err = es.err;

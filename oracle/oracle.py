@@ -118,6 +118,9 @@ def lib():
         L.orc_solve_mixed_dd_bc.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, _dp, _dp, ctypes.c_double,
                                             ctypes.c_long, ctypes.c_long, _dp, _dp, _dp, _dp, _lp, _ip]
         L.orc_solve_mixed_dd_bc.restype = ctypes.c_long
+        L.orc_solve_fp64_dd.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, _dp, _dp, ctypes.c_double,
+                                        ctypes.c_long, ctypes.c_long, _dp, _dp, _dp, _dp, _lp, _ip]
+        L.orc_solve_fp64_dd.restype = ctypes.c_long
         _lib = L
     return _lib
 
@@ -217,7 +220,7 @@ def scale_rhs(f: np.ndarray) -> np.ndarray:
     return b
 
 
-STATUS = {0: "converged", 1: "floor", 2: "max_sweeps", 3: "diverged"}
+STATUS = {0: "converged", 1: "floor", 2: "max_sweeps", 3: "diverged", 4: "stalled"}
 
 
 def abs_coeff_sum(st: int) -> float:
@@ -303,6 +306,25 @@ def solve_mixed_dd(st: int, f: np.ndarray, tol: float, M_in: int, u0: np.ndarray
         n = lib().orc_solve_mixed_dd_bc(st, f.shape[1], f.shape[0], _d(f), _d(_grid(G)), tol, M_in,
                                         max_outer, _d(u), _d(ulo), ctypes.byref(rl2), ctypes.byref(rinf),
                                         ctypes.byref(outer), ctypes.byref(stat))
+    if n < 0:
+        raise ValueError("bad argument")
+    return dict(u=u, u_lo=ulo, sweeps=n, outer=outer.value, rel_l2=rl2.value, rel_linf=rinf.value,
+                status=STATUS[stat.value], converged=stat.value == 0)
+
+
+def solve_fp64_dd(st: int, f: np.ndarray, tol: float, M_in: int, u0: np.ndarray | None = None,
+                  max_outer: int = 1000, G: np.ndarray | None = None) -> dict:
+    """FP64-inner CJM cycles of length M_in inside the double-FP64 defect-correction loop
+    (reading R20; with Dirichlet data G, see ghost_ring); returns u = fl(u_hi + u_lo), u_lo and
+    the FP64 sweeps done."""
+    f = _grid(f)
+    u = np.zeros_like(f) if u0 is None else _grid(u0).copy()
+    ulo = np.zeros_like(f)
+    rl2, rinf = ctypes.c_double(), ctypes.c_double()
+    outer, stat = ctypes.c_long(), ctypes.c_int()
+    n = lib().orc_solve_fp64_dd(st, f.shape[1], f.shape[0], _d(f), None if G is None else _d(_grid(G)), tol,
+                                M_in, max_outer, _d(u), _d(ulo), ctypes.byref(rl2), ctypes.byref(rinf),
+                                ctypes.byref(outer), ctypes.byref(stat))
     if n < 0:
         raise ValueError("bad argument")
     return dict(u=u, u_lo=ulo, sweeps=n, outer=outer.value, rel_l2=rl2.value, rel_linf=rinf.value,
@@ -479,10 +501,11 @@ def solve_mask(pat: int, f: np.ndarray, coef: np.ndarray, kmin: float, kmax: flo
 
 
 def solve_mixed_to_error(st: int, f: np.ndarray, u_exact: np.ndarray, err_goal: float, M_in: int,
-                         dd: bool = False, G: np.ndarray | None = None, max_outer: int = 1000,
+                         dd: int = 0, G: np.ndarray | None = None, max_outer: int = 1000,
                          cap: int = 4096) -> dict:
-    """Defect correction (FP32 inner cycles, FP64 or double-FP64 outer) stopped by the real error
-    at the outer steps (orc_solve_mixed_to_error)."""
+    """Defect correction stopped by the real error at the outer steps (orc_solve_mixed_to_error):
+    dd = 0 FP32 inner cycles in FP64 outer steps, 1 (or True) FP32 inner cycles in double-FP64
+    outer steps, 2 FP64 inner cycles in double-FP64 outer steps."""
     f, ue = _grid(f), _grid(u_exact)
     u, ulo = np.zeros_like(f), np.zeros_like(f)
     hist = np.zeros(2 * cap)
