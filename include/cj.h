@@ -39,8 +39,16 @@ extern "C" {
 
 typedef enum {
     CJ_OK = 0,                /* solve converged: relative residual <= tol */
-    CJ_FLOOR = 1,             /* solve stopped at the FP64 rounding floor (see cj_result) */
+    CJ_FLOOR = 1,             /* solve stopped at the FP64 rounding floor: relative residual
+                                 <= 4 x cj_result.floor_est */
     CJ_PENDING = 2,           /* reserved for asynchronous requests: not finished yet */
+    CJ_STALLED = 3,           /* solve stopped because the residual stopped falling while still
+                                 above 4 x floor_est: a cycle failed to halve it (two outer
+                                 steps in a row for defect correction; an interval that did not
+                                 lower it for CJ_JACOBI).  For plain FP64 cycles on large grids
+                                 this is the cycle's own rounding, amplified by the partial
+                                 products of its weights; a defect-correction precision reaches
+                                 lower residuals */
     CJ_ERR_INVALID_ARG = -1,  /* a size, pointer, stencil, tolerance or option is invalid */
     CJ_ERR_NOMEM = -2,        /* a device or host allocation failed */
     CJ_ERR_NOT_CONVERGED = -3,/* the sweep budget ran out first */
@@ -63,10 +71,15 @@ typedef enum {
 typedef enum {
     CJ_FP64 = 0,          /* plain CJM: every sweep in FP64 */
     CJ_FP32_INNER = 1,    /* FP32 inner CJM cycles inside an FP64 defect-correction loop */
-    CJ_FP32_INNER_DD = 2  /* FP32 inner CJM cycles inside a double-FP64 defect-correction
+    CJ_FP32_INNER_DD = 2, /* FP32 inner CJM cycles inside a double-FP64 defect-correction
                              loop: the solution is u_hi + u_lo and the defect is evaluated
                              to about twice FP64 precision, so the relative residual can go
                              below the FP64 floor (see cj_result.floor_est) */
+    CJ_FP64_INNER_DD = 3  /* FP64 inner CJM cycles inside the same double-FP64 loop: every
+                             sweep is the plain FP64 sweep (on the error equation L e = r,
+                             r = b - L u in FP64), so this is the all-FP64 way to tolerances
+                             below one FP64 array's floor, where plain cycles stall; the
+                             baseline the FP32-inner precisions are compared with */
 } cj_precision;
 
 typedef enum {
@@ -74,7 +87,7 @@ typedef enum {
                        residual tests */
     CJ_JACOBI = 1   /* classical Jacobi (omega = 1 at every sweep), the paper's comparison
                        method (Sec. 3.4, Table 1); the residual is tested every M sweeps, M the
-                       CJM cycle length of the same tolerance; it stops at the floor when an
+                       CJM cycle length of the same tolerance; it stops (CJ_STALLED) when an
                        interval does not lower the residual.  CJ_FP64 only */
 } cj_method;
 
@@ -83,7 +96,8 @@ typedef struct {
     int precision;          /* cj_precision (default CJ_FP64) */
     int literal_n;          /* 1: use the paper-literal N = Nx in the kappa formulas instead
                                of the exact N = Nx + 1 (ablation only) */
-    int inner_cycle;        /* FP32-inner modes: inner cycle length (a power of two); 0 = auto */
+    int inner_cycle;        /* defect-correction modes: inner cycle length (a power of two);
+                               0 = auto (the planner's choice for FP32 or FP64 inner sweeps) */
     int temporal_depth;     /* FP32-inner modes: sweeps fused per HBM round trip (temporal
                                blocking), 1..8; 0 = auto: the depth cj_autotune_depth
                                recorded for this stencil and size class, else 4 for the
@@ -103,7 +117,8 @@ typedef struct {
  * when b = 0); floor_est = 2^-53 * S * ||u||_2 / ||b||_2 is the FP64 rounding floor that
  * rel_res_l2 cannot go below (S = sum of the stencil's absolute coefficients). */
 typedef struct {
-    long long sweeps;       /* weighted sweeps applied (FP32 ones for CJ_FP32_INNER) */
+    long long sweeps;       /* weighted sweeps applied (the inner cycles' sweeps for the
+                               defect-correction precisions) */
     int cycles;             /* CJM cycles (or outer defect-correction steps) */
     int status;             /* the cj_status the solve returned */
     double rel_res_l2;
@@ -188,7 +203,7 @@ void cj_plan_destroy(cj_plan *plan);
  *   *w      host array of M per-sweep coefficients w_n = omega_n / c in application order
  *           (owned by the plan, valid until cj_plan_destroy);
  *   *M      cycle length; *kmin, *kmax eigenvalue bounds of D^-1 A;
- *   *M_inner inner cycle length for CJ_FP32_INNER (0 otherwise).
+ *   *M_inner inner cycle length of the defect-correction precisions (0 for CJ_FP64).
  */
 cj_status cj_plan_info(const cj_plan *plan, const double **w, long long *M, double *kmin,
                        double *kmax, long long *M_inner);
@@ -199,8 +214,9 @@ cj_status cj_plan_info(const cj_plan *plan, const double **w, long long *M, doub
  *   u: device, Ny x ld_u doubles; in: initial guess, out: the solution.
  * Runs the cycles on `stream`; the residual is tested on the host before each cycle,
  * so the call blocks until the solve ends.  Stops with CJ_OK when the relative
- * residual <= tol, CJ_FLOOR when it cannot fall further in FP64 (<= 4 x floor_est, or
- * one plain cycle -- two consecutive CJ_FP32_INNER outer steps -- failed to halve it),
+ * residual <= tol, CJ_FLOOR when it is within 4 x floor_est of the rounding floor of the
+ * solution's representation, CJ_STALLED when it stopped falling above that (one plain cycle --
+ * two consecutive outer steps of a defect-correction precision -- failed to halve it),
  * CJ_ERR_NOT_CONVERGED when the sweep budget is spent,
  * CJ_ERR_DIVERGED on a non-finite residual.  *res (may be NULL) describes the run.
  */
@@ -225,14 +241,14 @@ cj_status cj_solve_history(cj_plan *plan, const double *f, long long ld_f, doubl
  *   err_tol: the real-error goal (>= 0).
  *   check_every: the real error is tested before every cycle and, when > 0, after every
  *     check_every sweeps inside a cycle (0: at cycle ends only); the plan's tolerance sets
- *     only the cycle length M.  For CJ_FP32_INNER and CJ_FP32_INNER_DD plans the error of u
- *     (u_hi) is tested at every outer step, after its defect; check_every must be 0 and
- *     history counts FP32 sweeps.
+ *     only the cycle length M.  For the defect-correction precisions the error of u (u_hi)
+ *     is tested at every outer step, after its defect; check_every must be 0 and history
+ *     counts inner sweeps.
  *   history: host array of 2*cap doubles (may be NULL when cap = 0) receiving (sweeps done,
  *     real error) at every test; *count (may be NULL) = number of tests made (may exceed cap).
  *   *real_error (may be NULL): the real error at the last test.
- * Returns CJ_OK when the goal is met; CJ_FLOOR when the residual, still evaluated before every
- * cycle, stalls first (a goal below the discretisation error); CJ_ERR_NOT_CONVERGED when the
+ * Returns CJ_OK when the goal is met; CJ_FLOOR or CJ_STALLED when the residual, still evaluated
+ * before every cycle, reaches its floor or stalls first (a goal below the discretisation error); CJ_ERR_NOT_CONVERGED when the
  * sweep budget is spent; CJ_ERR_DIVERGED on a non-finite error; CJ_ERR_INVALID_ARG for a
  * classical-Jacobi plan, a NULL u_exact, ld_exact < Nx, err_tol < 0, check_every < 0, or a
  * nonzero check_every on a defect-correction plan.
@@ -295,7 +311,7 @@ cj_status cj_autotune_depth(int Nx, int Ny, cj_stencil st, int sweeps, void *str
                             double *gupd);
 
 /*
- * cj_solution_lo -- for a CJ_FP32_INNER_DD plan, the low part u_lo of the last solve's
+ * cj_solution_lo -- for a CJ_FP32_INNER_DD or CJ_FP64_INNER_DD plan, the low part u_lo of the last solve's
  * double-FP64 solution (cj_solve returned u = u_hi, with |u_lo| <= ulp(u_hi)/2); the
  * relative residual cj_result reported is that of u_hi + u_lo.  u_lo: device, Ny x ld
  * doubles.  Asynchronous on `stream`.  CJ_ERR_INVALID_ARG for other plans.
@@ -372,12 +388,15 @@ typedef struct {
 cj_status cj_autotune_engine(int Nx, int Ny, cj_stencil st, int *tile_rows, int *depth, double *gupd);
 
 /*
- * cj_server_create -- a request loop with continuous batching on the current device: a
- * worker thread admits submitted problems, in arrival order, into free engine slots while
- * their device footprint (FP64 u, b [, u_lo], FP32 e, e', r, weights; 28-36 bytes per
- * node) fits in hbm_budget_bytes; admitted problems join the running engine between graph
- * replays and leave it as each one finishes, so requests arriving while others run overlap
- * with them on the device.
+ * cj_server_create -- a request loop with continuous batching on the current device.  Requests
+ * are sorted into three size lanes (up to 2^20 nodes, up to 2^23, larger); each lane is an engine
+ * with up to max_slots slots, its own stream (smaller lanes at higher stream priority) and its
+ * own worker thread, which admits the lane's requests, in arrival order, into free slots while
+ * their device footprint (FP64 u, b [, u_lo], FP32 e, e', r, weights; 28-36 bytes per node) fits
+ * in hbm_budget_bytes (one budget shared by the lanes); admitted problems join the lane's running
+ * engine between graph replays and leave it as each one finishes, so requests arriving while
+ * others run overlap with them on the device, and a small request's replays sweep only small
+ * grids: its latency follows its own work, not that of the largest grids being solved.
  */
 cj_status cj_server_create(size_t hbm_budget_bytes, int max_slots, cj_server **out);
 
@@ -392,8 +411,10 @@ cj_status cj_submit(cj_server *server, int Nx, int Ny, cj_stencil st, double tol
 
 /*
  * cj_poll -- CJ_PENDING while the request is queued or running; otherwise its final status,
- * with the solution copied to u_host (Ny x Nx, may be NULL) and *res filled (res->seconds =
- * latency from submit to result ready).  A finished ticket can be polled once.
+ * with the solution copied to u_host (Ny x Nx, may be NULL) and *res filled: res->seconds =
+ * latency from submit to result ready, res->sweep_seconds = service time from admission into a
+ * slot to result ready (the rest of the latency is the wait in the lane's queue).  A finished
+ * ticket can be polled once.
  */
 cj_status cj_poll(cj_server *server, uint64_t ticket, double *u_host, cj_result *res);
 
@@ -404,16 +425,19 @@ cj_status cj_server_stats(cj_server *server, cj_server_stats_t *out);
 void cj_server_destroy(cj_server *server);
 
 /*
- * cj_residual_noalloc -- the relative residual norms of cj_residual, for callers that
- * cannot allocate device memory: for example code running under a framework whose caching
+ * cj_residual_noalloc -- the relative residual norms of cj_residual for a homogeneous-Dirichlet
+ * problem (those of a CJ_BC_DIRICHLET0 plan: zero boundary nodes, odd reflection for the
+ * 17-point stencil's second ring; no boundary data is read), for callers that cannot allocate
+ * device memory: for example code running under a framework whose caching
  * allocator has already reserved the device (a cudaMalloc of its own would fail or carve
  * up that pool), or a latency-critical loop that must not take the device-wide
  * synchronisation cudaMalloc / cudaFree can cause.  It needs no plan and calls no
  * cudaMalloc, cudaFree or allocating library routine.  (The paper has no counterpart: it
  * is a deployment variant of the stop test's residual.)
- *   Nx, Ny >= 1, st in {5, 9, 17}; f, u: device, Ny x ld_f / Ny x ld_u doubles (f unscaled,
- *   as for cj_solve); out: device, 3 doubles, receives (rel_l2, rel_inf, floor_est) as in
- *   cj_residual.  Asynchronous on `stream`: out is valid once the stream reaches the call.
+ *   1 <= Nx, Ny <= 2^20, st in {5, 9, 17}; f, u: device, Ny x ld_f / Ny x ld_u doubles (f
+ *   unscaled, as for cj_solve); out: device, 3 doubles, receives (rel_l2, rel_inf, floor_est)
+ *   as in cj_residual (a NaN anywhere in the residual makes both norms NaN).  Asynchronous on
+ *   `stream`: out is valid once the stream reaches the call.
  * Scratch: a fixed 640 KiB array in the library's device memory, one slot per block of
  * 128 x 64 nodes, 16384 slots; grids needing more slots (more than 134,217,728 nodes) are
  * rejected with CJ_ERR_INVALID_ARG and a message in cj_last_error().  Every GPU that loads
@@ -426,6 +450,18 @@ void cj_server_destroy(cj_server *server);
  */
 cj_status cj_residual_noalloc(int Nx, int Ny, cj_stencil st, const double *f, long long ld_f,
                               const double *u, long long ld_u, double *out, void *stream);
+
+/*
+ * cj_issue_peaks -- measured FP64 and FP32 fused multiply-add issue rates of the current device,
+ * in 10^12 FMA instructions per second: the denominators of the instruction-issue rooflines of
+ * the FP64 sweep (on GB300 every FP64 operation of its tree is issued as an FMA, and the FP64
+ * pipe, not HBM, bounds it) and of the temporally blocked FP32 sweep.  Not part of the paper's
+ * method: a measurement of this library.  Each thread of 4 blocks of 256 per SM runs 8
+ * independent dependent FMA chains; the rate is the FMAs of one launch over its CUDA-event time
+ * on `stream`, after a warm-up launch (each stream about 50 ms).  Either output may be NULL (not
+ * measured), not both.  Synchronous.  Errors: CJ_ERR_INVALID_ARG, CJ_ERR_CUDA.
+ */
+cj_status cj_issue_peaks(void *stream, double *fp64_tfma, double *fp32_tfma);
 
 #ifdef __cplusplus
 }

@@ -15,12 +15,12 @@ import numpy as np
 
 from . import build as _build
 
-CJ_OK, CJ_FLOOR, CJ_PENDING = 0, 1, 2
+CJ_OK, CJ_FLOOR, CJ_PENDING, CJ_STALLED = 0, 1, 2, 3
 CJ_ERR_INVALID_ARG, CJ_ERR_NOMEM, CJ_ERR_NOT_CONVERGED = -1, -2, -3
 CJ_ERR_DIVERGED, CJ_ERR_TIMEOUT, CJ_ERR_CUDA, CJ_ERR_BUDGET = -4, -5, -6, -7
 CJ_ST5, CJ_ST9, CJ_ST17 = 5, 9, 17
 CJ_BC_DIRICHLET0, CJ_BC_DIRICHLET = 0, 1
-CJ_FP64, CJ_FP32_INNER, CJ_FP32_INNER_DD = 0, 1, 2
+CJ_FP64, CJ_FP32_INNER, CJ_FP32_INNER_DD, CJ_FP64_INNER_DD = 0, 1, 2, 3
 CJ_CJM, CJ_JACOBI = 0, 1
 CJ_LAUNCH_AUTO, CJ_LAUNCH_STREAM, CJ_LAUNCH_GRAPH = 0, 1, 2
 
@@ -151,6 +151,8 @@ def _lib():
         L.cj_server_destroy.restype = None
         L.cj_residual.argtypes = [_vp, _vp, _ll, _vp, _ll, _vp, _dp, _dp, _dp]
         L.cj_residual.restype = ctypes.c_int
+        L.cj_issue_peaks.argtypes = [_vp, _dp, _dp]
+        L.cj_issue_peaks.restype = ctypes.c_int
         _L = L
     return _L
 
@@ -385,16 +387,45 @@ def cj_residual(plan, f, u, stream=None):
     return a.value, b.value, c.value
 
 
+def _noalloc_args(Nx: int, Ny: int, f, u, out, current_device=None):
+    """Checks of cj_residual_noalloc's tensors, all made before anything is launched: f and u are
+    2-D CUDA float64 tensors with unit x-stride holding at least Ny rows of Nx columns (the
+    kernel reads exactly that block), out a contiguous CUDA float64 tensor of >= 3 elements, and
+    all three live on the current device (the scratch address is that device's).  Returns
+    (f pointer, ld_f, u pointer, ld_u)."""
+    fp, ldf = _grid(f, "float64")
+    up, ldu = _grid(u, "float64")
+    for name, t in (("f", f), ("u", u)):
+        if t.shape[0] < Ny or t.shape[1] < Nx:
+            raise ValueError("%s has shape %s, smaller than the %d x %d grid" % (name, tuple(t.shape), Ny, Nx))
+    if not (out.is_cuda and str(out.dtype) == "torch.float64" and out.numel() >= 3 and out.is_contiguous()):
+        raise ValueError("out must be a contiguous CUDA float64 tensor of >= 3 elements")
+    if current_device is None:
+        import torch
+        current_device = torch.cuda.current_device()
+    for name, t in (("f", f), ("u", u), ("out", out)):
+        if t.device.index != current_device:
+            raise ValueError("%s is on cuda:%s, not on the current device cuda:%d" % (name, t.device.index,
+                                                                                    current_device))
+    return fp, ldf, up, ldu
+
+
 def cj_residual_noalloc(Nx: int, Ny: int, st: int, f, u, out, stream=None) -> None:
     """Allocation-free residual norms: writes (rel_l2, rel_inf, floor_est) into the device
     tensor ``out`` (3 float64) on the stream; no plan, no device allocation."""
-    fp, ldf = _grid(f, "float64")
-    up, ldu = _grid(u, "float64")
-    if not (out.is_cuda and str(out.dtype) == "torch.float64" and out.numel() >= 3 and out.is_contiguous()):
-        raise ValueError("out must be a contiguous CUDA float64 tensor of >= 3 elements")
+    fp, ldf, up, ldu = _noalloc_args(Nx, Ny, f, u, out)
     rc = _lib().cj_residual_noalloc(Nx, Ny, st, fp, ldf, up, ldu, out.data_ptr(), _stream(stream))
     if rc != CJ_OK:
         raise CJError(rc, "cj_residual_noalloc")
+
+
+def cj_issue_peaks(stream=None) -> dict:
+    """Measured FP64 and FP32 FMA issue rates of the current device (T FMA/s), see cj.h."""
+    a, b = ctypes.c_double(), ctypes.c_double()
+    rc = _lib().cj_issue_peaks(_stream(stream), ctypes.byref(a), ctypes.byref(b))
+    if rc != CJ_OK:
+        raise CJError(rc, "cj_issue_peaks")
+    return {"fp64_tfma_s": a.value, "fp32_tfma_s": b.value}
 
 
 def cj_solve_batch(problems, stream=None) -> list:

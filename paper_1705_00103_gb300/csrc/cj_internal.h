@@ -45,11 +45,14 @@ struct cj_plan {
     int depth = 1;            // FP32 sweeps per launch (temporal blocking depth)
     std::vector<double> w;    // sweep coefficients w_n = omega_n / c, application order
     std::vector<float> w32;   // FP32 inner cycle coefficients
+    std::vector<double> w_in; // FP64 inner cycle coefficients (CJ_FP64_INNER_DD)
     int device;
     Grid g64, g32;
     March m64, m32;
     double *u0 = nullptr, *u1 = nullptr, *b = nullptr;    // padded FP64
     float *e0 = nullptr, *e1 = nullptr, *rt = nullptr;    // padded FP32 (mixed only)
+    double *d0 = nullptr, *d1 = nullptr, *r64 = nullptr;  // padded FP64 correction ping-pong and
+                                                          // defect (CJ_FP64_INNER_DD only)
     double *partials = nullptr;                           // 3 doubles per block
     double *red = nullptr;                                // 8 reduced doubles
     double *h_red = nullptr;                              // pinned copy of red
@@ -75,6 +78,7 @@ double plan_abs_coeff_sum(int st);
 void plan_kappa_bounds(int st, double nint_x, double nint_y, double *kmin, double *kmax);
 long long plan_cycle_length(double kmin, double kmax, double tol);
 long long plan_inner_cycle(double kmin, double kmax, long long M);
+long long plan_inner_cycle_fp64(double kmin, double kmax, long long M, double tol);
 void plan_sweep_coeffs(int st, double kmin, double kmax, long long M, std::vector<double> &w);
 // the same with the centre c given (c = 1: the weights omega_n of a Jacobi-normalised operator)
 void plan_sweep_coeffs_c(double c, double kmin, double kmax, long long M, std::vector<double> &w);
@@ -122,6 +126,10 @@ cudaError_t launch_export(const cj_plan *p, const double *u_pad, double *u, long
                           cudaStream_t s);
 cudaError_t launch_sweep64(const cj_plan *p, const double *u, double *out, double w,
                            cudaStream_t s);
+// FP64 sweep of the error equation L e = rhs with the homogeneous boundary of the plan's stencil
+// (odd reflection for 17 points whatever the plan's bc): the inner cycle of CJ_FP64_INNER_DD
+cudaError_t launch_sweep64_err(const cj_plan *p, const double *e, const double *rhs, double *out,
+                               double w, cudaStream_t s);
 cudaError_t launch_sweep32(const cj_plan *p, const float *e, const float *r, float *out, float w,
                            cudaStream_t s);
 // residual of u_pad against p->b: red[0..2] = (sum r^2, max|r|, sum u^2); with rt != NULL
@@ -138,6 +146,11 @@ cudaError_t launch_defect_dd(const cj_plan *p, const double *uh, const double *u
                              float *e_zero, cudaStream_t s);
 cudaError_t launch_correct_dd(const cj_plan *p, double *uh, double *ul, const float *e,
                               cudaStream_t s);
+// the same two steps with an FP64 inner cycle: r64 = -R in FP64, e_zero (FP64) = 0; (uh, ul) += e
+cudaError_t launch_defect_dd64(const cj_plan *p, const double *uh, const double *ul, double *r64,
+                               double *e_zero, cudaStream_t s);
+cudaError_t launch_correct_dd64(const cj_plan *p, double *uh, double *ul, const double *e,
+                                cudaStream_t s);
 // register wavefront temporal-blocked FP32 sweeps (wave_reg.cu): k = 2 sweeps per launch, or
 // 3 or 4 for the 5- and 9-point stencils
 int wave_reg_supported(int st, int k);

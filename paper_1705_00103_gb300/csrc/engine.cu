@@ -141,15 +141,15 @@ __global__ void __launch_bounds__(kEngThreads) eng_defect(EngineDev E) {
     }
 }
 
-// Stop rule of the solver (tol, FP64 floor, two consecutive outer steps that fail to halve
-// the residual, outer-step budget); -1 = continue.
+// Stop rule of the solver (tol, rounding floor, two consecutive outer steps that fail to halve
+// the residual above it, outer-step budget); -1 = continue.
 __device__ __forceinline__ int eng_stop(SlotDev &S) {
     if (S.rho <= S.tol) return CJ_OK;
     if (!(S.rho == S.rho) || S.rho > 1e300) return CJ_ERR_DIVERGED;
     if (S.rho <= 4.0 * S.fl) return CJ_FLOOR;
     if (S.outer > 0) {
         S.stall = S.rho > 0.5 * S.prev ? S.stall + 1 : 0;
-        if (S.stall >= 2) return CJ_FLOOR;
+        if (S.stall >= 2) return CJ_STALLED;
     }
     if (S.outer >= S.max_outer) return CJ_ERR_NOT_CONVERGED;
     return -1;

@@ -257,6 +257,17 @@ cudaError_t launch_sweep64(const cj_plan *p, const double *u, double *out, doubl
     return cudaGetLastError();
 }
 
+cudaError_t launch_sweep64_err(const cj_plan *p, const double *e, const double *rhs, double *out,
+                               double w, cudaStream_t s) {
+    dim3 grid(p->m64.nbx, p->m64.nby);
+    switch (p->st) {
+        case 5: sweep_kernel<5, double><<<grid, kBX, 0, s>>>(e, rhs, out, p->g64, p->m64.ty, w, 1.0); break;
+        case 9: sweep_kernel<9, double><<<grid, kBX, 0, s>>>(e, rhs, out, p->g64, p->m64.ty, w, 1.0); break;
+        default: sweep_kernel<17, double><<<grid, kBX, 0, s>>>(e, rhs, out, p->g64, p->m64.ty, w, 1.0); break;
+    }
+    return cudaGetLastError();
+}
+
 // Dirichlet data g (node (i, j) at g[(j+1) ldg + i+1], i, j in -1..N+2) into the ghost ring of
 // both FP64 solution buffers.
 __global__ void __launch_bounds__(256) ring_kernel(const double *__restrict__ gdat, long long ldg,

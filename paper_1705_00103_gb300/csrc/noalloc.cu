@@ -68,9 +68,12 @@ __device__ __forceinline__ double warp_sum(double v) {
     return v;
 }
 
+// max that keeps a NaN (fmax would drop it), so a non-finite residual shows in the L-inf norm too
+__device__ __forceinline__ double max_nan(double a, double b) { return (a != a || a > b) ? a : b; }
+
 __device__ __forceinline__ double warp_max(double v) {
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_down_sync(0xffffffffu, v, o));
+    for (int o = 16; o > 0; o >>= 1) v = max_nan(v, __shfl_down_sync(0xffffffffu, v, o));
     return v;
 }
 
@@ -90,10 +93,10 @@ __global__ void __launch_bounds__(kBX) na_partials(const double *__restrict__ f,
             const double r = resid_node<ST>(u, ldu, Nx, Ny, i, j, bk);
             const double uc = u[(long long)(j - 1) * ldu + (i - 1)];
             v[0] = fma(r, r, v[0]);
-            v[1] = fmax(v[1], fabs(r));
+            v[1] = max_nan(v[1], fabs(r));
             v[2] = fma(uc, uc, v[2]);
             v[3] = fma(bk, bk, v[3]);
-            v[4] = fmax(v[4], fabs(bk));
+            v[4] = max_nan(v[4], fabs(bk));
         }
     }
     __shared__ double sh[kBX / 32][kNaSlot];
@@ -107,7 +110,7 @@ __global__ void __launch_bounds__(kBX) na_partials(const double *__restrict__ f,
     if (threadIdx.x < kNaSlot) {
         const int k = threadIdx.x;
         double a = 0.0;
-        for (int w = 0; w < kBX / 32; ++w) a = (k == 1 || k == 4) ? fmax(a, sh[w][k]) : a + sh[w][k];
+        for (int w = 0; w < kBX / 32; ++w) a = (k == 1 || k == 4) ? max_nan(a, sh[w][k]) : a + sh[w][k];
         scratch[(long long)(blockIdx.y * gridDim.x + blockIdx.x) * kNaSlot + k] = a;
     }
 }
@@ -121,7 +124,7 @@ __global__ void __launch_bounds__(256) na_finish(const double *__restrict__ scra
 #pragma unroll
         for (int k = 0; k < kNaSlot; ++k) {
             const double x = scratch[(long long)b * kNaSlot + k];
-            v[k] = (k == 1 || k == 4) ? fmax(v[k], x) : v[k] + x;
+            v[k] = (k == 1 || k == 4) ? max_nan(v[k], x) : v[k] + x;
         }
 #pragma unroll
     for (int k = 0; k < kNaSlot; ++k) sh[k][threadIdx.x] = v[k];
@@ -130,7 +133,7 @@ __global__ void __launch_bounds__(256) na_finish(const double *__restrict__ scra
         if (threadIdx.x < s)
 #pragma unroll
             for (int k = 0; k < kNaSlot; ++k)
-                sh[k][threadIdx.x] = (k == 1 || k == 4) ? fmax(sh[k][threadIdx.x], sh[k][threadIdx.x + s])
+                sh[k][threadIdx.x] = (k == 1 || k == 4) ? max_nan(sh[k][threadIdx.x], sh[k][threadIdx.x + s])
                                                         : sh[k][threadIdx.x] + sh[k][threadIdx.x + s];
         __syncthreads();
     }
@@ -165,9 +168,12 @@ cudaError_t scratch_address(double **out) {
 extern "C" cj_status cj_residual_noalloc(int Nx, int Ny, cj_stencil st, const double *f,
                                          long long ld_f, const double *u, long long ld_u,
                                          double *out, void *stream) {
-    if (Nx < 1 || Ny < 1 || !f || !u || !out || ld_f < Nx || ld_u < Nx) return CJ_ERR_INVALID_ARG;
+    // sides up to 2^20 nodes, as for cj_plan_create; the block counts are formed in 64 bits
+    if (Nx < 1 || Ny < 1 || Nx > (1 << 20) || Ny > (1 << 20) || !f || !u || !out || ld_f < Nx ||
+        ld_u < Nx)
+        return CJ_ERR_INVALID_ARG;
     if (st != CJ_ST5 && st != CJ_ST9 && st != CJ_ST17) return CJ_ERR_INVALID_ARG;
-    const long long bx = (Nx + kBX - 1) / kBX, by = (Ny + kNaRows - 1) / kNaRows;
+    const long long bx = ((long long)Nx + kBX - 1) / kBX, by = ((long long)Ny + kNaRows - 1) / kNaRows;
     if (bx * by > kNaMaxBlocks) {
         char msg[256];
         std::snprintf(msg, sizeof(msg),
@@ -182,7 +188,7 @@ extern "C" cj_status cj_residual_noalloc(int Nx, int Ny, cj_stencil st, const do
         set_cuda_error(e, "cj_residual_noalloc: scratch address");
         return CJ_ERR_CUDA;
     }
-    const double h = 1.0 / (double)(Nx + 1);
+    const double h = 1.0 / ((double)Nx + 1.0);
     const double h2 = h * h;
     cudaStream_t s = (cudaStream_t)stream;
     const dim3 grid((unsigned)bx, (unsigned)by);

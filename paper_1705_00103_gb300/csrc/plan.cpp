@@ -93,6 +93,35 @@ long long plan_inner_cycle(double kmin, double kmax, long long M) {
     return best;
 }
 
+// Inner FP64 cycle length of the double-FP64 defect correction with FP64 inner cycles.  One
+// outer step multiplies the error by about q(M) = max(2 exp(-M theta), eps64 G(M)) (the
+// Chebyshev factor, or FP64 rounding amplified by the partial products as in plan_inner_cycle);
+// the solve from u = 0 then needs ceil(log(1/tol) / log(1/q)) steps.  The rule takes the power
+// of two with the fewest sweeps in total, the shorter cycle on a tie (it restarts the
+// contraction more often).  Measured on the 9-point 4096^2 problem to 1e-10 (FP64 sweeps,
+// outer steps, time): 4096: 28,672 in 7 steps, 7.74 s; 8192: 32,768 in 4, 8.85 s; 16384:
+// 32,768 in 2, 8.84 s; 32768: 65,536 in 2, 17.7 s -- the rule picks 4096.
+long long plan_inner_cycle_fp64(double kmin, double kmax, long long M, double tol) {
+    const double d = 2.0 * kmin / (kmax - kmin);
+    const double theta = std::log1p(d + std::sqrt(d * (2.0 + d)));
+    const double eps64 = 1.1102230246251565e-16;  // 2^-53
+    const double need = std::log(1.0 / tol);
+    long long best = M < 2 ? M : 2;
+    double best_total = 1e300;
+    for (long long m = 2; m <= (1LL << 20) && m <= M; m *= 2) {
+        const double cheb = 2.0 * std::exp(-(double)m * theta);
+        const double growth = std::pow(10.0, 2.6 + 0.62 * std::log2((double)m / 512.0));
+        const double q = std::fmax(cheb, eps64 * growth);
+        if (q >= 0.5) continue;
+        const double total = (double)m * std::ceil(need / std::log(1.0 / q) - 1e-9);
+        if (total < best_total) {
+            best_total = total;
+            best = m;
+        }
+    }
+    return best;
+}
+
 // Per-sweep coefficients w_n = 1 / (c * lambda_{o(n)}), lambda_j = (kmax+kmin)/2 +
 // (kmax-kmin)/2 * cos((2j-1) pi / 2M), applied in the mirror-pairing order o: o = (1)
 // for M = 1; going from m to 2m, every entry j of o is followed by 2m+1-j.

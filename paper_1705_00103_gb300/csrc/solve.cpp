@@ -52,6 +52,9 @@ void free_plan(cj_plan *p) {
     cudaFree(p->e0);
     cudaFree(p->e1);
     cudaFree(p->rt);
+    cudaFree(p->d0);
+    cudaFree(p->d1);
+    cudaFree(p->r64);
     cudaFree(p->partials);
     cudaFree(p->red);
     if (p->h_red) cudaFreeHost(p->h_red);
@@ -73,10 +76,10 @@ cudaError_t dev_alloc(T **ptr, size_t count) {
 }
 
 // Stop rule applied after each residual evaluation; -1 = go on.  Converged at tol; at
-// the FP64 rounding floor when rho <= 4 fl, or when `patience` consecutive cycles each
-// failed to halve rho (*stall counts them): 1 for plain cycles, 2 for defect-correction
-// steps, whose residual may jump up once (FP32 rounding noise, high-frequency) before
-// it contracts.
+// the rounding floor when rho <= 4 fl; stalled when `patience` consecutive cycles each
+// failed to halve rho above that (*stall counts them): 1 for plain cycles, 2 for
+// defect-correction steps, whose residual may jump up once (rounding noise of the inner
+// cycle, high-frequency) before it contracts.
 int stop_rule(double rho, double fl, double prev, long long cycles, double tol, int patience,
               int *stall) {
     if (rho <= tol) return CJ_OK;
@@ -84,17 +87,18 @@ int stop_rule(double rho, double fl, double prev, long long cycles, double tol, 
     if (rho <= 4.0 * fl) return CJ_FLOOR;
     if (cycles > 0) {
         *stall = rho > 0.5 * prev ? *stall + 1 : 0;
-        if (*stall >= patience) return CJ_FLOOR;
+        if (*stall >= patience) return CJ_STALLED;
     }
     return -1;
 }
 
 // Stop rule of classical Jacobi, tested every M sweeps: its residual falls monotonically in
-// exact arithmetic, so an interval that did not lower it has reached the rounding floor.
+// exact arithmetic, so an interval that did not lower it has stalled on rounding.
 int jacobi_stop_rule(double rho, double fl, double prev, long long intervals, double tol) {
     if (rho <= tol) return CJ_OK;
     if (!(rho == rho) || rho > 1e300) return CJ_ERR_DIVERGED;
-    if (rho <= 4.0 * fl || (intervals > 0 && rho >= prev)) return CJ_FLOOR;
+    if (rho <= 4.0 * fl) return CJ_FLOOR;
+    if (intervals > 0 && rho >= prev) return CJ_STALLED;
     return -1;
 }
 
@@ -226,8 +230,8 @@ cj_status run_fp64(cj_plan *p, cudaStream_t s, double **cur_out, cj_result *res,
 // Real-error stop (Sec. 3.4, Fig. 4 right): plain FP64 cycles of the plan's length; the real
 // error E = max |u - u_exact| is tested before every cycle and every `every` sweeps inside one
 // (every = 0: at cycle ends only) and the solve stops at the first test with E <= err_tol.  The
-// residual is still evaluated before every cycle, for the floor part of the stop rule only (a
-// goal below the discretisation error ends with CJ_FLOOR once the residual stalls).  hist
+// residual is still evaluated before every cycle, for the floor and stall parts of the stop rule
+// only (a goal below the discretisation error ends with CJ_FLOOR or CJ_STALLED).  hist
 // receives (sweeps, E) pairs.
 struct ErrorStop {
     const double *ue;
@@ -330,7 +334,8 @@ cj_status run_fp64_to_error(cj_plan *p, cudaStream_t s, ErrorStop *es, double **
 }
 
 // The real-error stop at an outer step of a defect-correction solve (after the defect and the
-// real-error launches have been read): the error first, then the floor part of the stop rule.
+// real-error launches have been read): the error first, then the floor and stall parts of the
+// stop rule.
 int mixed_error_stop(ErrorStop *es, long long sweeps, const Norms &n, double prev, long long outer,
                      int *stall) {
     es->add(sweeps, n.err);
@@ -471,6 +476,63 @@ cj_status run_mixed_dd(cj_plan *p, cudaStream_t s, double **cur_out, cj_result *
     return (cj_status)stat;
 }
 
+// FP64 inner cycles in the double-FP64 outer loop: as run_mixed_dd, with the defect -R kept in
+// FP64 (r64) and the inner cycle of M_in FP64 sweeps of L e = r64 (the plain FP64 sweep kernel
+// with the homogeneous boundary, weights w_in), so every operation is FP64 or error-free.
+cj_status run_fp64_dd(cj_plan *p, cudaStream_t s, double **cur_out, cj_result *res, History *h,
+                      ErrorStop *es = nullptr) {
+    long long sweeps = 0, outer = 0;
+    const long long max_outer = p->max_sweeps / p->M_in;
+    const double eps2 = 1.2325951644078309e-32;  // 2^-106
+    double prev = 0.0, sweep_ms = 0.0;
+    bool timed = false;
+    Norms n{};
+    int stat, stall = 0;
+    CJ_TRY(cudaMemsetAsync(p->u1, 0, (size_t)p->g64.elems() * sizeof(double), s), "zero u_lo");
+    for (;;) {
+        CJ_TRY(launch_defect_dd64(p, p->u0, p->u1, p->r64, p->d0, s), "defect dd");
+        res->launches += 2;
+        if (es) {  // the real error of u_hi
+            CJ_TRY(launch_real_error(p, p->u0, es->ue, es->lde, s), "real error");
+            res->launches += 2;
+        }
+        cj_status st = fetch_norms(p, s, &n, eps2);
+        if (st != CJ_OK) return st;
+        if (timed) sweep_ms += elapsed_ms(p);
+        h->add(n.l2);
+        stat = es ? mixed_error_stop(es, sweeps, n, prev, outer, &stall)
+                  : stop_rule(n.l2, n.fl, prev, outer, p->tol, 2, &stall);
+        if (stat != -1) break;
+        if (outer >= max_outer) {
+            stat = CJ_ERR_NOT_CONVERGED;
+            break;
+        }
+        double *cur = p->d0, *nxt = p->d1;
+        CJ_TRY(cudaEventRecord(p->ev0, s), "event");
+        for (long long k = 0; k < p->M_in; ++k) {
+            CJ_TRY(launch_sweep64_err(p, cur, p->r64, nxt, p->w_in[k], s), "sweep");
+            std::swap(cur, nxt);
+        }
+        CJ_TRY(cudaEventRecord(p->ev1, s), "event");
+        timed = true;
+        res->launches += p->M_in;
+        CJ_TRY(launch_correct_dd64(p, p->u0, p->u1, cur, s), "correct dd");
+        res->launches += 1;
+        sweeps += p->M_in;
+        outer += 1;
+        prev = n.l2;
+    }
+    res->sweep_seconds = 1e-3 * sweep_ms;
+    *cur_out = p->u0;
+    res->sweeps = sweeps;
+    res->cycles = (int)outer;
+    res->status = stat;
+    res->rel_res_l2 = n.l2;
+    res->rel_res_inf = n.inf;
+    res->floor_est = n.fl;
+    return (cj_status)stat;
+}
+
 cj_status solve_core(cj_plan *p, const double *f, long long ldf, double *u, long long ldu,
                      cudaStream_t s, cj_result *res, History *h) {
     auto t0 = std::chrono::steady_clock::now();
@@ -480,6 +542,7 @@ cj_status solve_core(cj_plan *p, const double *f, long long ldf, double *u, long
     double *cur = nullptr;
     cj_status st = p->precision == CJ_FP32_INNER      ? run_mixed(p, s, &cur, &r, h)
                    : p->precision == CJ_FP32_INNER_DD ? run_mixed_dd(p, s, &cur, &r, h)
+                   : p->precision == CJ_FP64_INNER_DD ? run_fp64_dd(p, s, &cur, &r, h)
                                                       : run_fp64(p, s, &cur, &r, h);
     if (st < 0 && st != CJ_ERR_NOT_CONVERGED && st != CJ_ERR_DIVERGED) return st;
     CJ_TRY(launch_export(p, cur, u, ldu, s), "export");
@@ -503,8 +566,9 @@ extern "C" {
 const char *cj_status_string(int status) {
     switch (status) {
         case CJ_OK: return "converged";
-        case CJ_FLOOR: return "stopped at the FP64 rounding floor";
+        case CJ_FLOOR: return "stopped at the rounding floor";
         case CJ_PENDING: return "pending";
+        case CJ_STALLED: return "stalled above the rounding floor";
         case CJ_ERR_INVALID_ARG: return "invalid argument";
         case CJ_ERR_NOMEM: return "out of memory";
         case CJ_ERR_NOT_CONVERGED: return "sweep budget exhausted";
@@ -528,7 +592,8 @@ cj_status cj_plan_create(int Nx, int Ny, cj_stencil st, cj_bc bc, double tol,
     if (st != CJ_ST5 && st != CJ_ST9 && st != CJ_ST17) return CJ_ERR_INVALID_ARG;
     if (bc != CJ_BC_DIRICHLET0 && bc != CJ_BC_DIRICHLET) return CJ_ERR_INVALID_ARG;
     if (!(tol > 0.0 && tol < 1.0)) return CJ_ERR_INVALID_ARG;
-    if (o.precision != CJ_FP64 && o.precision != CJ_FP32_INNER && o.precision != CJ_FP32_INNER_DD)
+    if (o.precision != CJ_FP64 && o.precision != CJ_FP32_INNER && o.precision != CJ_FP32_INNER_DD &&
+        o.precision != CJ_FP64_INNER_DD)
         return CJ_ERR_INVALID_ARG;
     if (o.inner_cycle != 0 && !is_pow2(o.inner_cycle)) return CJ_ERR_INVALID_ARG;
     if (o.max_sweeps < 0) return CJ_ERR_INVALID_ARG;
@@ -569,7 +634,10 @@ cj_status cj_plan_create(int Nx, int Ny, cj_stencil st, cj_bc bc, double tol,
         else
             plan_sweep_coeffs(st, p->kmin, p->kmax, p->M, p->w);
         p->M_in = 0;
-        if (p->precision != CJ_FP64) {
+        if (p->precision == CJ_FP64_INNER_DD) {
+            p->M_in = o.inner_cycle ? o.inner_cycle : plan_inner_cycle_fp64(p->kmin, p->kmax, p->M, tol);
+            plan_sweep_coeffs(st, p->kmin, p->kmax, p->M_in, p->w_in);
+        } else if (p->precision != CJ_FP64) {
             p->M_in = o.inner_cycle ? o.inner_cycle : plan_inner_cycle(p->kmin, p->kmax, p->M);
             std::vector<double> wi;
             plan_sweep_coeffs(st, p->kmin, p->kmax, p->M_in, wi);
@@ -615,7 +683,11 @@ cj_status cj_plan_create(int Nx, int Ny, cj_stencil st, cj_bc bc, double tol,
     e = dev_alloc(&p->u0, n64);
     if (e == cudaSuccess) e = dev_alloc(&p->b, n64);
     if (e == cudaSuccess && p->precision != CJ_FP32_INNER) e = dev_alloc(&p->u1, n64);
-    if (e == cudaSuccess && p->precision != CJ_FP64) {
+    if (e == cudaSuccess && p->precision == CJ_FP64_INNER_DD) {
+        e = dev_alloc(&p->d0, n64);
+        if (e == cudaSuccess) e = dev_alloc(&p->d1, n64);
+        if (e == cudaSuccess) e = dev_alloc(&p->r64, n64);
+    } else if (e == cudaSuccess && p->precision != CJ_FP64) {
         e = dev_alloc(&p->e0, n32);
         if (e == cudaSuccess) e = dev_alloc(&p->e1, n32);
         if (e == cudaSuccess) e = dev_alloc(&p->rt, n32);
@@ -753,6 +825,7 @@ cj_status cj_solve_to_error(cj_plan *p, const double *f, long long ldf, double *
     History h;
     cj_status st = p->precision == CJ_FP32_INNER      ? run_mixed(p, s, &cur, &r, &h, &es)
                    : p->precision == CJ_FP32_INNER_DD ? run_mixed_dd(p, s, &cur, &r, &h, &es)
+                   : p->precision == CJ_FP64_INNER_DD ? run_fp64_dd(p, s, &cur, &r, &h, &es)
                                                       : run_fp64_to_error(p, s, &es, &cur, &r);
     if (count) *count = es.n;
     if (st < 0 && st != CJ_ERR_NOT_CONVERGED && st != CJ_ERR_DIVERGED) return st;
@@ -884,7 +957,8 @@ cj_status cj_set_boundary(cj_plan *p, const double *g, long long ldg, void *stre
 }
 
 cj_status cj_solution_lo(cj_plan *p, double *u_lo, long long ld, void *stream) {
-    if (!p || !u_lo || ld < p->Nx || p->precision != CJ_FP32_INNER_DD) return CJ_ERR_INVALID_ARG;
+    if (!p || !u_lo || ld < p->Nx || (p->precision != CJ_FP32_INNER_DD && p->precision != CJ_FP64_INNER_DD))
+        return CJ_ERR_INVALID_ARG;
     CJ_TRY(launch_export(p, p->u1, u_lo, ld, (cudaStream_t)stream), "export lo");
     return CJ_OK;
 }

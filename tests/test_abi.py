@@ -47,7 +47,7 @@ def test_invalid_arguments_rejected_without_gpu():
     bad = [dict(Nx=0, Ny=4, st=5, tol=1e-6), dict(Nx=4, Ny=-1, st=5, tol=1e-6),
            dict(Nx=4, Ny=4, st=7, tol=1e-6), dict(Nx=4, Ny=4, st=9, tol=0.0),
            dict(Nx=4, Ny=4, st=9, tol=1.0), dict(Nx=4, Ny=4, st=17, tol=1e-6, inner_cycle=12),
-           dict(Nx=4, Ny=4, st=17, tol=1e-6, precision=3), dict(Nx=4, Ny=4, st=5, tol=1e-6, bc=2),
+           dict(Nx=4, Ny=4, st=17, tol=1e-6, precision=4), dict(Nx=4, Ny=4, st=5, tol=1e-6, bc=2),
            dict(Nx=4, Ny=4, st=9, tol=1e-6, method=3),
            dict(Nx=4, Ny=4, st=9, tol=1e-6, method=1, precision=2), dict(Nx=4, Ny=4, st=9, tol=1e-6, launch=3),
            dict(Nx=(1 << 20) + 1, Ny=1, st=5, tol=1e-6), dict(Nx=1, Ny=(1 << 20) + 1, st=9, tol=1e-6)]
@@ -107,3 +107,70 @@ def test_batch_server_and_mask_arguments_rejected_without_gpu(lib):
     assert lib.cj_solve_to_error(None, None, ctypes.c_longlong(0), None, ctypes.c_longlong(0), None,
                                  ctypes.c_longlong(0), ctypes.c_double(0.0), ctypes.c_longlong(0), None,
                                  None, None, None, 0, None) == -1
+
+
+class _FakeCuda:
+    """Stands in for a CUDA float64 tensor in the binding's argument checks (no GPU here)."""
+    is_cuda = True
+    dtype = "torch.float64"
+
+    def __init__(self, shape, device=0):
+        self.shape = shape
+        self.device = type("dev", (), {"index": device})()
+
+    def dim(self):
+        return len(self.shape)
+
+    def stride(self, k):
+        return (self.shape[1], 1)[k] if len(self.shape) == 2 else 1
+
+    def data_ptr(self):
+        return 64
+
+    def numel(self):
+        n = 1
+        for s in self.shape:
+            n *= s
+        return n
+
+    def is_contiguous(self):
+        return True
+
+    def __str__(self):
+        return "fake"
+
+
+def test_noalloc_binding_rejects_mismatched_tensors_before_any_launch(monkeypatch):
+    """The Python binding of cj_residual_noalloc refuses, with ValueError and before the library
+    is called, tensors smaller than the Nx x Ny grid it is told about and tensors on another
+    device than the current one."""
+    import paper_1705_00103_gb300.cj as cjm
+
+    def no_call():
+        raise AssertionError("the library was called")
+    monkeypatch.setattr(cjm, "_lib", no_call)
+    monkeypatch.setattr(cjm, "_grid", lambda t, name: (t.data_ptr(), t.shape[1]))
+    out = _FakeCuda((3,))
+    ok = _FakeCuda((20, 30))
+    assert cjm._noalloc_args(30, 20, ok, ok, out, current_device=0) == (64, 30, 64, 30)
+    for f, u in ((_FakeCuda((19, 30)), ok), (ok, _FakeCuda((20, 29))), (_FakeCuda((20, 8)), ok)):
+        with pytest.raises(ValueError):
+            cjm.cj_residual_noalloc(30, 20, 9, f, u, out, stream=0)
+    with pytest.raises(ValueError):
+        cjm._noalloc_args(30, 20, ok, _FakeCuda((20, 30), device=1), out, current_device=0)
+    with pytest.raises(ValueError):
+        cjm._noalloc_args(30, 20, ok, ok, _FakeCuda((3,), device=1), current_device=0)
+
+
+def test_noalloc_rejects_sizes_without_gpu(lib):
+    """Sides beyond 2^20 and grids needing more than the 16384 scratch slots (here 2^20 x 129:
+    8192 x 3 blocks) are refused before the scratch or the arrays are touched."""
+    fn = lib.cj_residual_noalloc
+    fn.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_longlong,
+                   ctypes.c_void_p, ctypes.c_longlong, ctypes.c_void_p, ctypes.c_void_p]
+    lib.cj_last_error.restype = ctypes.c_char_p
+    p = ctypes.c_void_p(64)
+    for Nx, Ny in (((1 << 20) + 1, 1), (1, (1 << 20) + 1), ((1 << 31) - 1, 1), (0, 4), (4, 0)):
+        assert fn(Nx, Ny, 5, p, max(Nx, 1), p, max(Nx, 1), p, None) == -1, (Nx, Ny)
+    assert fn(1 << 20, 129, 9, p, 1 << 20, p, 1 << 20, p, None) == -1
+    assert b"limit" in lib.cj_last_error()

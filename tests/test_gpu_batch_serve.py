@@ -63,7 +63,7 @@ def test_batch_matches_oracle(cj, torch):
     for k, (Nx, Ny, st, tol, prec, M_in, depth) in enumerate(MIX):
         ref = _oracle(Nx, Ny, st, tol, prec, M_in, fs[k])
         assert res[k]["sweeps"] == ref["sweeps"] and res[k]["cycles"] == ref["outer"], (k, res[k], ref["sweeps"])
-        assert {0: "converged", 1: "floor"}[res[k]["rc"]] == ref["status"]
+        assert {0: "converged", 1: "floor", 3: "stalled"}[res[k]["rc"]] == ref["status"]
         np.testing.assert_array_equal(probs[k]["u"].cpu().numpy(), ref["u"], err_msg="problem %d" % k)
         assert res[k]["rel_res_l2"] == pytest.approx(ref["rel_l2"], rel=1e-10)
 
@@ -130,7 +130,7 @@ def test_server_results_match_oracle_and_alone(cj, torch):
         with cj.Plan(Nx, Ny, st, tol, precision=prec) as p:
             M_in = p.info()["M_inner"]
         ref = _oracle(Nx, Ny, st, tol, prec, M_in, fs[k])
-        assert r["rc"] in (cj.CJ_OK, cj.CJ_FLOOR) and r["sweeps"] == ref["sweeps"], (k, r, ref["sweeps"])
+        assert r["rc"] in (cj.CJ_OK, cj.CJ_FLOOR, cj.CJ_STALLED) and r["sweeps"] == ref["sweeps"], (k, r, ref["sweeps"])
         np.testing.assert_array_equal(u, ref["u"], err_msg="request %d" % k)
         assert r["seconds"] > 0
     # the same request alone gives the same bits

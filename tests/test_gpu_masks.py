@@ -103,7 +103,7 @@ def test_mask_solves_match_oracle(cj, torch, name, method):
         ud = torch.zeros((Ny, Nx), dtype=torch.float64, device="cuda")
         res = cj.cj_solve(p.handle, _dev(torch, P["f"]), ud)
     assert res["sweeps"] == ref["sweeps"] and res["cycles"] == ref["cycles"]
-    assert {0: "converged", 1: "floor"}[res["status"]] == ref["status"]
+    assert {0: "converged", 1: "floor", 3: "stalled"}[res["status"]] == ref["status"]
     np.testing.assert_array_equal(ud.cpu().numpy(), ref["u"])
     if P["u_exact"] is not None:
         np.testing.assert_allclose(ref["u"], P["u_exact"], rtol=0, atol=1e-7 * np.abs(P["u_exact"]).max())
