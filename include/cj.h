@@ -199,6 +199,19 @@ cj_status cj_plan_create_mask(int Nx, int Ny, const cj_mask *mask, double tol, c
 void cj_plan_destroy(cj_plan *plan);
 
 /*
+ * cj_plan_weights -- the plan's numbers alone, computed on the host with no device work or
+ * allocation (Sec. 2.1: the weights are precalculated before the iteration): kmin, kmax of
+ * D^-1 A (equations after Eq. 1 and Eq. 2; the exact N = Nx + 1, or the paper-literal N = Nx when
+ * literal_n is 1), the cycle length M and the M sweep coefficients w_n = omega_n / c in
+ * application order (mirror pairing), bit-equal to cj_plan_info's.  This is what every rank of a
+ * decomposed solve needs of the whole grid's plan.  Arguments as cj_plan_create; w: host array of
+ * cap doubles, or NULL to ask for M, kmin, kmax only (any of those may be NULL).
+ * CJ_ERR_INVALID_ARG for a bad argument, a cycle longer than 2^24, or cap < M with w given.
+ */
+cj_status cj_plan_weights(int Nx, int Ny, cj_stencil st, double tol, int literal_n, double *w, long long cap,
+                          long long *M, double *kmin, double *kmax);
+
+/*
  * cj_plan_info -- the plan's numbers (any output pointer may be NULL).
  *   *w      host array of M per-sweep coefficients w_n = omega_n / c in application order
  *           (owned by the plan, valid until cj_plan_destroy);
@@ -450,6 +463,37 @@ void cj_server_destroy(cj_server *server);
  */
 cj_status cj_residual_noalloc(int Nx, int Ny, cj_stencil st, const double *f, long long ld_f,
                               const double *u, long long ld_u, double *out, void *stream);
+
+/* ------------------------------------------------------------------ subdomains */
+
+/*
+ * Kernels for a rank of a 2-D domain decomposition of one grid (the partition, the halo exchange
+ * and the stop test across ranks are host logic; the Python module dd.py drives them).  The grid
+ * is split into blocks; each rank keeps its block in an extended array whose margin holds the
+ * neighbours' halo (or, on the sides that are the grid's boundary, the homogeneous ghosts: 0 at
+ * distance 1 and, for the 17-point stencil, the odd reflection at distance 2).  Both kernels work
+ * on a box of nx x ny nodes of such an array: u, b and out point at the box's first node, rows
+ * ld apart, and the stencil reads up to 2 nodes outside the box from the array itself, which the
+ * caller guarantees exist.  The arithmetic and its order are those of the plan kernels, so a
+ * decomposed solve gives the undecomposed solve's bits at every node.
+ *
+ * cj_box_sweep -- out = u + w (L u - b) on the box (Sec. 2.1's sweep with the weight w);
+ *   out != u, ldo == ldu.  edges: bit 0 the box's first column is the grid's column 1, bit 1 its
+ *   last is column Nx, bit 2 its first row is row 1, bit 3 its last is row Ny; for the 17-point
+ *   stencil the odd-reflection ghosts beyond those sides are written with the nodes.
+ * cj_box_residual -- (sum r^2, max |r|, sum u^2, sum b^2, max |b|) of r = L u - b over the box
+ *   into out[0..4] (device), reduced in a fixed order (maxima keep a NaN); scratch: device, at
+ *   least cj_box_residual_slots(nx, ny) doubles.
+ * cj_box_scale -- dst = alpha * src on nx x ny nodes (b = h^2 f of a block).
+ * All asynchronous on `stream`.  Errors: CJ_ERR_INVALID_ARG, CJ_ERR_CUDA.
+ */
+cj_status cj_box_sweep(int nx, int ny, cj_stencil st, double w, const double *u, long long ldu, const double *b,
+                       long long ldb, double *out, long long ldo, int edges, void *stream);
+cj_status cj_box_residual(int nx, int ny, cj_stencil st, const double *u, long long ldu, const double *b,
+                          long long ldb, double *scratch, long long scratch_len, double *out, void *stream);
+long long cj_box_residual_slots(int nx, int ny);
+cj_status cj_box_scale(int nx, int ny, double alpha, const double *src, long long lds, double *dst, long long ldd,
+                       void *stream);
 
 /*
  * cj_issue_peaks -- measured FP64 and FP32 fused multiply-add issue rates of the current device,

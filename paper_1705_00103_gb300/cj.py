@@ -153,6 +153,19 @@ def _lib():
         L.cj_residual.restype = ctypes.c_int
         L.cj_issue_peaks.argtypes = [_vp, _dp, _dp]
         L.cj_issue_peaks.restype = ctypes.c_int
+        L.cj_plan_weights.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_int, _dp,
+                                      _ll, ctypes.POINTER(_ll), _dp, _dp]
+        L.cj_plan_weights.restype = ctypes.c_int
+        L.cj_box_sweep.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double, _vp, _ll, _vp, _ll,
+                                   _vp, _ll, ctypes.c_int, _vp]
+        L.cj_box_sweep.restype = ctypes.c_int
+        L.cj_box_residual.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, _vp, _ll, _vp, _ll, _vp, _ll, _vp,
+                                      _vp]
+        L.cj_box_residual.restype = ctypes.c_int
+        L.cj_box_residual_slots.argtypes = [ctypes.c_int, ctypes.c_int]
+        L.cj_box_residual_slots.restype = _ll
+        L.cj_box_scale.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double, _vp, _ll, _vp, _ll, _vp]
+        L.cj_box_scale.restype = ctypes.c_int
         _L = L
     return _L
 

@@ -65,15 +65,25 @@ class Engine {
   public:
     ~Engine() { destroy(); }
 
-    cj_status init(int max_slots, int max_depth) {
+    // priority_rank 0 = the device's default stream priority; k > 0 = k levels above it
+    // (clamped to the device's range): a lane of small requests is scheduled ahead of the others.
+    // tile_grid: launch the tile kernels with one block per tile of the current tile list (the
+    // captured graph's grids are updated when the list changes) instead of 8 blocks per SM that
+    // stride over it; short-lived blocks let another stream's higher-priority kernels onto the SMs
+    // within microseconds, where resident striding blocks would hold them for a whole launch.
+    cj_status init(int max_slots, int max_depth, int priority_rank = 0, bool tile_grid = false) {
         if (max_slots < 1 || max_depth < 1 || max_depth > kTbMaxDepth) return CJ_ERR_INVALID_ARG;
         max_slots_ = max_slots;
         max_depth_ = max_depth;
         ENG_TRY(cudaGetDevice(&dev_), "cudaGetDevice");
-        ENG_TRY(cudaStreamCreateWithFlags(&s_, cudaStreamNonBlocking), "engine stream");
+        int least = 0, greatest = 0;
+        ENG_TRY(cudaDeviceGetStreamPriorityRange(&least, &greatest), "stream priorities");
+        const int prio = std::max(greatest, least - priority_rank);  // numerically lower = higher
+        ENG_TRY(cudaStreamCreateWithPriority(&s_, cudaStreamNonBlocking, prio), "engine stream");
         int sms = 152;
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev_);
         grid_tiles_ = sms * 8;
+        tile_grid_ = tile_grid;
         grid_slots_ = std::min(max_slots, sms * 4);
         smem_ = eng_sweep_smem(max_depth);
         ENG_TRY(eng_prepare(smem_), "engine smem attribute");
@@ -102,6 +112,7 @@ class Engine {
         for (int q = 0; q < max_slots_; ++q)
             if (mem_[q].base) cudaFree(mem_[q].base);
         if (gexec_) cudaGraphExecDestroy(gexec_);
+        if (graph_) cudaGraphDestroy(graph_);
         cudaFree(d_.slots);
         cudaFree(d_.status);
         cudaFree(d_.ntiles);
@@ -258,6 +269,13 @@ class Engine {
             cj_status st = capture();
             if (st != CJ_OK) return st;
         }
+        if (tile_grid_) {
+            const int want = std::max(1, *h_ntiles_);
+            if (want != cur_grid_) {
+                cj_status st = set_tile_grid(want);
+                if (st != CJ_OK) return st;
+            }
+        }
         for (int k = 0; k < replays; ++k) ENG_TRY(cudaGraphLaunch(gexec_, s_), "graph launch");
         launches_ += (long long)replays * steps_per_graph_ * (4 + (smem_ > 0 ? 3 : 2) * kSweepsPerStep);
         ENG_TRY(cudaMemcpyAsync(h_status_, d_.status, sizeof(SlotStatus) * max_slots_,
@@ -283,6 +301,8 @@ class Engine {
         if (gexec_) {  // the graph bakes the table pointer in: capture again
             cudaGraphExecDestroy(gexec_);
             gexec_ = nullptr;
+            cudaGraphDestroy(graph_);
+            graph_ = nullptr;
         }
         return CJ_OK;
     }
@@ -313,8 +333,40 @@ class Engine {
         cudaError_t e2 = cudaStreamEndCapture(s_, &g);
         if (err == cudaSuccess) err = e2;
         if (err == cudaSuccess) err = cudaGraphInstantiate(&gexec_, g, 0);
-        if (g) cudaGraphDestroy(g);
+        tile_nodes_.clear();
+        cur_grid_ = grid_tiles_;
+        if (err == cudaSuccess && tile_grid_) {  // the nodes whose grid follows the tile list
+            size_t n = 0;
+            err = cudaGraphGetNodes(g, nullptr, &n);
+            std::vector<cudaGraphNode_t> nodes(n);
+            if (err == cudaSuccess && n) err = cudaGraphGetNodes(g, nodes.data(), &n);
+            for (size_t k = 0; k < n && err == cudaSuccess; ++k) {
+                cudaGraphNodeType type;
+                err = cudaGraphNodeGetType(nodes[k], &type);
+                if (err != cudaSuccess || type != cudaGraphNodeTypeKernel) continue;
+                cudaKernelNodeParams kp{};
+                err = cudaGraphKernelNodeGetParams(nodes[k], &kp);
+                if (err == cudaSuccess && eng_is_tile_kernel(kp.func)) tile_nodes_.push_back(nodes[k]);
+            }
+        }
+        if (err == cudaSuccess) {
+            graph_ = g;  // kept: the tile kernels' nodes are updated through it
+        } else if (g) {
+            cudaGraphDestroy(g);
+        }
         ENG_TRY(err, "graph capture");
+        return CJ_OK;
+    }
+
+    // Every tile kernel of the instantiated graph launches `blocks` blocks from now on.
+    cj_status set_tile_grid(int blocks) {
+        for (cudaGraphNode_t node : tile_nodes_) {
+            cudaKernelNodeParams kp{};
+            ENG_TRY(cudaGraphKernelNodeGetParams(node, &kp), "tile node params");
+            kp.gridDim = dim3((unsigned)blocks);
+            ENG_TRY(cudaGraphExecKernelNodeSetParams(gexec_, node, &kp), "tile grid update");
+        }
+        cur_grid_ = blocks;
         return CJ_OK;
     }
 
@@ -333,6 +385,10 @@ class Engine {
     SlotStatus *h_status_ = nullptr;
     int *h_ntiles_ = nullptr;
     cudaGraphExec_t gexec_ = nullptr;
+    cudaGraph_t graph_ = nullptr;
+    bool tile_grid_ = false;
+    std::vector<cudaGraphNode_t> tile_nodes_;
+    int cur_grid_ = 0;
     long long launches_ = 0;
 };
 
@@ -399,13 +455,33 @@ void fill_result(const SlotStatus &st, cj_result *r) {
 
 // ------------------------------------------------------------------ request server
 
+// Size lanes of the server: requests of up to kLaneNodes[k] nodes (and more than the previous
+// lane's) run in lane k, an engine of its own on its own stream, driven by its own worker
+// thread, so a small request's engine replays sweep only small grids and its latency follows
+// its own work rather than the largest grids on the device.  Smaller lanes' streams have higher
+// priority.  Admission stays by footprint against the one shared budget, in arrival order
+// within a lane.
+constexpr int kLanes = 3;
+constexpr long long kLaneNodes[kLanes] = {1LL << 20, 1LL << 23, 1LL << 62};
+// Every lane launches its tile kernels with one block per tile (Engine::init's tile_grid): with
+// blocks that live a few microseconds, the block scheduler puts the smaller lanes' higher-priority
+// blocks on the SMs as soon as any block retires, while each lane still fills the device when it
+// runs alone.
+
+int lane_of(const Spec &sp) {
+    const long long n = (long long)sp.Nx * sp.Ny;
+    int k = 0;
+    while (k < kLanes - 1 && n > kLaneNodes[k]) ++k;
+    return k;
+}
+
 struct cj_server {
     struct Request {
         uint64_t ticket;
         Spec sp;
         std::vector<double> f;     // host copy of the right-hand side
         std::vector<double> u;     // host result
-        int slot = -1;
+        int slot = -1, lane = 0;
         size_t bytes = 0;
         int state = 0;             // 0 queued, 1 running, 2 done
         cj_status rc = CJ_PENDING;
@@ -413,54 +489,84 @@ struct cj_server {
         Clock::time_point t_submit, t_admit, t_done;
     };
 
-    Engine eng;
+    struct Lane {
+        Engine eng;
+        std::deque<uint64_t> queue;
+        std::map<int, uint64_t> by_slot;
+        std::thread worker;
+    };
+
+    Lane lanes[kLanes];
     size_t budget = 0, in_use = 0;
     int max_slots = 0;
     std::mutex mu;
     std::condition_variable cv;
-    std::deque<uint64_t> queue;
     std::map<uint64_t, Request> reqs;
-    std::map<int, uint64_t> by_slot;
     uint64_t next_ticket = 1;
     bool stop = false;
     cj_status fatal = CJ_OK;
-    std::thread worker;
     int device = 0;
     long long steps = 0, admitted = 0, completed = 0, peak_active = 0;
     size_t peak_bytes = 0;
 
-    void loop() {
+    long long active_all() const {
+        long long n = 0;
+        for (const Lane &L : lanes) n += (long long)L.by_slot.size();
+        return n;
+    }
+
+    long long queued_all() const {
+        long long n = 0;
+        for (const Lane &L : lanes) n += (long long)L.queue.size();
+        return n;
+    }
+
+    // Marks every running request of lane L failed (after a CUDA error of its engine).
+    void fail_lane(Lane &L) {
+        fatal = CJ_ERR_CUDA;
+        for (auto &kv : L.by_slot) {
+            Request &r = reqs[kv.second];
+            r.state = 2;
+            r.rc = CJ_ERR_CUDA;
+            in_use -= r.bytes;
+        }
+        L.by_slot.clear();
+        cv.notify_all();
+    }
+
+    void loop(int lane) {
         cudaSetDevice(device);
+        Lane &L = lanes[lane];
         for (;;) {
             std::vector<uint64_t> admit_now;
             {
                 std::unique_lock<std::mutex> lk(mu);
-                cv.wait(lk, [&] { return stop || !queue.empty() || !by_slot.empty(); });
+                cv.wait(lk, [&] { return stop || !L.queue.empty() || !L.by_slot.empty(); });
                 if (stop) return;
                 // admission by footprint and free slots, in arrival order
-                while (!queue.empty()) {
-                    Request &r = reqs[queue.front()];
+                while (!L.queue.empty()) {
+                    Request &r = reqs[L.queue.front()];
                     double kmin, kmax;
                     long long M_in;
                     if (Engine::plan(r.sp, &kmin, &kmax, &M_in) != CJ_OK) {
                         r.state = 2;
                         r.rc = CJ_ERR_INVALID_ARG;
-                        queue.pop_front();
+                        L.queue.pop_front();
                         continue;
                     }
                     const size_t need = slot_bytes(r.sp, M_in);
                     if (need > budget) {
                         r.state = 2;
                         r.rc = CJ_ERR_BUDGET;
-                        queue.pop_front();
+                        L.queue.pop_front();
                         continue;
                     }
-                    if (in_use + need > budget || (int)(by_slot.size() + admit_now.size()) >= max_slots)
+                    if (in_use + need > budget || (int)(L.by_slot.size() + admit_now.size()) >= max_slots)
                         break;
                     r.bytes = need;
                     in_use += need;
-                    admit_now.push_back(queue.front());
-                    queue.pop_front();
+                    admit_now.push_back(L.queue.front());
+                    L.queue.pop_front();
                 }
             }
             for (uint64_t t : admit_now) {
@@ -469,71 +575,70 @@ struct cj_server {
                     std::lock_guard<std::mutex> lk(mu);
                     r = &reqs[t];
                 }
-                cj_status st = admit(*r);
+                cj_status st = admit(L.eng, *r);
                 std::lock_guard<std::mutex> lk(mu);
                 if (st != CJ_OK) {
                     r->state = 2;
                     r->rc = st;
                     in_use -= r->bytes;
                     if (st == CJ_ERR_CUDA) fatal = st;
+                    cv.notify_all();
                 } else {
                     r->state = 1;
                     r->t_admit = Clock::now();
-                    by_slot[r->slot] = t;
+                    L.by_slot[r->slot] = t;
                     ++admitted;
-                    peak_active = std::max<long long>(peak_active, (long long)by_slot.size());
+                    peak_active = std::max<long long>(peak_active, active_all());
                     peak_bytes = std::max(peak_bytes, in_use);
                 }
             }
             bool active;
             {
                 std::lock_guard<std::mutex> lk(mu);
-                active = !by_slot.empty();
+                active = !L.by_slot.empty();
             }
             if (!active) continue;
-            if (eng.run(1) != CJ_OK) {
+            if (L.eng.run(1) != CJ_OK) {
                 std::lock_guard<std::mutex> lk(mu);
-                fatal = CJ_ERR_CUDA;
-                for (auto &kv : by_slot) {
-                    reqs[kv.second].state = 2;
-                    reqs[kv.second].rc = CJ_ERR_CUDA;
-                }
-                by_slot.clear();
-                cv.notify_all();
+                fail_lane(L);
                 return;
             }
-            steps += eng.steps_per_graph();
-            // release finished problems
             std::vector<std::pair<int, uint64_t>> done;
             {
                 std::lock_guard<std::mutex> lk(mu);
-                for (auto &kv : by_slot)
-                    if (eng.status(kv.first).phase == PHASE_RETIRED) done.push_back(kv);
+                steps += L.eng.steps_per_graph();
+                for (auto &kv : L.by_slot)
+                    if (L.eng.status(kv.first).phase == PHASE_RETIRED) done.push_back(kv);
             }
+            // release finished problems
             for (auto &d : done) {
                 Request *r;
                 {
                     std::lock_guard<std::mutex> lk(mu);
                     r = &reqs[d.second];
                 }
-                const SlotStatus &ss = eng.status(d.first);
+                const SlotStatus &ss = L.eng.status(d.first);
                 double *bin;
                 long long pitch;
-                eng.b_interior(d.first, &bin, &pitch);
-                r->u.assign((size_t)r->sp.Nx * r->sp.Ny, 0.0);
-                cudaError_t e = cudaMemcpy2DAsync(r->u.data(), (size_t)r->sp.Nx * 8, bin, (size_t)pitch * 8,
+                L.eng.b_interior(d.first, &bin, &pitch);
+                std::vector<double> u((size_t)r->sp.Nx * r->sp.Ny, 0.0);
+                cudaError_t e = cudaMemcpy2DAsync(u.data(), (size_t)r->sp.Nx * 8, bin, (size_t)pitch * 8,
                                                   (size_t)r->sp.Nx * 8, r->sp.Ny, cudaMemcpyDeviceToHost,
-                                                  eng.stream());
-                if (e == cudaSuccess) e = cudaStreamSynchronize(eng.stream());
-                fill_result(ss, &r->res);
-                eng.release(d.first);
+                                                  L.eng.stream());
+                if (e == cudaSuccess) e = cudaStreamSynchronize(L.eng.stream());
+                cj_result res{};
+                fill_result(ss, &res);
+                L.eng.release(d.first);
                 std::lock_guard<std::mutex> lk(mu);
+                r->u.swap(u);
+                r->res = res;
                 r->t_done = Clock::now();
                 r->res.seconds = std::chrono::duration<double>(r->t_done - r->t_submit).count();
+                r->res.sweep_seconds = std::chrono::duration<double>(r->t_done - r->t_admit).count();
                 r->rc = e != cudaSuccess ? CJ_ERR_CUDA : (cj_status)ss.status;
                 r->state = 2;
                 in_use -= r->bytes;
-                by_slot.erase(d.first);
+                L.by_slot.erase(d.first);
                 ++completed;
                 cv.notify_all();
             }
@@ -542,7 +647,7 @@ struct cj_server {
 
     // Stages f on the device, admits the request, and points its result at the slot's own b
     // interior (read back by the worker when the slot retires).
-    cj_status admit(Request &r) {
+    cj_status admit(Engine &eng, Request &r) {
         double *fd = nullptr;
         const size_t fbytes = (size_t)r.sp.Nx * r.sp.Ny * 8;
         ENG_TRY(cudaMallocAsync((void **)&fd, fbytes, eng.stream()), "request f");
@@ -703,6 +808,8 @@ cj_status cj_autotune_engine(int Nx, int Ny, cj_stencil st, int *tile_rows, int 
     return CJ_OK;
 }
 
+void cj_server_destroy(cj_server *sv);
+
 cj_status cj_server_create(size_t hbm_budget_bytes, int max_slots, cj_server **out) {
     if (!out || hbm_budget_bytes == 0 || max_slots < 1) return CJ_ERR_INVALID_ARG;
     *out = nullptr;
@@ -711,15 +818,17 @@ cj_status cj_server_create(size_t hbm_budget_bytes, int max_slots, cj_server **o
     sv->budget = hbm_budget_bytes;
     sv->max_slots = max_slots;
     cudaGetDevice(&sv->device);
-    cj_status st = sv->eng.init(max_slots, 1);
-    if (st != CJ_OK) {
-        delete sv;
-        return st;
+    for (int k = 0; k < kLanes; ++k) {
+        cj_status st = sv->lanes[k].eng.init(max_slots, 1, kLanes - 1 - k, true);
+        if (st != CJ_OK) {
+            cj_server_destroy(sv);
+            return st;
+        }
     }
     try {
-        sv->worker = std::thread([sv] { sv->loop(); });
+        for (int k = 0; k < kLanes; ++k) sv->lanes[k].worker = std::thread([sv, k] { sv->loop(k); });
     } catch (...) {
-        delete sv;
+        cj_server_destroy(sv);
         return CJ_ERR_NOMEM;
     }
     *out = sv;
@@ -745,9 +854,10 @@ cj_status cj_submit(cj_server *sv, int Nx, int Ny, cj_stencil st, double tol, co
     cj_server::Request &r = sv->reqs[t];
     r.ticket = t;
     r.sp = spec_of(pr);
+    r.lane = lane_of(r.sp);
     r.f.assign(f_host, f_host + (size_t)Nx * Ny);
     r.t_submit = Clock::now();
-    sv->queue.push_back(t);
+    sv->lanes[r.lane].queue.push_back(t);
     *ticket = t;
     sv->cv.notify_all();
     return CJ_OK;
@@ -770,8 +880,8 @@ cj_status cj_poll(cj_server *sv, uint64_t ticket, double *u_host, cj_result *res
 cj_status cj_server_stats(cj_server *sv, cj_server_stats_t *out) {
     if (!sv || !out) return CJ_ERR_INVALID_ARG;
     std::lock_guard<std::mutex> lk(sv->mu);
-    out->queued = (long long)sv->queue.size();
-    out->active = (long long)sv->by_slot.size();
+    out->queued = sv->queued_all();
+    out->active = sv->active_all();
     out->admitted = sv->admitted;
     out->completed = sv->completed;
     out->steps = sv->steps;
@@ -789,7 +899,8 @@ void cj_server_destroy(cj_server *sv) {
         sv->stop = true;
         sv->cv.notify_all();
     }
-    if (sv->worker.joinable()) sv->worker.join();
+    for (int k = 0; k < kLanes; ++k)
+        if (sv->lanes[k].worker.joinable()) sv->lanes[k].worker.join();
     delete sv;
 }
 

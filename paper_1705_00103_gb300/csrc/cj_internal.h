@@ -64,6 +64,8 @@ struct cj_plan {
     long long *pos = nullptr;
     cudaGraphExec_t graph = nullptr;
     int graph_G = 0;
+    // whole solves in one thread-block cluster (cluster.cu): CTAs per cluster (0 = not used)
+    int cluster_C = 0;
     // coefficient-mask plans (mask.cu): pattern 5/9/17/25 (0 = one of the paper's stencils),
     // normalised off-centre planes with their element strides, and dC = s c_C (full)
     int pattern = 0;
@@ -111,6 +113,14 @@ bool sweep_graph_wanted(const cj_plan *p);
 cudaError_t make_sweep_graph(cj_plan *p);
 // one full cycle (p->M sweeps from u0, ending in u0) on stream s
 cudaError_t launch_sweep_cycle_graph(const cj_plan *p, cudaStream_t s);
+
+// ---- whole small FP64 solves in one cluster (cluster.cu)
+// CTAs of the cluster the plan's solve fits in (0: not eligible: not plain FP64 on the paper's
+// stencils, more than 2^14 nodes, or no cluster launch on this device)
+int cluster_solve_size(const cj_plan *p);
+// the solve of p->u0 against p->b (imported, red[3..4] set) with the plan's weights table w_dev;
+// res_dev[0..5] = status, sweeps, cycles, rho, rinf, fl
+cudaError_t launch_cluster_solve(const cj_plan *p, double *res_dev, cudaStream_t s);
 
 // ---- kernel launchers (kernels.cu); every launcher returns the launch error
 March plan_march(int Nx, int Ny, int st, bool fp64);

@@ -224,8 +224,10 @@ __device__ __forceinline__ void sweep_tile(SlotDev &S, const TileRef &T, int k, 
 // Sweep launches: tiles whose slot advances one sweep now (k = 1: march4, no shared memory)
 // and tiles of temporally blocked slots (k > 1: tb_tile in dynamic shared memory) go to two
 // kernels, so that the blocked tiles' shared memory does not lower the occupancy of the rest.
+// (64 registers for the one-sweep tiles: 8 blocks per SM stay resident, which measured 1.4x faster on
+// the 512-problem batch than the 95-register, 5-blocks-per-SM build)
 template <bool BLOCKED>
-__global__ void __launch_bounds__(kEngThreads) eng_sweep(EngineDev E) {
+__global__ void __launch_bounds__(kEngThreads, BLOCKED ? 1 : 8) eng_sweep(EngineDev E) {
     extern __shared__ float sm[];
     const int n = *E.ntiles;
     for (int t = blockIdx.x; t < n; t += gridDim.x) {
@@ -377,6 +379,18 @@ size_t eng_sweep_smem(int max_depth) {
     if (max_depth <= 1) return 0;
     const int H = 2 * max_depth;  // radius 2 covers every stencil
     return (size_t)3 * (kEngTX + 2 * H) * (kEngTYMax + 2 * H) * sizeof(float);
+}
+
+bool eng_is_tile_kernel(const void *fn) {
+    return fn == (const void *)eng_correct || fn == (const void *)eng_defect || fn == (const void *)eng_sweep<false> ||
+           fn == (const void *)eng_sweep<true> || fn == (const void *)eng_export;
+}
+
+int eng_sweep_blocks_per_sm() {
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, eng_sweep<false>, kEngThreads, 0) != cudaSuccess || n < 1)
+        n = 1;
+    return n;
 }
 
 cudaError_t eng_prepare(size_t sweep_smem) {

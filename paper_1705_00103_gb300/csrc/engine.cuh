@@ -61,4 +61,8 @@ cudaError_t eng_launch_step(const EngineDev &e, int grid_tiles, int grid_slots, 
 cudaError_t eng_launch_import(const EngineDev &e, int slot, int ntiles, const double *f,
                               long long ldf, const double *u0, long long ldu, cudaStream_t s);
 size_t eng_sweep_smem(int max_depth);
+// blocks of the one-sweep tile kernel (the engine's heaviest in registers) resident per SM
+int eng_sweep_blocks_per_sm();
+// true for the kernels that loop over the tile list (their grid may be any size)
+bool eng_is_tile_kernel(const void *fn);
 cudaError_t eng_prepare(size_t sweep_smem);

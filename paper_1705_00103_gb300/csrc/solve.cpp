@@ -174,8 +174,30 @@ cudaError_t import64(const cj_plan *p, const double *f, long long ldf, const dou
                       : launch_import(p, f, ldf, u, ldu, p->b, p->u0, s);
 }
 
+// A whole plain FP64 solve in one cluster launch (small grids): the stop test runs on the
+// device, so the host reads the outcome once.
+cj_status run_fp64_cluster(cj_plan *p, cudaStream_t s, double **cur_out, cj_result *res) {
+    CJ_TRY(cudaEventRecord(p->ev0, s), "event");
+    CJ_TRY(launch_cluster_solve(p, p->red, s), "cluster solve");
+    CJ_TRY(cudaEventRecord(p->ev1, s), "event");
+    res->launches += 1;
+    CJ_TRY(cudaMemcpyAsync(p->h_red, p->red, 6 * sizeof(double), cudaMemcpyDeviceToHost, s), "cluster readback");
+    CJ_TRY(cudaStreamSynchronize(s), "cluster sync");
+    const double *r = p->h_red;
+    res->sweep_seconds = 1e-3 * elapsed_ms(p);
+    *cur_out = p->u0;
+    res->status = (int)r[0];
+    res->sweeps = (long long)r[1];
+    res->cycles = (int)r[2];
+    res->rel_res_l2 = r[3];
+    res->rel_res_inf = r[4];
+    res->floor_est = r[5];
+    return (cj_status)res->status;
+}
+
 // The solve proper, once f and u have been imported into the plan's padded buffers.
 cj_status run_fp64(cj_plan *p, cudaStream_t s, double **cur_out, cj_result *res, History *h) {
+    if (p->cluster_C > 0 && h->cap == 0) return run_fp64_cluster(p, s, cur_out, res);
     double *cur = p->u0, *nxt = p->u1;
     long long sweeps = 0, cycles = 0;
     double prev = 0.0, sweep_ms = 0.0;
@@ -600,7 +622,7 @@ cj_status cj_plan_create(int Nx, int Ny, cj_stencil st, cj_bc bc, double tol,
     if (o.temporal_depth < 0 || o.temporal_depth > kTbMaxDepth) return CJ_ERR_INVALID_ARG;
     if (o.method != CJ_CJM && o.method != CJ_JACOBI) return CJ_ERR_INVALID_ARG;
     if (o.method == CJ_JACOBI && o.precision != CJ_FP64) return CJ_ERR_INVALID_ARG;
-    if (o.launch < 0 || o.launch > 2) return CJ_ERR_INVALID_ARG;
+    if (o.launch < 0 || o.launch > 3) return CJ_ERR_INVALID_ARG;
 
     cj_plan *p = new (std::nothrow) cj_plan();
     if (!p) return CJ_ERR_NOMEM;
@@ -700,11 +722,24 @@ cj_status cj_plan_create(int Nx, int Ny, cj_stencil st, cj_bc bc, double tol,
     const bool graph = p->precision == CJ_FP64 && p->M % 2 == 0 &&
                        (o.launch == 2 || (o.launch == 0 && sweep_graph_wanted(p)));
     if (e == cudaSuccess && graph) e = make_sweep_graph(p);
+    if (e == cudaSuccess && (o.launch == 0 || o.launch == 3)) {
+        p->cluster_C = cluster_solve_size(p);
+        if (p->cluster_C > 0 && !p->w_dev) {
+            e = cudaMalloc((void **)&p->w_dev, sizeof(double) * (size_t)p->M);
+            if (e == cudaSuccess)
+                e = cudaMemcpy(p->w_dev, p->w.data(), sizeof(double) * (size_t)p->M, cudaMemcpyHostToDevice);
+        }
+    }
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
     if (e != cudaSuccess) {
         set_cuda_error(e, "plan allocation");
         free_plan(p);
         return e == cudaErrorMemoryAllocation ? CJ_ERR_NOMEM : CJ_ERR_CUDA;
+    }
+    if (o.launch == 3 && p->cluster_C == 0) {  // the cluster solve was asked for and does not fit
+        set_error_text("cj_plan_create: launch 3 needs a plain FP64 plan of at most 2^14 nodes");
+        free_plan(p);
+        return CJ_ERR_INVALID_ARG;
     }
     *out = p;
     return CJ_OK;
@@ -771,6 +806,32 @@ cj_status cj_plan_create_mask(int Nx, int Ny, const cj_mask *m, double tol, cons
 }
 
 void cj_plan_destroy(cj_plan *plan) { free_plan(plan); }
+
+cj_status cj_plan_weights(int Nx, int Ny, cj_stencil st, double tol, int literal_n, double *w, long long cap,
+                          long long *M, double *kmin, double *kmax) {
+    if (Nx < 1 || Ny < 1 || Nx > (1 << 20) || Ny > (1 << 20)) return CJ_ERR_INVALID_ARG;
+    if (st != CJ_ST5 && st != CJ_ST9 && st != CJ_ST17) return CJ_ERR_INVALID_ARG;
+    if (!(tol > 0.0 && tol < 1.0) || cap < 0) return CJ_ERR_INVALID_ARG;
+    double a = 0.0, b = 0.0;
+    plan_kappa_bounds(st, literal_n ? (double)Nx : (double)(Nx + 1), literal_n ? (double)Ny : (double)(Ny + 1), &a,
+                      &b);
+    if (!(a > 0.0 && a < b)) return CJ_ERR_INVALID_ARG;
+    const long long m = plan_cycle_length(a, b, tol);
+    if (m > (1LL << 24)) return CJ_ERR_INVALID_ARG;
+    if (M) *M = m;
+    if (kmin) *kmin = a;
+    if (kmax) *kmax = b;
+    if (!w) return CJ_OK;
+    if (cap < m) return CJ_ERR_INVALID_ARG;
+    try {
+        std::vector<double> v;
+        plan_sweep_coeffs(st, a, b, m, v);
+        std::memcpy(w, v.data(), (size_t)m * sizeof(double));
+    } catch (...) {
+        return CJ_ERR_NOMEM;
+    }
+    return CJ_OK;
+}
 
 cj_status cj_plan_info(const cj_plan *p, const double **w, long long *M, double *kmin,
                        double *kmax, long long *M_inner) {

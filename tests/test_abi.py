@@ -49,7 +49,7 @@ def test_invalid_arguments_rejected_without_gpu():
            dict(Nx=4, Ny=4, st=9, tol=1.0), dict(Nx=4, Ny=4, st=17, tol=1e-6, inner_cycle=12),
            dict(Nx=4, Ny=4, st=17, tol=1e-6, precision=4), dict(Nx=4, Ny=4, st=5, tol=1e-6, bc=2),
            dict(Nx=4, Ny=4, st=9, tol=1e-6, method=3),
-           dict(Nx=4, Ny=4, st=9, tol=1e-6, method=1, precision=2), dict(Nx=4, Ny=4, st=9, tol=1e-6, launch=3),
+           dict(Nx=4, Ny=4, st=9, tol=1e-6, method=1, precision=2), dict(Nx=4, Ny=4, st=9, tol=1e-6, launch=4),
            dict(Nx=(1 << 20) + 1, Ny=1, st=5, tol=1e-6), dict(Nx=1, Ny=(1 << 20) + 1, st=9, tol=1e-6)]
     for kw in bad:
         with pytest.raises(cj.CJError) as ei:

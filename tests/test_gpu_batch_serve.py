@@ -182,3 +182,34 @@ def test_engine_autotune_records_and_uses_its_choice(cj, torch):
     np.testing.assert_array_equal(pr["u"].cpu().numpy(), ref["u"])
     with pytest.raises(cj.CJError):
         cj.cj_autotune_engine(0, 10, 9)
+
+
+def test_server_lanes_give_the_batch_engines_bits(cj, torch):
+    """Requests in all three size lanes (up to 2^20 nodes, up to 2^23, larger) give the bits the
+    batch engine gives for the same problems (the batch engine is checked against the oracle
+    above); a small request submitted after a large one finishes first."""
+    cases = [(3000, 2900, 9, 1e-6), (1100, 1000, 5, 1e-6), (100, 80, 17, 1e-8), (64, 64, 9, 1e-10)]
+    fs = [workloads.smooth_random_rhs(Nx, Ny, 80 + k, kmax=30) for k, (Nx, Ny, st, tol) in enumerate(cases)]
+    done_at = {}
+    with cj.Server(8 << 30, 8) as srv:
+        tickets = {srv.submit(f, st, tol): k for k, (f, (Nx, Ny, st, tol)) in enumerate(zip(fs, cases))}
+        got, t0 = {}, time.time()
+        while len(got) < len(cases) and time.time() - t0 < 300:
+            for t, k in tickets.items():
+                if k not in got:
+                    g = srv.poll(t, fs[k].shape)
+                    if g is not None:
+                        got[k] = g
+                        done_at[k] = len(done_at)
+            time.sleep(0.001)
+    assert len(got) == len(cases)
+    assert done_at[3] < done_at[0] and done_at[2] < done_at[0]
+    probs = [dict(Nx=Nx, Ny=Ny, st=st, tol=tol, f=torch.from_numpy(f).cuda(),
+                  u=torch.zeros((Ny, Nx), dtype=torch.float64, device="cuda"))
+             for f, (Nx, Ny, st, tol) in zip(fs, cases)]
+    res = cj.cj_solve_batch(probs)
+    for k in range(len(cases)):
+        u, r = got[k]
+        assert r["rc"] == res[k]["rc"] and r["sweeps"] == res[k]["sweeps"], (k, r, res[k])
+        np.testing.assert_array_equal(u, probs[k]["u"].cpu().numpy(), err_msg="request %d" % k)
+        assert 0 < r["sweep_seconds"] <= r["seconds"]

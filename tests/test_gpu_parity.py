@@ -725,3 +725,67 @@ def test_mixed_solve_to_error_matches_oracle(cj, torch, st, prec, data):
     np.testing.assert_array_equal(res["history"], ref["history"])
     np.testing.assert_array_equal(ud.cpu().numpy(), ref["u"])
     assert res["real_error"] == ref["err"]
+
+
+# ----------------------------------------------------------------- whole solves in one cluster
+
+@pytest.mark.parametrize("st", STENCILS)
+@pytest.mark.parametrize("Nx,Ny", [(64, 64), (1, 1), (1, 100), (100, 1), (17, 9), (128, 128), (33, 65), (3, 40)])
+@pytest.mark.parametrize("method", [0, 1])
+def test_cluster_solve_equals_launched_sweeps_and_the_oracle(cj, torch, st, Nx, Ny, method):
+    """The single-launch cluster solve (launch 3) gives the bits, sweep count and status of one
+    launch per sweep (launch 1) and of the oracle, for CJM and classical Jacobi."""
+    f = workloads.smooth_random_rhs(Nx, Ny, 3, kmax=min(20, Nx, Ny))
+    tol = 1e-10 if method == 0 else 1e-4
+    out = {}
+    for launch in (3, 1):
+        with cj.Plan(Nx, Ny, st, tol, launch=launch, method=method) as p:
+            u = torch.zeros((Ny, Nx), dtype=torch.float64, device="cuda")
+            out[launch] = (cj.cj_solve(p.handle, dev(torch, f), u), u.cpu().numpy())
+    r3, u3 = out[3]
+    r1, u1 = out[1]
+    assert r3["launches"] == 4 and (r3["sweeps"], r3["cycles"], r3["rc"]) == (r1["sweeps"], r1["cycles"], r1["rc"])
+    np.testing.assert_array_equal(u3, u1)
+    assert r3["rel_res_l2"] == pytest.approx(r1["rel_res_l2"], rel=1e-12)
+    ref = orc.solve(st, f, tol) if method == 0 else orc.solve_jacobi(st, f, tol)
+    assert r3["sweeps"] == ref["sweeps"]
+    assert {0: "converged", 1: "floor", 3: "stalled"}[r3["rc"]] == ref["status"]
+    np.testing.assert_array_equal(u3, ref["u"])
+
+
+@pytest.mark.parametrize("st", STENCILS)
+def test_cluster_solve_with_dirichlet_data(cj, torch, st):
+    N = 90
+    f, _, g = workloads.paper_problem(N, N)
+    G, Gd = _ring(torch, N, N, g)
+    ref = orc.solve_bc(st, f, G, 1e-10)
+    for launch in (3, 1):
+        with cj.Plan(N, N, st, 1e-10, bc=cj.CJ_BC_DIRICHLET, launch=launch) as p:
+            cj.cj_set_boundary(p.handle, Gd)
+            u = torch.zeros((N, N), dtype=torch.float64, device="cuda")
+            r = cj.cj_solve(p.handle, dev(torch, f), u)
+        assert r["sweeps"] == ref["sweeps"] and {0: "converged", 1: "floor", 3: "stalled"}[r["rc"]] == ref["status"]
+        np.testing.assert_array_equal(u.cpu().numpy(), ref["u"])
+
+
+def test_cluster_solve_repeats_and_warm_starts(cj, torch):
+    """A second solve on the same plan, and a warm start, give the launched sweeps' results."""
+    Nx, Ny, st = 80, 70, 9
+    f = workloads.smooth_random_rhs(Nx, Ny, 8)
+    u0 = np.random.default_rng(1).standard_normal((Ny, Nx)) * 1e-3
+    res = {}
+    for launch in (3, 1):
+        with cj.Plan(Nx, Ny, st, 1e-9, launch=launch) as p:
+            for k in range(2):
+                u = dev(torch, u0)
+                r = cj.cj_solve(p.handle, dev(torch, f), u)
+            res[launch] = (r["sweeps"], u.cpu().numpy())
+    assert res[3][0] == res[1][0]
+    np.testing.assert_array_equal(res[3][1], res[1][1])
+
+
+def test_cluster_launch_refused_where_it_does_not_fit(cj):
+    with pytest.raises(cj.CJError):
+        cj.Plan(200, 200, 9, 1e-8, launch=3)
+    with pytest.raises(cj.CJError):
+        cj.Plan(64, 64, 9, 1e-8, launch=3, precision=cj.CJ_FP32_INNER)
