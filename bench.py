@@ -949,6 +949,35 @@ def serve_key(cj, n_requests: int, fp64_every: int = 4, fp64_max_nodes: int = 1 
                      "fp64_s": dt, "fp64_status": cj.cj_status_string(rr["rc"]),
                      "served_latency_s": got[j]["seconds"], "served_service_s": got[j]["sweep_seconds"]})
         own.append(dt)
+    # every request of the prefix by the FP64 path, one at a time, as a lower bound: its FP64 sweep
+    # time (8 timed sweeps) x the fewest sweeps an FP64 solve can take (the plain cycle length M for
+    # tol 1e-6, which plain FP64 reaches; for 1e-10 the all-FP64 path's two inner cycles, or M if less)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    lower = 0.0
+    for j, r in enumerate(reqs):
+        fd = torch.from_numpy(fs[j]).cuda()
+        with cj.Plan(r["Nx"], r["Ny"], r["st"], r["tol"], launch=cj.CJ_LAUNCH_STREAM) as pl:
+            M = pl.info()["M"]
+            g = torch.zeros_like(fd)
+            cj.cj_sweeps(pl.handle, fd, g, 0, 2, stream)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            cj.cj_sweeps(pl.handle, fd, g, 0, 8, stream)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            t0s = e0.elapsed_time(e1) * 1e-3
+            e0.record(stream)
+            cj.cj_sweeps(pl.handle, fd, g, 0, 0, stream)  # the import and export alone
+            e1.record(stream)
+            torch.cuda.synchronize()
+            per = max(0.0, t0s - e0.elapsed_time(e1) * 1e-3) / 8
+        n_min = M
+        if r["tol"] < 1e-6:
+            with cj.Plan(r["Nx"], r["Ny"], r["st"], r["tol"], precision=cj.CJ_FP64_INNER_DD) as pdd:
+                n_min = min(M, 2 * pdd.info()["M_inner"])
+        lower += per * n_min
+        del fd, g
     return {"workload": "served: arrival-faithful prefix of the seeded Poisson stream (2000/s), first %d of "
                         "10,000 requests, sides log-uniform in [32, 8192], 5/9/17-point, tol 1e-6 / 1e-10, "
                         "budget 150 GB" % len(reqs),
@@ -964,8 +993,16 @@ def serve_key(cj, n_requests: int, fp64_every: int = 4, fp64_max_nodes: int = 1 
                                    "sum_served_service_s": sum(x["served_service_s"] for x in fp64),
                                    "median_fp64_s": float(np.median(own)) if own else None,
                                    "note": "every %d-th request of at most %d nodes, alone: plain FP64 CJM for tol "
-                                           "1e-6, FP64 cycles in double-FP64 defect correction for 1e-10"
-                                           % (fp64_every, fp64_max_nodes)}}
+                                           "1e-6, FP64 cycles in double-FP64 defect correction for 1e-10; for these "
+                                           "small requests the FP64 path alone is faster than their service in the "
+                                           "mix, whose engine spends ~2.5 launches per sweep"
+                                           % (fp64_every, fp64_max_nodes)},
+            "fp64_whole_prefix_lower_bound_s_extrapolated": lower,
+            "speedup_vs_fp64_one_at_a_time_lower_bound": lower / wall,
+            "fp64_whole_prefix_note": "every request of the prefix by the FP64 path one at a time: its FP64 sweep "
+                                      "time (8 timed sweeps) x the fewest sweeps an FP64 solve can take (the plain "
+                                      "cycle length for 1e-6; for 1e-10 two inner cycles of the all-FP64 path, or the "
+                                      "plain cycle if shorter); a lower bound, so the speed-up is one too"}
 
 
 def run_serve(args):

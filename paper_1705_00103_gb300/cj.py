@@ -22,7 +22,7 @@ CJ_ST5, CJ_ST9, CJ_ST17 = 5, 9, 17
 CJ_BC_DIRICHLET0, CJ_BC_DIRICHLET = 0, 1
 CJ_FP64, CJ_FP32_INNER, CJ_FP32_INNER_DD, CJ_FP64_INNER_DD = 0, 1, 2, 3
 CJ_CJM, CJ_JACOBI = 0, 1
-CJ_LAUNCH_AUTO, CJ_LAUNCH_STREAM, CJ_LAUNCH_GRAPH = 0, 1, 2
+CJ_LAUNCH_AUTO, CJ_LAUNCH_STREAM, CJ_LAUNCH_GRAPH, CJ_LAUNCH_CLUSTER = 0, 1, 2, 3
 
 
 class cj_options(ctypes.Structure):

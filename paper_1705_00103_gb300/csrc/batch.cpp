@@ -489,11 +489,20 @@ struct cj_server {
         Clock::time_point t_submit, t_admit, t_done;
     };
 
+    // Pinned staging buffer of each lane: request data crosses the bus through it in chunks on
+    // the lane's stream, so a large request's copies neither stage through the driver's pageable
+    // path nor hold up the other lanes' work.
+    static constexpr size_t kStageBytes = (size_t)16 << 20;
+
     struct Lane {
         Engine eng;
         std::deque<uint64_t> queue;
         std::map<int, uint64_t> by_slot;
         std::thread worker;
+        char *stage = nullptr;
+        ~Lane() {
+            if (stage) cudaFreeHost(stage);
+        }
     };
 
     Lane lanes[kLanes];
@@ -575,7 +584,7 @@ struct cj_server {
                     std::lock_guard<std::mutex> lk(mu);
                     r = &reqs[t];
                 }
-                cj_status st = admit(L.eng, *r);
+                cj_status st = admit(L, *r);
                 std::lock_guard<std::mutex> lk(mu);
                 if (st != CJ_OK) {
                     r->state = 2;
@@ -622,10 +631,7 @@ struct cj_server {
                 long long pitch;
                 L.eng.b_interior(d.first, &bin, &pitch);
                 std::vector<double> u((size_t)r->sp.Nx * r->sp.Ny, 0.0);
-                cudaError_t e = cudaMemcpy2DAsync(u.data(), (size_t)r->sp.Nx * 8, bin, (size_t)pitch * 8,
-                                                  (size_t)r->sp.Nx * 8, r->sp.Ny, cudaMemcpyDeviceToHost,
-                                                  L.eng.stream());
-                if (e == cudaSuccess) e = cudaStreamSynchronize(L.eng.stream());
+                cudaError_t e = download(L, u.data(), bin, pitch, r->sp.Nx, r->sp.Ny);
                 cj_result res{};
                 fill_result(ss, &res);
                 L.eng.release(d.first);
@@ -647,11 +653,40 @@ struct cj_server {
 
     // Stages f on the device, admits the request, and points its result at the slot's own b
     // interior (read back by the worker when the slot retires).
-    cj_status admit(Engine &eng, Request &r) {
+    // Host -> device of n bytes through the lane's staging buffer (whole rows of nothing: a flat copy).
+    cudaError_t upload(Lane &L, void *dst, const void *src, size_t n) {
+        for (size_t off = 0; off < n; off += kStageBytes) {
+            const size_t k = std::min(kStageBytes, n - off);
+            std::memcpy(L.stage, (const char *)src + off, k);
+            cudaError_t e = cudaMemcpyAsync((char *)dst + off, L.stage, k, cudaMemcpyHostToDevice, L.eng.stream());
+            if (e == cudaSuccess) e = cudaStreamSynchronize(L.eng.stream());  // before the buffer is reused
+            if (e != cudaSuccess) return e;
+        }
+        return cudaSuccess;
+    }
+
+    // Device (Ny rows of Nx doubles, row pitch `pitch` elements) -> host (dense) through the staging
+    // buffer, a band of whole rows at a time.
+    cudaError_t download(Lane &L, double *dst, const double *src, long long pitch, int Nx, int Ny) {
+        const size_t row = (size_t)Nx * 8;
+        const int band = (int)std::max<size_t>(1, kStageBytes / row);
+        for (int j = 0; j < Ny; j += band) {
+            const int rows = std::min(band, Ny - j);
+            cudaError_t e = cudaMemcpy2DAsync(L.stage, row, src + (size_t)j * pitch, (size_t)pitch * 8, row, rows,
+                                              cudaMemcpyDeviceToHost, L.eng.stream());
+            if (e == cudaSuccess) e = cudaStreamSynchronize(L.eng.stream());
+            if (e != cudaSuccess) return e;
+            std::memcpy(dst + (size_t)j * Nx, L.stage, row * rows);
+        }
+        return cudaSuccess;
+    }
+
+    cj_status admit(Lane &L, Request &r) {
+        Engine &eng = L.eng;
         double *fd = nullptr;
         const size_t fbytes = (size_t)r.sp.Nx * r.sp.Ny * 8;
         ENG_TRY(cudaMallocAsync((void **)&fd, fbytes, eng.stream()), "request f");
-        ENG_TRY(cudaMemcpyAsync(fd, r.f.data(), fbytes, cudaMemcpyHostToDevice, eng.stream()), "request H2D");
+        ENG_TRY(upload(L, fd, r.f.data(), fbytes), "request H2D");
         int slot = -1;
         cj_status st = eng.admit(r.sp, fd, r.sp.Nx, nullptr, 0, nullptr, 0, &slot, true);
         cudaError_t e = cudaFreeAsync(fd, eng.stream());
@@ -820,6 +855,8 @@ cj_status cj_server_create(size_t hbm_budget_bytes, int max_slots, cj_server **o
     cudaGetDevice(&sv->device);
     for (int k = 0; k < kLanes; ++k) {
         cj_status st = sv->lanes[k].eng.init(max_slots, 1, kLanes - 1 - k, true);
+        if (st == CJ_OK && cudaMallocHost((void **)&sv->lanes[k].stage, cj_server::kStageBytes) != cudaSuccess)
+            st = CJ_ERR_NOMEM;
         if (st != CJ_OK) {
             cj_server_destroy(sv);
             return st;

@@ -6,10 +6,12 @@
 // grid in shared memory for the whole solve: CTA c owns a band of rows, with two ghost rows above
 // and below, in two ping-pong buffers of full padded width (columns -1 .. Nx+2).  A sweep is:
 // every CTA computes its rows from one buffer into the other (the weight w_n from the plan's
-// table), storing each node of its first and last two rows also into the neighbouring CTA's ghost
-// rows of that buffer through distributed shared memory, then the cluster barrier, which makes
-// those stores visible.  The neighbour last read that buffer in the sweep before, ahead of the
-// previous barrier, so the stores never overwrite rows it still needs.  The residual test
+// table), storing each node of its first and last R rows (R the stencil radius) also into the
+// neighbouring CTA's ghost rows of that buffer through distributed shared memory.  Those boundary
+// rows are computed first, then the arrive half of the cluster barrier (release), the interior rows,
+// and the wait half (acquire), so the barrier's latency overlaps the interior work.  A neighbour
+// reads its ghost rows only for its own boundary rows, which it computes before it arrives, so the
+// next sweep's stores never overwrite rows it still needs.  The residual test
 // before every cycle reduces (sum r^2, max |r|, sum u^2) per CTA, and every CTA then reads all
 // CTAs' triples in rank order through distributed shared memory, so all take the identical stop
 // decision and leave the loop together.  No thread waits on a flag: the only waits are the
@@ -161,6 +163,8 @@ __global__ void __launch_bounds__(kClThreads) cluster_solve_kernel(ClArgs a) {
         cl.sync();  // every CTA has read the triples before any CTA writes new ones
         if (status != -1) break;
         prev = rho;
+        constexpr int R = ST == 17 ? 2 : 1;
+        const int nbt = R < nr ? R : nr, nbb = R < nr - nbt ? R : nr - nbt;  // boundary rows
         for (long long n = 0; n < a.M; ++n) {
             const double w = a.w[n];
             const double *Ui = cur ? buf1 : buf0;
@@ -172,16 +176,16 @@ __global__ void __launch_bounds__(kClThreads) cluster_solve_kernel(ClArgs a) {
                 up_base = cl.map_shared_rank(Uo, c - 1) + (long long)(pnr + 2) * W;
             }
             if (c < C - 1) dn_base = cl.map_shared_rank(Uo, c + 1);
-            for (long long k = t; k < (long long)nr * Nx; k += kClThreads) {
-                const int q = (int)(k / Nx) + 2, x = (int)(k % Nx) + 2;
+            // node (q, x) of the new buffer; the first and last R rows also go to the neighbours'
+            // ghost rows: my rows 2 .. R+1 are rows pnr+2 .. of the CTA above (rank c-1), my rows
+            // nr-R+2 .. nr+1 are rows 2-R .. 1 of the CTA below (rank c+1)
+            auto node = [&](int q, int x) {
                 auto U = [&](int di, int dj) { return Ui[(long long)(q + dj) * W + x + di]; };
-                const double v = fma(w, resid_direct<ST, double>(U, bs[k]), U(0, 0));
+                const double v = fma(w, resid_direct<ST, double>(U, bs[(long long)(q - 2) * Nx + x - 2]), U(0, 0));
                 Uo[(long long)q * W + x] = v;
-                // the neighbours' ghost rows: my rows 2, 3 are rows pnr+2, pnr+3 of the CTA above
-                // (rank c-1), my rows nr, nr+1 are rows 0, 1 of the CTA below (rank c+1)
                 double *up = nullptr, *dn = nullptr;
-                if (c > 0 && q <= 3) up = up_base + (long long)(q - 2) * W;
-                if (c < C - 1 && q >= nr) dn = dn_base + (long long)(q - nr) * W;
+                if (c > 0 && q < 2 + R) up = up_base + (long long)(q - 2) * W;
+                if (c < C - 1 && q > nr + 1 - R) dn = dn_base + (long long)(q - nr) * W;
                 if (up) up[x] = v;
                 if (dn) dn[x] = v;
                 if (ST == 17 && a.mirror) {  // store_node's reflection rule, in band coordinates
@@ -208,8 +212,20 @@ __global__ void __launch_bounds__(kClThreads) cluster_solve_kernel(ClArgs a) {
                         if (i == Nx) Uo[(long long)(q + 2) * W + Nx + 3] = v;
                     }
                 }
+            };
+            // the rows the neighbours need first (rows 2 .. 1+nbt and nr+2-nbb .. nr+1), then the
+            // arrive half of the cluster barrier, the interior rows while the others arrive, and
+            // the wait half: the interior rows read no ghost row, so a neighbour still finishing
+            // them is never disturbed by the next sweep's stores into its ghost rows
+            for (long long k = t; k < (long long)(nbt + nbb) * Nx; k += kClThreads) {
+                const int row = (int)(k / Nx), x = (int)(k % Nx) + 2;
+                node(row < nbt ? 2 + row : nr + 2 - nbb + (row - nbt), x);
             }
-            cl.sync();  // every band of the new buffer, and every ghost row, is complete
+            asm volatile("barrier.cluster.arrive.release;\n" ::: "memory");
+            for (long long k = t; k < (long long)(nr - nbt - nbb) * Nx; k += kClThreads)
+                node(2 + nbt + (int)(k / Nx), (int)(k % Nx) + 2);
+            __syncthreads();  // the interior rows, written after the arrive, for the next sweep
+            asm volatile("barrier.cluster.wait.acquire;\n" ::: "memory");
             cur ^= 1;
         }
         sweeps += a.M;
