@@ -21,6 +21,8 @@
 //
 // Per node, every kernel evaluates the same arithmetic, in the same order, as the
 // single-problem solver, so a problem's result does not depend on what it is batched with.
+#include <mutex>
+
 #include "engine.cuh"
 #include "grid_dev.cuh"
 #include "march4_dev.cuh"
@@ -393,9 +395,17 @@ int eng_sweep_blocks_per_sm() {
     return n;
 }
 
+// The blocked sweep kernel's dynamic shared-memory limit is one attribute of the function, shared by
+// every engine in the process (the server's lanes are several): it is only ever raised, so an engine
+// created later with a shallower depth never takes it from one that needs it.
 cudaError_t eng_prepare(size_t sweep_smem) {
-    return cudaFuncSetAttribute(eng_sweep<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)(sweep_smem > 0 ? sweep_smem : 0));
+    static std::mutex mu;
+    static size_t granted = 0;
+    std::lock_guard<std::mutex> lk(mu);
+    if (sweep_smem <= granted) return cudaSuccess;
+    cudaError_t e = cudaFuncSetAttribute(eng_sweep<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sweep_smem);
+    if (e == cudaSuccess) granted = sweep_smem;
+    return e;
 }
 
 cudaError_t eng_launch_step(const EngineDev &e, int grid_tiles, int grid_slots, size_t sweep_smem,

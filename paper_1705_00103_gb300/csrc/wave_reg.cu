@@ -29,6 +29,8 @@
 //
 // HBM traffic per update: about (8 B in + 4 B out) / K, plus the strip's 8-column and the row
 // block's 2H-row overlap with its neighbours.
+#include <type_traits>
+
 #include "cj_internal.h"
 #include "fold_dev.cuh"
 #include "grid_dev.cuh"
@@ -181,6 +183,15 @@ __device__ __forceinline__ void wr_resid(const float (&rc)[WC], const float (&rn
     }
 }
 
+// Calls f(std::integral_constant<int, I>) for I = B .. E-1, each with its index a constant.
+template <int B, int E, class F>
+__device__ __forceinline__ void wr_static_for(F &&f) {
+    if constexpr (B < E) {
+        f(std::integral_constant<int, B>{});
+        wr_static_for<B + 1, E>(f);
+    }
+}
+
 // First staged column of strip x: strip 0 starts at column 1 and stores lanes 0 .. 30, the
 // others start 4 columns before their first output column and store lanes 1 .. 30.
 __host__ __device__ __forceinline__ int wr_strip_x0(int x) { return x == 0 ? 1 : 121 + 120 * (x - 1); }
@@ -267,83 +278,113 @@ __global__ void __launch_bounds__(kWrThreads, ST == 17 || (ST == 9 && K == 4) ? 
         cp_async_commit();
     }
 
-    for (int t0 = 0; t0 < T; t0 += W) {
-#pragma unroll
-        for (int k = 0; k < W; ++k) {  // k = t mod W: the windows' ring positions are constants
-            const int t = t0 + k;
-            if (t >= T) break;
-            const int yin = ystart + t;
-            if (live && yin + D <= ylast)
-                wr_issue(e, r, g, c0, yin + D, &er[((t + D) & (kWrERing - 1)) * 32 + lane],
-                         &rr[((t + D) & (kWrRRing - 1)) * 32 + lane]);
-            cp_async_commit();
-            cp_async_wait<D>();  // row yin has landed
-            float4 ve = er[(t & (kWrERing - 1)) * 32 + lane];
-            if (yin < 1 || yin > Ny) {  // a mirrored row: apply its sign once, for every stage
-                float sy;
-                wr_row(yin, Ny, sy);
-                float4 *pr = &rr[(t & (kWrRRing - 1)) * 32 + lane];
-                const float4 vr = *pr;
-                ve = make_float4(sy * ve.x, sy * ve.y, sy * ve.z, sy * ve.w);
-                *pr = make_float4(sy * vr.x, sy * vr.y, sy * vr.z, sy * vr.w);
+    // Iterations ts .. te-1 (ts a multiple of W) are the steady state: the row entering is inside
+    // the grid and within the row block's reach, the row consumed is not mirrored, and the row
+    // leaving is an output row; they run without those tests (FAST), the warm-up and the drain
+    // with them.  The arithmetic is the same in both.
+    const int ts = (H + K * SK + W - 1) / W * W;
+    int te = min(T, min(Ny - y0 + H - D + 1, (y1 - y0) + 2 * H - D + 1));
+    te = te > ts ? ts + (te - ts) / W * W : ts;
+    const bool vec_lane = out_lane && c0 + 3 <= Nx && !(ST == 17 && (c0 == 1 || c0 + 3 >= Nx));
+    auto iter = [&](auto kc, auto fastc, int t0) {
+        constexpr int k = decltype(kc)::value;       // t mod W: the windows' ring positions are constants
+        constexpr bool FAST = decltype(fastc)::value;
+        const int t = t0 + k;
+        if (!FAST && t >= T) return;
+        const int yin = ystart + t;
+        if (FAST) {
+            if (live) {
+                const long long q = g.idx(c0, yin + D);
+                cp_async16(&er[((t + D) & (kWrERing - 1)) * 32 + lane], e + q);
+                cp_async16(&rr[((t + D) & (kWrRRing - 1)) * 32 + lane], r + q);
             }
-            // stage s: row yin - s SK from the rows of ages SK - R .. SK + R of its window; the
-            // row of age 0 is the one this iteration produces, so the K stages are computed
-            // first and the new rows (ve and the stages' outputs) enter the windows afterwards
-            float4 nr[K];  // new row of each window: nr[0] = ve, nr[s] = stage s's output
-            nr[0] = ve;
-            float4 ov;     // stage K's output
+        } else if (live && yin + D <= ylast) {
+            wr_issue(e, r, g, c0, yin + D, &er[((t + D) & (kWrERing - 1)) * 32 + lane],
+                     &rr[((t + D) & (kWrRRing - 1)) * 32 + lane]);
+        }
+        cp_async_commit();
+        cp_async_wait<D>();  // row yin has landed
+        float4 ve = er[(t & (kWrERing - 1)) * 32 + lane];
+        if (!FAST && (yin < 1 || yin > Ny)) {  // a mirrored row: apply its sign once, for every stage
+            float sy;
+            wr_row(yin, Ny, sy);
+            float4 *pr = &rr[(t & (kWrRRing - 1)) * 32 + lane];
+            const float4 vr = *pr;
+            ve = make_float4(sy * ve.x, sy * ve.y, sy * ve.z, sy * ve.w);
+            *pr = make_float4(sy * vr.x, sy * vr.y, sy * vr.z, sy * vr.w);
+        }
+        // stage s: row yin - s SK from the rows of ages SK - R .. SK + R of its window; the
+        // row of age 0 is the one this iteration produces, so the K stages are computed
+        // first and the new rows (ve and the stages' outputs) enter the windows afterwards
+        float4 nr[K];  // new row of each window: nr[0] = ve, nr[s] = stage s's output
+        nr[0] = ve;
+        float4 ov;     // stage K's output
 #pragma unroll
-            for (int s = 1; s <= K; ++s) {
-                const float4 rq = rr[((t - s * SK) & (kWrRRing - 1)) * 32 + lane];
-                const float rk[4] = {rq.x, rq.y, rq.z, rq.w};
-                float nv[4];
-                if (ST == 17) {
+        for (int s = 1; s <= K; ++s) {
+            const float4 rq = rr[((t - s * SK) & (kWrRRing - 1)) * 32 + lane];
+            const float rk[4] = {rq.x, rq.y, rq.z, rq.w};
+            float nv[4];
+            if (ST == 17) {
 #pragma unroll
-                    for (int m = 0; m < 4; ++m) {
-                        auto N = [&](int dx, int dy) { return win[s - 1][(k - SK + dy + 2 * W) % W][R + m + dx]; };
-                        const float uc = win[s - 1][(k - SK + 2 * W) % W][R + m];
-                        nv[m] = fmaf(wt.w[s - 1], resid_diff32<ST>(N, uc, rk[m]), uc);
-                    }
-                } else {
-                    float res[4];
-                    wr_resid<ST, R, WC>(win[s - 1][(k - SK + 2 * W) % W], win[s - 1][(k - SK + 1 + 2 * W) % W],
-                                        pr2[s - 1][(k + 1) & 1], pr2[s - 1][k & 1], rk, res);
-#pragma unroll
-                    for (int m = 0; m < 4; ++m) {
-                        const float uc = win[s - 1][(k - SK + 2 * W) % W][R + m];
-                        nv[m] = fmaf(wt.w[s - 1], res[m], uc);
-                    }
+                for (int m = 0; m < 4; ++m) {
+                    auto N = [&](int dx, int dy) { return win[s - 1][(k - SK + dy + 2 * W) % W][R + m + dx]; };
+                    const float uc = win[s - 1][(k - SK + 2 * W) % W][R + m];
+                    nv[m] = fmaf(wt.w[s - 1], resid_diff32<ST>(N, uc, rk[m]), uc);
                 }
-                if (s < K)
-                    nr[s] = make_float4(nv[0], nv[1], nv[2], nv[3]);
-                else
-                    ov = make_float4(nv[0], nv[1], nv[2], nv[3]);
-            }
-            // the new rows enter the windows, with the Dirichlet columns under one branch
-            if (edge) {
+            } else {
+                float res[4];
+                wr_resid<ST, R, WC>(win[s - 1][(k - SK + 2 * W) % W], win[s - 1][(k - SK + 1 + 2 * W) % W],
+                                    pr2[s - 1][(k + 1) & 1], pr2[s - 1][k & 1], rk, res);
 #pragma unroll
-                for (int s = 0; s < K; ++s) nr[s] = wr_edge_own<R>(ed, nr[s]);
-            }
-#pragma unroll
-            for (int s = 0; s < K; ++s) wr_put<R, WC>(win[s][k], nr[s], false, ed);
-            if (edge) {
-#pragma unroll
-                for (int s = 0; s < K; ++s) wr_edge_side<R, WC>(ed, win[s][k]);
-            }
-            const int yo = yin - K * SK;
-            if (out_lane && yo >= y0 && yo <= y1) {
-                const bool bnd = ST == 17 && (c0 == 1 || c0 + 3 >= Nx || yo == 1 || yo == Ny);
-                if (c0 + 3 <= Nx && !bnd) {
-                    *reinterpret_cast<float4 *>(out + g.idx(c0, yo)) = ov;
-                } else {
-                    const float o4[4] = {ov.x, ov.y, ov.z, ov.w};
-#pragma unroll
-                    for (int m = 0; m < 4; ++m)
-                        if (c0 + m <= Nx) store_node<R, float>(out, g, c0 + m, yo, o4[m]);
+                for (int m = 0; m < 4; ++m) {
+                    const float uc = win[s - 1][(k - SK + 2 * W) % W][R + m];
+                    nv[m] = fmaf(wt.w[s - 1], res[m], uc);
                 }
+            }
+            if (s < K)
+                nr[s] = make_float4(nv[0], nv[1], nv[2], nv[3]);
+            else
+                ov = make_float4(nv[0], nv[1], nv[2], nv[3]);
+        }
+        // the new rows enter the windows, with the Dirichlet columns under one branch
+        if (edge) {
+#pragma unroll
+            for (int s = 0; s < K; ++s) nr[s] = wr_edge_own<R>(ed, nr[s]);
+        }
+#pragma unroll
+        for (int s = 0; s < K; ++s) wr_put<R, WC>(win[s][k], nr[s], false, ed);
+        if (edge) {
+#pragma unroll
+            for (int s = 0; s < K; ++s) wr_edge_side<R, WC>(ed, win[s][k]);
+        }
+        const int yo = yin - K * SK;
+        if (FAST && ST != 17) {  // yo is an output row
+            if (vec_lane) {
+                *reinterpret_cast<float4 *>(out + g.idx(c0, yo)) = ov;
+            } else if (out_lane) {
+                const float o4[4] = {ov.x, ov.y, ov.z, ov.w};
+#pragma unroll
+                for (int m = 0; m < 4; ++m)
+                    if (c0 + m <= Nx) store_node<R, float>(out, g, c0 + m, yo, o4[m]);
+            }
+        } else if (out_lane && yo >= y0 && yo <= y1) {
+            const bool bnd = ST == 17 && (c0 == 1 || c0 + 3 >= Nx || yo == 1 || yo == Ny);
+            if (c0 + 3 <= Nx && !bnd) {
+                *reinterpret_cast<float4 *>(out + g.idx(c0, yo)) = ov;
+            } else {
+                const float o4[4] = {ov.x, ov.y, ov.z, ov.w};
+#pragma unroll
+                for (int m = 0; m < 4; ++m)
+                    if (c0 + m <= Nx) store_node<R, float>(out, g, c0 + m, yo, o4[m]);
             }
         }
+    };
+    for (int t0 = 0; t0 < T; t0 += W) {
+        if (t0 == ts && ts < te) {
+            for (; t0 < te; t0 += W) wr_static_for<0, W>([&](auto kc) { iter(kc, std::true_type{}, t0); });
+            if (t0 >= T) break;
+        }
+        wr_static_for<0, W>([&](auto kc) { iter(kc, std::false_type{}, t0); });
     }
     cp_async_wait<0>();
 }
