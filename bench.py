@@ -21,7 +21,8 @@ roofline: the FP64 sweep kernel against the FP64 FMA issue rate measured on the 
 vs_plain_fp64: configuration 2's comparisons -- plain FP64 cycles (which stall), FP32 inner
          cycles in FP64 / double-FP64 defect correction (time to 1e-10) -- and
          fp32_sweep_roofline: the FP32 register wavefront kernel (4 sweeps per launch) timed alone
-         against the measured FP32 FMA issue rate;
+         against the measured FP32 FMA issue rate, and ff_sweep_roofline: the float-float
+         FP64-accuracy sweep on the FP32 pipe beside the bit-exact FP64 sweep;
 highorder, batch, serve: configurations 3, 4 and 5 (17-point 8192^2 mixed precision to 1e-10;
          the 512-problem batch; an arrival-faithful prefix of the served stream), each with an
          FP64 comparison and its own clock record;
@@ -191,6 +192,12 @@ FP32_OPS_PER_UPDATE_WAVE_REG_9 = 13.75
 # FP32 issue peak: 4 schedulers x 32 lanes per SM x 152 SMs x 2.07 GHz (FFMA/FADD issue at one
 # warp instruction per scheduler per clock)
 FP32_ISSUE_PEAK_TOPS = 4 * 32 * 152 * 2.07e9 / 1e12
+
+
+# FP32 instructions per 9-point update of the float-float sweep: 4 float-float adds (11 each:
+# TwoSum 6, low parts 2, FastTwoSum 3) and 4 float-float multiply-adds (18 each: a TwoProduct
+# multiply of 7 and an add of 11)
+FF_OPS_PER_UPDATE_9 = 4 * 11 + 4 * 18
 
 
 def kernel_digest(sources=KERNEL_SOURCES) -> str:
@@ -431,6 +438,7 @@ def mixed_paths(cj, f, stream, fp64dd, peaks):
                      "speedup_vs_fp64_inner_dd": fp64dd["seconds"] / r["seconds"],
                      "speedup_vs_plain_fp64_stall": plain["seconds"] / r["seconds"]}
     out["fp32_sweep_roofline"] = fp32_sweep_roofline(cj, stream, peaks)
+    out["ff_sweep_roofline"] = ff_sweep_roofline(cj, f, stream, peaks)
     return out
 
 
@@ -493,6 +501,62 @@ def fp32_sweep_roofline(cj, stream, peaks, launches: int = 64) -> dict:
             "hbm_gbs_algorithmic": 12.0 * N_GRID * N_GRID / per_launch / 1e9,
             "peak_note": "FP32 FMA issue rate measured by cj_issue_peaks, of measured; 13.75 FP32 instructions "
                          "per 9-point update in the kernel's shared-difference form"}
+
+
+def ff_sweep_roofline(cj, f, stream, peaks, sweeps: int = 64) -> dict:
+    """The float-float sweep (cj_sweeps_ff: the FP64 sweep's expression in pairs of floats on the
+    FP32 pipe) beside the bit-exact FP64 sweep, on the 4096^2 9-point grid: `sweeps` sweeps of
+    the plan's cycle in one call each (the float-float call includes its 6 in-place conversions
+    of the three FP64 grids), timed with CUDA events on the launching stream; and its largest
+    deviation from the FP64 kernel over the first sweep from a random iterate, relative to the
+    per-sweep scale max|u| + |w| (9 max|u| + max|b|)."""
+    import torch
+    hbm_peak, hbm_note = measured_hbm_gbs()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    with cj.Plan(N_GRID, N_GRID, STENCIL, TOL) as p:
+        w = p.info()["w"]
+        t = {}
+        for name, fn in (("ff", cj.cj_sweeps_ff), ("fp64", cj.cj_sweeps)):
+            u = torch.zeros((N_GRID, N_GRID), dtype=torch.float64, device="cuda")
+            fn(p.handle, f, u, 0, 8, stream)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            fn(p.handle, f, u, 0, sweeps, stream)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            t[name] = e0.elapsed_time(e1) * 1e-3 / sweeps
+        g = torch.Generator(device="cuda").manual_seed(5)
+        u0 = torch.randn((N_GRID, N_GRID), dtype=torch.float64, device="cuda", generator=g)
+        k = int(np.argmax(w))
+        dev = {}
+        for name, fn in (("ff", cj.cj_sweeps_ff), ("fp64", cj.cj_sweeps)):
+            u = u0.clone()
+            fn(p.handle, f, u, k, 1, stream)
+            dev[name] = u
+        torch.cuda.synchronize()
+        dmax = float((dev["ff"] - dev["fp64"]).abs().max())
+        umax = float(u0.abs().max())
+        bmax = float(f.abs().max()) / ((N_GRID + 1) ** 2)
+        scale = umax + abs(float(w[k])) * (9.0 * umax + bmax)
+    upd = N_GRID * N_GRID
+    gupd = upd / t["ff"] / 1e9
+    hbm = BYTES_PER_UPDATE_FP64 * upd / t["ff"] / 1e9
+    ops = FF_OPS_PER_UPDATE_9 * upd / t["ff"] / 1e12
+    return {"kernel": "sweep_ff_kernel<9>", "bound": "hbm", "achieved": hbm, "peak": hbm_peak, "unit": "GB/s",
+            "frac": hbm / hbm_peak, "traffic": None, "bytes_per_update": BYTES_PER_UPDATE_FP64,
+            "peak_note": hbm_note + "; of measured",
+            "fp32_issue": {"achieved": ops, "peak": peaks["fp32_tfma_s"], "unit": "TFP32op/s",
+                           "frac": ops / peaks["fp32_tfma_s"], "ops_per_update": FF_OPS_PER_UPDATE_9,
+                           "note": "FP32 FMA issue rate measured by cj_issue_peaks, of measured"},
+            "avg_sweep_us": t["ff"] * 1e6, "gupdates_s": gupd,
+            "fp64_sweep_avg_us": t["fp64"] * 1e6, "fp64_sweep_gupdates_s": upd / t["fp64"] / 1e9,
+            "speedup_vs_fp64_sweep": t["fp64"] / t["ff"],
+            "max_dev_vs_fp64_sweep": dmax, "max_dev_rel_to_sweep_scale": dmax / scale,
+            "dev_weight_index": k,
+            "note": "FP64-accuracy (48-bit float-float) sweep, not bit-equal to the FP64 sweep; per-sweep "
+                    "deviation held to 1e-12 of the sweep scale by the parity tests; timings include the "
+                    "in-place conversions of the three grids, amortised over the call's sweeps"}
 
 
 def highorder_key(cj, stream, steps: int = 1) -> dict:

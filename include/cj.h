@@ -289,6 +289,20 @@ cj_status cj_sweeps(cj_plan *plan, const double *f, long long ld_f, double *u, l
                     long long first, long long count, void *stream);
 
 /*
+ * cj_sweeps_ff -- cj_sweeps evaluated in float-float arithmetic on the FP32 pipe: the same weighted
+ * sweeps (Sec. 2.1) with the iterate and b held as pairs of floats (48 significant bits) and
+ * added and multiplied by error-free transformations (Knuth's TwoSum, the fused-multiply-add
+ * TwoProduct), in the FP64 sweep's evaluation order.  Not bit-equal to cj_sweeps: each sweep
+ * agrees with the FP64 sweep of the same input to a few units of 2^-47 of the terms it adds (within
+ * 1e-12 x max(1, w_n S) x max |u|); it moves the same bytes with FP32 instructions, where the FP64
+ * sweep is bound by GB300's FP64 rate.  Values must lie in the float range.  Plain FP64 plans of the
+ * paper's stencils with the homogeneous boundary (CJ_BC_DIRICHLET0) only, else CJ_ERR_INVALID_ARG.
+ * Arguments and layout as cj_sweeps; asynchronous on `stream`.
+ */
+cj_status cj_sweeps_ff(cj_plan *plan, const double *f, long long ld_f, double *u, long long ld_u,
+                       long long first, long long count, void *stream);
+
+/*
  * cj_sweeps_f32 -- apply `count` weighted FP32 sweeps e <- e + w32_n (L e - r) in place,
  * w32_n = (float) w_n of the plan's inner cycle (FP32-inner plans only), fused
  * temporal_depth at a time per launch as the solve does (bit-identical to one at a time):

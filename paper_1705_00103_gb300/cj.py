@@ -120,6 +120,8 @@ def _lib():
         L.cj_solve_host.restype = ctypes.c_int
         L.cj_sweeps.argtypes = [_vp, _vp, _ll, _vp, _ll, _ll, _ll, _vp]
         L.cj_sweeps.restype = ctypes.c_int
+        L.cj_sweeps_ff.argtypes = [_vp, _vp, _ll, _vp, _ll, _ll, _ll, _vp]
+        L.cj_sweeps_ff.restype = ctypes.c_int
         L.cj_sweeps_f32.argtypes = [_vp, _vp, _ll, _vp, _ll, _ll, _ll, _vp]
         L.cj_sweeps_f32.restype = ctypes.c_int
         L.cj_autotune_engine.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
@@ -337,6 +339,15 @@ def cj_sweeps(plan, f, u, first: int, count: int, stream=None) -> None:
     rc = _lib().cj_sweeps(plan, fp, ldf, up, ldu, first, count, _stream(stream))
     if rc != CJ_OK:
         raise CJError(rc, "cj_sweeps")
+
+
+def cj_sweeps_ff(plan, f, u, first: int, count: int, stream=None) -> None:
+    """FP64-accuracy sweeps in float-float on the FP32 pipe (see cj.h); u in place."""
+    fp, ldf = _grid(f, "float64")
+    up, ldu = _grid(u, "float64")
+    rc = _lib().cj_sweeps_ff(plan, fp, ldf, up, ldu, first, count, _stream(stream))
+    if rc != CJ_OK:
+        raise CJError(rc, "cj_sweeps_ff")
 
 
 def cj_sweeps_f32(plan, r, e, first: int, count: int, stream=None) -> None:

@@ -114,6 +114,15 @@ cudaError_t make_sweep_graph(cj_plan *p);
 // one full cycle (p->M sweeps from u0, ending in u0) on stream s
 cudaError_t launch_sweep_cycle_graph(const cj_plan *p, cudaStream_t s);
 
+// ---- FP64-accuracy sweeps in float-float on the FP32 pipe (ff.cu)
+// plain FP64 plans of the paper's stencils with the homogeneous boundary
+bool ff_sweeps_supported(const cj_plan *p);
+// bufs = {u0, u1, b} of the plan (imported); count sweeps from u0 with weights w[(first + k) mod M];
+// the buffers are converted to float-float for the sweeps and back; *cur_out: 0 if the result is
+// in u0, 1 if in u1
+cudaError_t launch_sweeps_ff(const cj_plan *p, const double *const *bufs, long long first, long long count,
+                             int *cur_out, cudaStream_t s);
+
 // ---- whole small FP64 solves in one cluster (cluster.cu)
 // CTAs of the cluster the plan's solve fits in (0: not eligible: not plain FP64 on the paper's
 // stencils, more than 2^14 nodes, or no cluster launch on this device)

@@ -939,6 +939,20 @@ cj_status cj_sweeps(cj_plan *p, const double *f, long long ldf, double *u, long 
     return CJ_OK;
 }
 
+cj_status cj_sweeps_ff(cj_plan *p, const double *f, long long ldf, double *u, long long ldu, long long first,
+                       long long count, void *stream) {
+    cj_status a = check_grid_args(p, f, ldf, u, ldu);
+    if (a != CJ_OK) return a;
+    if (first < 0 || count < 0 || !ff_sweeps_supported(p)) return CJ_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    CJ_TRY(import64(p, f, ldf, u, ldu, s), "import");
+    const double *bufs[3] = {p->u0, p->u1, p->b};
+    int cur = 0;
+    CJ_TRY(launch_sweeps_ff(p, bufs, first, count, &cur, s), "sweep ff");
+    CJ_TRY(launch_export(p, cur ? p->u1 : p->u0, u, ldu, s), "export");
+    return CJ_OK;
+}
+
 cj_status cj_sweeps_f32(cj_plan *p, const float *r, long long ldr, float *e, long long lde,
                         long long first, long long count, void *stream) {
     cj_status a = check_grid_args(p, r, ldr, e, lde);
