@@ -55,10 +55,11 @@
  *      terms that are exact in FP64 (power-of-two multiples of u_hi and b), added by the
  *      error-free TwoSum cascade (Ogita, Rump and Oishi's Sum2); D L u_lo is added in plain
  *      FP64.  The correction is added by TwoSum.  This removes the FP64 floor of R8.
- *   R14 FP32 evaluation (not in the paper): the FP32 inner sweep evaluates L e - r in
- *      difference form, sum_k c_k (e_k - e_C) - r, grouped like R9 without a centre term;
- *      on a 8192^2 grid the pair-sum form loses ~40 % of the lowest mode's L e in FP32, the
- *      difference form keeps it to a few FP32 ulps.
+ *   R14 FP32 evaluation (not in the paper): the FP32 inner sweep evaluates L e - r from
+ *      horizontal and vertical second differences of neighbour differences, an exact
+ *      rewriting of Eq. 1 and Eq. 2's stencils (see resid_at32); on a 8192^2 grid the
+ *      pair-sum form loses ~40 % of the lowest mode's L e in FP32, the difference forms keep
+ *      it to a few FP32 ulps.
  *   R15 non-homogeneous Dirichlet (Sec. 3.3's test problem): the data fill the two-node
  *      ring around the interior and stay fixed (see orc_solve_bc).
  *   R16 real-error stop (Sec. 3.4, Fig. 4 right): the infinity norm of u - u_exact tested
@@ -357,29 +358,40 @@ static float at32(const float *u, int Nx, int Ny, int i, int j) {
     return s * u[(size_t)(j - 1) * Nx + (i - 1)];
 }
 
-/* r = (L e)(i, j) - rk in FP32, in difference form (reading R14): every neighbour enters as
- * its difference from the centre, (e_k - e_C), which is exact in FP32 whenever the two are
- * within a factor 2 of each other (Sterbenz), as they are for the smooth low modes the
- * solver is slowest on; L e = sum_k c_k (e_k - e_C) because the stencil coefficients sum
- * to zero.  Groups as in resid_at (pairs, axis and diagonal groups), coefficients are the
- * FP32 quotients (e.g. 4.0f/6.0f); no centre term. */
+/* r = (L e)(i, j) - rk in FP32, in second-difference form (reading R14).  Every value enters
+ * through differences of neighbours, which are exact in FP32 whenever the two are within a
+ * factor 2 of each other (Sterbenz), as they are for the smooth low modes the solver is
+ * slowest on.  With the horizontal and vertical second differences at spacing s,
+ *   X_s(dy) = (e(i+s, j+dy) - e(i, j+dy)) - (e(i, j+dy) - e(i-s, j+dy)),
+ *   Y_s     = (e(i, j+s) - e(i, j)) - (e(i, j) - e(i, j-s)),
+ * the paper's stencils are, exactly:
+ *   5-point (Table 3):          h^2 L = X_1(0) + Y_1;
+ *   9-point (Eq. 1, alpha 2/3): 6 h^2 L = X_1(-1) + X_1(1) + 4 X_1(0) + 6 Y_1 =: S_1
+ *     (the stencil [1 4 1; 4 -20 4; 1 4 1] is the product of [1 4 1] across x and y, less
+ *     36 at the centre);
+ *   17-point (Eq. 2):          72 h^2 L = 16 S_1 - S_2, S_2 the 9-point form at spacing 2
+ *     (X_2(-2) + X_2(2) + 4 X_2(0) + 6 Y_2).
+ * Coefficients are the FP32 quotients (e.g. 2.0f/3.0f).  The second differences are formed
+ * once per row and node and shared by the rows that use them in the GPU kernels; here they
+ * are recomputed per node. */
 static float resid_at32(int st, const float *u, int Nx, int Ny, int i, int j, float rk) {
     float uC = at32(u, Nx, Ny, i, j);
-#define D32(di, dj) (at32(u, Nx, Ny, i + (di), j + (dj)) - uC)
-    float v1 = D32(0, -1) + D32(0, 1);
-    float p0 = D32(-1, 0) + D32(1, 0);
-    if (st == 5) return (p0 + v1) - rk;
-    float pm = D32(-1, -1) + D32(1, -1);
-    float pp = D32(-1, 1) + D32(1, 1);
-    if (st == 9) return fmaf(4.0f / 6.0f, p0 + v1, fmaf(1.0f / 6.0f, pm + pp, -rk));
-    float v2 = D32(0, -2) + D32(0, 2);
-    float P0 = D32(-2, 0) + D32(2, 0);
-    float Pm = D32(-2, -2) + D32(2, -2);
-    float Pp = D32(-2, 2) + D32(2, 2);
-#undef D32
-    return fmaf(64.0f / 72.0f, p0 + v1,
-                fmaf(-4.0f / 72.0f, P0 + v2,
-                     fmaf(16.0f / 72.0f, pm + pp, fmaf(-1.0f / 72.0f, Pm + Pp, -rk))));
+#define E32(di, dj) at32(u, Nx, Ny, i + (di), j + (dj))
+#define X32(s, dy) ((E32(s, dy) - E32(0, dy)) - (E32(0, dy) - E32(-(s), dy)))
+    float Y1 = (E32(0, 1) - uC) - (uC - E32(0, -1));
+    float X1c = X32(1, 0);
+    if (st == 5) return (X1c + Y1) - rk;
+    float X1s = X32(1, -1) + X32(1, 1);
+    if (st == 9) return fmaf(1.0f / 6.0f, X1s, fmaf(2.0f / 3.0f, X1c, Y1 - rk));
+    float Y2 = (E32(0, 2) - uC) - (uC - E32(0, -2));
+    float X2c = X32(2, 0);
+    float X2s = X32(2, -2) + X32(2, 2);
+#undef X32
+#undef E32
+    return fmaf(2.0f / 9.0f, X1s,
+                fmaf(8.0f / 9.0f, X1c,
+                     fmaf(4.0f / 3.0f, Y1,
+                          fmaf(-1.0f / 72.0f, X2s, fmaf(-1.0f / 18.0f, X2c, fmaf(-1.0f / 12.0f, Y2, -rk))))));
 }
 
 /* One FP32 weighted sweep e_out = e + w (L e - r). */

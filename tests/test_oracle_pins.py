@@ -455,6 +455,25 @@ def test_fp32_sweep_exact_on_integers():
 
 
 @pytest.mark.parametrize("st", STENCILS)
+def test_fp32_impulse_response_is_the_printed_stencil(st):
+    """The FP32 sweep (second-difference form) of a unit impulse with r = 0 and w = 1 gives, at
+    every node within reach, the coefficient of Fig. 1 / Table 3 at that offset (zero where the
+    paper prints none, e.g. the 17-point stencil's knight-move offsets), to FP32 rounding: each
+    coefficient's FP32 quotient and the rounding of the centre's 1 + c."""
+    n = 11
+    e = np.zeros((n, n), dtype=np.float32)
+    c = n // 2
+    e[c, c] = 1.0
+    out = orc.sweep_f32(st, e, np.zeros_like(e), np.float32(1.0)).astype(np.float64)
+    out[c, c] -= 1.0
+    for dy in range(-3, 4):
+        for dx in range(-3, 4):
+            # node (c + dx, c + dy) sees the impulse at offset (-dx, -dy); the stencils are symmetric
+            want = COEF[st].get((-dx, -dy), 0.0)
+            assert abs(out[c + dy, c + dx] - want) <= 4e-7, (dx, dy, out[c + dy, c + dx], want)
+
+
+@pytest.mark.parametrize("st", STENCILS)
 @pytest.mark.parametrize("N", [1024, 8192])
 def test_fp32_sweep_keeps_the_lowest_mode(st, N):
     """On the smoothest mode of a fine grid, where L e is ~1e-7 of the values that cancel in
