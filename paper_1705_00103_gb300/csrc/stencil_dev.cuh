@@ -145,25 +145,33 @@ __device__ __forceinline__ void march(const T *__restrict__ u, const T *__restri
 
 
 
-// FP32 residual in difference form, L e - rk = sum_k c_k (e_k - e_C) - rk: every neighbour
-// enters as its (for smooth e, exact) difference from the centre, so the smooth low modes
-// keep their digits on fine grids where the neighbour sums would cancel against the centre
-// term.  N(di, dj) returns the neighbour at offset (di, dj); groups as in the FP64 order.
+// FP32 residual in second-difference form, L e - rk, from the horizontal and vertical second
+// differences at spacing s, X_s(dy) = (e(s, dy) - e(0, dy)) - (e(0, dy) - e(-s, dy)) and
+// Y_s = (e(0, s) - e_C) - (e_C - e(0, -s)): every value enters through a neighbour difference,
+// so the smooth low modes keep their digits on fine grids where neighbour sums would cancel
+// against the centre.  The forms are exact rewritings of the stencils: 5-point X_1(0) + Y_1;
+// 9-point (Eq. 1) (X_1(-1) + X_1(1) + 4 X_1(0))/6 + Y_1 ([1 4 1; 4 -20 4; 1 4 1] is [1 4 1]
+// across x times [1 4 1] across y, less 36 at the centre); 17-point (Eq. 2) 16/72 of the
+// 9-point form times 6 less 1/72 of the same at spacing 2.  N(di, dj) returns the neighbour
+// at offset (di, dj); the operation order is the FP32 reference's.
 template <int ST, class F>
 __device__ __forceinline__ float resid_diff32(F N, float uC, float rk) {
-    const float v1 = (N(0, -1) - uC) + (N(0, 1) - uC);
-    const float p0 = (N(-1, 0) - uC) + (N(1, 0) - uC);
-    if (ST == 5) return (p0 + v1) - rk;
-    const float pm = (N(-1, -1) - uC) + (N(1, -1) - uC);
-    const float pp = (N(-1, 1) - uC) + (N(1, 1) - uC);
-    if (ST == 9) return fmaf(4.0f / 6.0f, p0 + v1, fmaf(1.0f / 6.0f, pm + pp, -rk));
-    const float v2 = (N(0, -2) - uC) + (N(0, 2) - uC);
-    const float P0 = (N(-2, 0) - uC) + (N(2, 0) - uC);
-    const float Pm = (N(-2, -2) - uC) + (N(2, -2) - uC);
-    const float Pp = (N(-2, 2) - uC) + (N(2, 2) - uC);
-    return fmaf(64.0f / 72.0f, p0 + v1,
-                fmaf(-4.0f / 72.0f, P0 + v2,
-                     fmaf(16.0f / 72.0f, pm + pp, fmaf(-1.0f / 72.0f, Pm + Pp, -rk))));
+    auto X = [&](int sp, int dy) {
+        const float c = N(0, dy);
+        return (N(sp, dy) - c) - (c - N(-sp, dy));
+    };
+    const float Y1 = (N(0, 1) - uC) - (uC - N(0, -1));
+    const float X1c = (N(1, 0) - uC) - (uC - N(-1, 0));
+    if (ST == 5) return (X1c + Y1) - rk;
+    const float X1s = X(1, -1) + X(1, 1);
+    if (ST == 9) return fmaf(1.0f / 6.0f, X1s, fmaf(2.0f / 3.0f, X1c, Y1 - rk));
+    const float Y2 = (N(0, 2) - uC) - (uC - N(0, -2));
+    const float X2c = (N(2, 0) - uC) - (uC - N(-2, 0));
+    const float X2s = X(2, -2) + X(2, 2);
+    return fmaf(2.0f / 9.0f, X1s,
+                fmaf(8.0f / 9.0f, X1c,
+                     fmaf(4.0f / 3.0f, Y1,
+                          fmaf(-1.0f / 72.0f, X2s, fmaf(-1.0f / 18.0f, X2c, fmaf(-1.0f / 12.0f, Y2, -rk))))));
 }
 
 

@@ -141,45 +141,92 @@ __device__ __forceinline__ void wr_put(float (&row)[WC], float4 v, bool edge, co
     if (edge) wr_edge_side<R, WC>(ed, row);
 }
 
-// Differences of the row pair (y, y+1) of one stage's input at this lane's columns:
-// dN[m] = e(c0+m, y+1) - e(c0+m, y); dNE[j] = e(c0+j, y+1) - e(c0-1+j, y);
-// dNW[j] = e(c0-1+j, y+1) - e(c0+j, y).  Node (i, y) uses them for its upper neighbours and
-// node (i, y+1), one iteration later, for its lower ones, negated: e(a) - e(b) is computed
-// as -(e(b) - e(a)), which round-to-nearest makes exact.
+// Per-row differences of one stage's input at this lane's columns, alternating between
+// iterations: dN[m] = e(c0+m, y+1) - e(c0+m, y) for the row pair (y, y+1), and (9-point) X[m],
+// the horizontal second difference of row y + 1.  Node (i, y) uses dN for its upper
+// neighbour and node (i, y+1), one iteration later, for its lower one (the two signs of the
+// same difference: e(a) - e(b) = -(e(b) - e(a)) exactly under round-to-nearest); a row's X
+// serves the three rows whose stencils include it.
 struct WrPair {
-    float dN[4], dNE[5], dNW[5];
+    float dN[4], X[4];
 };
 
-// (L e - r) at this lane's four nodes of the centre row rc (upper row rn; lo: the pair
-// (y-1, y) from the previous iteration; hi: filled here with the pair (y, y+1)), in the
-// operation order of resid_diff32, so each node's result is bit-identical to it.  The
-// horizontal differences are shared the same way: e(i-1) - e(i) = -(e(i) - e(i-1)).
+// (L e - r) at this lane's four nodes of the centre row rc (upper row rn; lo: the entries of
+// the previous iteration, dN of (y-1, y) and X of row y; hi: on entry the entries of two
+// iterations back, whose X is that of row y - 1; filled here with dN of (y, y+1) and X of row
+// y + 1), in the operation order of resid_diff32, so each node's result is bit-identical to it.
 template <int ST, int R, int WC>
 __device__ __forceinline__ void wr_resid(const float (&rc)[WC], const float (&rn)[WC], const WrPair &lo,
                                          WrPair &hi, const float (&rk)[4], float (&res)[4]) {
-    float dE[5];  // dE[j] = e(c0 + j) - e(c0 - 1 + j)
+    float dN[4];
 #pragma unroll
-    for (int j = 0; j < 5; ++j) dE[j] = rc[R + j] - rc[R + j - 1];
+    for (int m = 0; m < 4; ++m) dN[m] = rn[R + m] - rc[R + m];
+    if (ST == 5) {
+        float dE[5];  // dE[j] = e(c0 + j) - e(c0 - 1 + j) of the centre row
 #pragma unroll
-    for (int m = 0; m < 4; ++m) hi.dN[m] = rn[R + m] - rc[R + m];
-    if (ST == 9) {
+        for (int j = 0; j < 5; ++j) dE[j] = rc[R + j] - rc[R + j - 1];
 #pragma unroll
-        for (int j = 0; j < 5; ++j) {
-            hi.dNE[j] = rn[R + j] - rc[R + j - 1];
-            hi.dNW[j] = rn[R + j - 1] - rc[R + j];
+        for (int m = 0; m < 4; ++m) {
+            const float Y1 = dN[m] - lo.dN[m];
+            const float X1c = dE[m + 1] - dE[m];
+            res[m] = (X1c + Y1) - rk[m];
+            hi.dN[m] = dN[m];
+        }
+    } else {
+        float dE[5];  // of the upper row
+#pragma unroll
+        for (int j = 0; j < 5; ++j) dE[j] = rn[R + j] - rn[R + j - 1];
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+            const float Xn = dE[m + 1] - dE[m];
+            const float Y1 = dN[m] - lo.dN[m];
+            const float X1s = hi.X[m] + Xn;
+            res[m] = fmaf(1.0f / 6.0f, X1s, fmaf(2.0f / 3.0f, lo.X[m], Y1 - rk[m]));
+            hi.dN[m] = dN[m];
+            hi.X[m] = Xn;
         }
     }
+}
+
+// The 17-point stencil's per-row entries of one stage's input, in rings indexed by the
+// iteration (the window's ring length is 6, so every index below is a constant): X1 and X2,
+// the horizontal second differences at spacings 1 and 2 of the row that is two above the
+// centre when it is formed, serve the centre rows within one (X1) and at 0 or 2 (X2) rows of
+// it.  The vertical differences are formed from the window's rows at each centre.
+struct Wr17 {
+    float x1[3][4], x2[6][4];
+};
+
+// (L e - r) of the 17-point stencil at this lane's four nodes of the centre row rc (rows below
+// it rm2, rm1, above it r1, r2) at iteration Q (mod 6), in the operation order of resid_diff32.
+template <int Q, int WC>
+__device__ __forceinline__ void wr_resid17(const float (&rm2)[WC], const float (&rm1)[WC], const float (&rc)[WC],
+                                           const float (&r1)[WC], const float (&r2)[WC], Wr17 &z, const float (&rk)[4],
+                                           float (&res)[4]) {
+    constexpr int R = 2;
+    constexpr int n3 = Q % 3, c3 = (Q + 1) % 3, u3 = (Q + 2) % 3;  // X1 of rows y-1 (then y+2), y, y+1
+    float dE1[5], dE2[6];  // dE1[j] = e(c0+j) - e(c0+j-1), dE2[q] = e(c0+q) - e(c0+q-2) of row y + 2
+#pragma unroll
+    for (int j = 0; j < 5; ++j) dE1[j] = r2[R + j] - r2[R + j - 1];
+#pragma unroll
+    for (int q = 0; q < 6; ++q) dE2[q] = r2[R + q] - r2[R + q - 2];
 #pragma unroll
     for (int m = 0; m < 4; ++m) {
-        const float v1 = -lo.dN[m] + hi.dN[m];
-        const float p0 = -dE[m] + dE[m + 1];
-        if (ST == 5) {
-            res[m] = (p0 + v1) - rk[m];
-        } else {
-            const float pm = -lo.dNE[m] + -lo.dNW[m + 1];
-            const float pp = hi.dNW[m] + hi.dNE[m + 1];
-            res[m] = fmaf(4.0f / 6.0f, p0 + v1, fmaf(1.0f / 6.0f, pm + pp, -rk[m]));
-        }
+        const float X1n = dE1[m + 1] - dE1[m];
+        const float X2n = dE2[m + 2] - dE2[m];
+        const float d1 = r1[R + m] - rc[R + m];
+        const float d2 = r2[R + m] - rc[R + m];
+        const float Y1 = d1 - (rc[R + m] - rm1[R + m]);
+        const float Y2 = d2 - (rc[R + m] - rm2[R + m]);
+        const float X1s = z.x1[n3][m] + z.x1[u3][m];
+        const float X2s = z.x2[(Q + 2) % 6][m] + X2n;
+        res[m] = fmaf(2.0f / 9.0f, X1s,
+                      fmaf(8.0f / 9.0f, z.x1[c3][m],
+                           fmaf(4.0f / 3.0f, Y1,
+                                fmaf(-1.0f / 72.0f, X2s,
+                                     fmaf(-1.0f / 18.0f, z.x2[(Q + 4) % 6][m], fmaf(-1.0f / 12.0f, Y2, -rk[m]))))));
+        z.x1[n3][m] = X1n;
+        z.x2[Q][m] = X2n;
     }
 }
 
@@ -253,17 +300,21 @@ __global__ void __launch_bounds__(kWrThreads, ST == 17 || (ST == 9 && K == 4) ? 
     // win[s][q][c]: input of stage s+1 as a ring of W rows (the row produced at iteration t
     // sits at q = t mod W), columns c0 - R .. c0 + 3 + R
     float win[K][W][WC];
-    // pair differences of each stage's input, alternating between iterations (k & 1): the
-    // pair computed at one iteration is the lower pair of the next
+    // per-row differences of each stage's input, alternating between iterations (k & 1): the
+    // entries computed at one iteration are the lower ones of the next
     WrPair pr2[K][2];
+    Wr17 z17[ST == 17 ? K : 1];
+    if (ST == 17) {
+        float *zp = &z17[0].x1[0][0];
+#pragma unroll
+        for (int q = 0; q < (int)(sizeof(z17) / sizeof(float)); ++q) zp[q] = 0.0f;
+    }
 #pragma unroll
     for (int s = 0; s < K; ++s)
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
 #pragma unroll
-            for (int m = 0; m < 4; ++m) pr2[s][h].dN[m] = 0.0f;
-#pragma unroll
-            for (int j = 0; j < 5; ++j) pr2[s][h].dNE[j] = pr2[s][h].dNW[j] = 0.0f;
+            for (int m = 0; m < 4; ++m) pr2[s][h].dN[m] = pr2[s][h].X[m] = 0.0f;
         }
 #pragma unroll
     for (int s = 0; s < K; ++s)
@@ -325,11 +376,14 @@ __global__ void __launch_bounds__(kWrThreads, ST == 17 || (ST == 9 && K == 4) ? 
             const float rk[4] = {rq.x, rq.y, rq.z, rq.w};
             float nv[4];
             if (ST == 17) {
+                float res[4];
+                wr_resid17<k, WC>(win[s - 1][(k - SK - 2 + 2 * W) % W], win[s - 1][(k - SK - 1 + 2 * W) % W],
+                                  win[s - 1][(k - SK + 2 * W) % W], win[s - 1][(k - SK + 1 + 2 * W) % W],
+                                  win[s - 1][(k - SK + 2 + 2 * W) % W], z17[s - 1], rk, res);
 #pragma unroll
                 for (int m = 0; m < 4; ++m) {
-                    auto N = [&](int dx, int dy) { return win[s - 1][(k - SK + dy + 2 * W) % W][R + m + dx]; };
                     const float uc = win[s - 1][(k - SK + 2 * W) % W][R + m];
-                    nv[m] = fmaf(wt.w[s - 1], resid_diff32<ST>(N, uc, rk[m]), uc);
+                    nv[m] = fmaf(wt.w[s - 1], res[m], uc);
                 }
             } else {
                 float res[4];

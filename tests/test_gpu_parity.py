@@ -275,6 +275,27 @@ def test_full_size_fp32_temporal_sweeps_bit_exact(cj, torch, st):
     np.testing.assert_array_equal(got, ref)
 
 
+@pytest.mark.parametrize("depth", (1, 2))
+def test_full_size_fp32_17_point_8192_sweeps_bit_exact(cj, torch, depth):
+    """Five FP32 inner sweeps of the 17-point 8192^2 grid (the high-order workload's hot kernel) at
+    depth 1 (one sweep per launch) and depth 2 (the register wavefront, the default at this
+    size), against the oracle's one-sweep-at-a-time FP32 sweeps on the whole grid."""
+    N, st = 8192, 17
+    rng = np.random.default_rng(29 + depth)
+    r = rng.standard_normal((N, N)).astype(np.float32)
+    e = rng.standard_normal((N, N)).astype(np.float32)
+    with cj.Plan(N, N, st, 1e-10, precision=cj.CJ_FP32_INNER, inner_cycle=64, temporal_depth=depth) as p:
+        kmin, kmax = orc.kappa_bounds(st, N, N)
+        w32 = orc.sweep_coeffs(st, kmin, kmax, 64).astype(np.float32)
+        ed = dev(torch, e)
+        cj.cj_sweeps_f32(p.handle, dev(torch, r), ed, 3, 5)
+        got = ed.cpu().numpy()
+    ref = e
+    for k in range(5):
+        ref = orc.sweep_f32(st, ref, r, w32[(3 + k) % 64])
+    np.testing.assert_array_equal(got, ref)
+
+
 def test_full_size_residual(cj, torch):
     N, st = 4096, 9
     f = workloads.smooth_random_rhs(N, N, 1)
@@ -287,12 +308,12 @@ def test_full_size_residual(cj, torch):
     assert linf == pytest.approx(m / np.abs(b).max(), rel=1e-14)
 
 
-@pytest.mark.parametrize("st", (9, 17))
-def test_full_size_mixed_dd_meets_the_tolerance_by_the_oracle(cj, torch, st):
-    """The 4096^2 FP32-inner / double-FP64-outer solve to 1e-10 (the benchmark's problem, and the
-    17-point stencil): its relative residual as the oracle evaluates it, the double-FP64 defect
-    of u_hi + u_lo, is within the tolerance and agrees with the library's own figure."""
-    N = 4096
+@pytest.mark.parametrize("st,N", [(9, 4096), (17, 4096), (17, 8192)])
+def test_full_size_mixed_dd_meets_the_tolerance_by_the_oracle(cj, torch, st, N):
+    """The FP32-inner / double-FP64-outer solve to 1e-10 of the 4096^2 problems (9 points: the
+    benchmark's problem; 17 points) and of the 17-point 8192^2 high-order problem: its relative
+    residual as the oracle evaluates it, the double-FP64 defect of u_hi + u_lo, is within the
+    tolerance and agrees with the library's own figure."""
     f = workloads.smooth_random_rhs(N, N, 2)
     with cj.Plan(N, N, st, 1e-10, precision=cj.CJ_FP32_INNER_DD) as p:
         u = torch.zeros((N, N), dtype=torch.float64, device="cuda")
