@@ -186,14 +186,18 @@ class ClockSampler:
 KERNEL_SOURCES = ("kernels.cu", "stencil_dev.cuh", "grid_dev.cuh")
 # sources of the FP32 register wavefront kernel (temporal blocking)
 WAVE_REG_SOURCES = ("wave_reg.cu", "fold_dev.cuh", "grid_dev.cuh", "stencil_dev.cuh", "cj_internal.h")
-# FP32 instructions per 9-point update of the register wavefront kernel: 4.75 differences
-# (shared between neighbours), 4 pair sums, 2 group sums, 2 coefficient fmas, 1 update fma
-FP32_OPS_PER_UPDATE_WAVE_REG_9 = 13.75
+# FP32 instructions per 9-point update of the register wavefront kernel (second-difference form):
+# 1.25 first differences along the row (shared between neighbours) and 1 second difference, both
+# for the row entering the stencil; 1 vertical difference and 1 second difference; 1 sum of the
+# outer rows' second differences, 1 subtraction of r, 2 coefficient fmas, 1 update fma
+FP32_OPS_PER_UPDATE_WAVE_REG_9 = 9.25
 # FP32 issue peak: 4 schedulers x 32 lanes per SM x 152 SMs x 2.07 GHz (FFMA/FADD issue at one
 # warp instruction per scheduler per clock)
 FP32_ISSUE_PEAK_TOPS = 4 * 32 * 152 * 2.07e9 / 1e12
 
 
+# sources of the float-float sweep kernel
+FF_SOURCES = ("ff.cu", "grid_dev.cuh", "stencil_dev.cuh", "cj_internal.h")
 # FP32 instructions per 9-point update of the float-float sweep: 4 float-float adds (11 each:
 # TwoSum 6, low parts 2, FastTwoSum 3) and 4 float-float multiply-adds (18 each: a TwoProduct
 # multiply of 7 and an add of 11)
@@ -499,8 +503,8 @@ def fp32_sweep_roofline(cj, stream, peaks, launches: int = 64) -> dict:
             "dram_bytes_per_update": None if traffic is None else traffic / upd,
             # algorithmic bytes: one round trip of e, r, e' (12 B per node) per launch of 4 sweeps
             "hbm_gbs_algorithmic": 12.0 * N_GRID * N_GRID / per_launch / 1e9,
-            "peak_note": "FP32 FMA issue rate measured by cj_issue_peaks, of measured; 13.75 FP32 instructions "
-                         "per 9-point update in the kernel's shared-difference form"}
+            "peak_note": "FP32 FMA issue rate measured by cj_issue_peaks, of measured; 9.25 FP32 instructions "
+                         "per 9-point update in the kernel's shared second-difference form"}
 
 
 def ff_sweep_roofline(cj, f, stream, peaks, sweeps: int = 64) -> dict:
@@ -544,7 +548,8 @@ def ff_sweep_roofline(cj, f, stream, peaks, sweeps: int = 64) -> dict:
     hbm = BYTES_PER_UPDATE_FP64 * upd / t["ff"] / 1e9
     ops = FF_OPS_PER_UPDATE_9 * upd / t["ff"] / 1e12
     return {"kernel": "sweep_ff_kernel<9>", "bound": "hbm", "achieved": hbm, "peak": hbm_peak, "unit": "GB/s",
-            "frac": hbm / hbm_peak, "traffic": None, "bytes_per_update": BYTES_PER_UPDATE_FP64,
+            "frac": hbm / hbm_peak, "traffic": traffic_per_launch("sweep_ff_9_4096", FF_SOURCES),
+            "bytes_per_update": BYTES_PER_UPDATE_FP64,
             "peak_note": hbm_note + "; of measured",
             "fp32_issue": {"achieved": ops, "peak": peaks["fp32_tfma_s"], "unit": "TFP32op/s",
                            "frac": ops / peaks["fp32_tfma_s"], "ops_per_update": FF_OPS_PER_UPDATE_9,

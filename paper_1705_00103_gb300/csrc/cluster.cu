@@ -217,13 +217,20 @@ __global__ void __launch_bounds__(kClThreads) cluster_solve_kernel(ClArgs a) {
             // arrive half of the cluster barrier, the interior rows while the others arrive, and
             // the wait half: the interior rows read no ghost row, so a neighbour still finishing
             // them is never disturbed by the next sweep's stores into its ghost rows
-            for (long long k = t; k < (long long)(nbt + nbb) * Nx; k += kClThreads) {
+            // (one index space over the boundary rows, then the interior rows: a thread with no
+            // boundary node left arrives at once and starts on the interior, so every thread works
+            // while the boundary rows are computed)
+            const long long nbn = (long long)(nbt + nbb) * Nx, nall = (long long)nr * Nx;
+            long long k = t;
+            for (; k < nbn; k += kClThreads) {
                 const int row = (int)(k / Nx), x = (int)(k % Nx) + 2;
                 node(row < nbt ? 2 + row : nr + 2 - nbb + (row - nbt), x);
             }
             asm volatile("barrier.cluster.arrive.release;\n" ::: "memory");
-            for (long long k = t; k < (long long)(nr - nbt - nbb) * Nx; k += kClThreads)
-                node(2 + nbt + (int)(k / Nx), (int)(k % Nx) + 2);
+            for (; k < nall; k += kClThreads) {
+                const long long ki = k - nbn;
+                node(2 + nbt + (int)(ki / Nx), (int)(ki % Nx) + 2);
+            }
             __syncthreads();  // the interior rows, written after the arrive, for the next sweep
             asm volatile("barrier.cluster.wait.acquire;\n" ::: "memory");
             cur ^= 1;

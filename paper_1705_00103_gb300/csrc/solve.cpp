@@ -669,13 +669,11 @@ cj_status cj_plan_create(int Nx, int Ny, cj_stencil st, cj_bc bc, double tol,
         // default FP32 temporal depth, from measurements (cj_sweeps_f32, Gupd/s at depth 1 / 4):
         // 9-point 63 / 57 at 512^2, 179 / 226 at 1024^2, 510 / 545 at 2048^2, 480 / 1211 at
         // 4096^2, 539 / 1493 at 8192^2; 5-point 16 / 18 at 256^2, 63 / 72 at 512^2 and 481 / 1413
-        // at 4096^2; 17-point depth 1 / 2: 329 / 356 at 4096^2, 365 / 408 at 8192^2.
+        // at 4096^2; 17-point depth 1 / 2: 382 / 356 at 4096^2, 422 / 408 at 8192^2.
         // cj_autotune_depth records a measured choice per size class, which takes precedence.
         const int tuned = tuned_depth(st, Nx, Ny);
         const long long nodes = (long long)Nx * Ny;
-        const int dflt = (st == 5 && nodes >= (1LL << 16)) || (st == 9 && nodes >= (1LL << 20)) ? 4
-                         : st == 17 && nodes >= (1LL << 24)                                  ? 2
-                                                                                             : 1;
+        const int dflt = (st == 5 && nodes >= (1LL << 16)) || (st == 9 && nodes >= (1LL << 20)) ? 4 : 1;
         p->depth = o.temporal_depth ? o.temporal_depth : tuned ? tuned : dflt;
         long long unit = p->precision != CJ_FP64 ? p->M_in : p->M;
         p->max_sweeps = o.max_sweeps ? o.max_sweeps : 64 * unit;

@@ -278,8 +278,8 @@ def test_full_size_fp32_temporal_sweeps_bit_exact(cj, torch, st):
 @pytest.mark.parametrize("depth", (1, 2))
 def test_full_size_fp32_17_point_8192_sweeps_bit_exact(cj, torch, depth):
     """Five FP32 inner sweeps of the 17-point 8192^2 grid (the high-order workload's hot kernel) at
-    depth 1 (one sweep per launch) and depth 2 (the register wavefront, the default at this
-    size), against the oracle's one-sweep-at-a-time FP32 sweeps on the whole grid."""
+    depth 1 (one sweep per launch, the default) and depth 2 (the register wavefront), against
+    the oracle's one-sweep-at-a-time FP32 sweeps on the whole grid."""
     N, st = 8192, 17
     rng = np.random.default_rng(29 + depth)
     r = rng.standard_normal((N, N)).astype(np.float32)
