@@ -185,7 +185,7 @@ class ClockSampler:
 
 KERNEL_SOURCES = ("kernels.cu", "stencil_dev.cuh", "grid_dev.cuh")
 # sources of the FP32 register wavefront kernel (temporal blocking)
-WAVE_REG_SOURCES = ("wave_reg.cu", "fold_dev.cuh", "grid_dev.cuh", "stencil_dev.cuh", "cj_internal.h")
+WAVE_REG_SOURCES = ("wave_reg.cu", "wave_reg_dev.cuh", "fold_dev.cuh", "grid_dev.cuh", "stencil_dev.cuh", "cj_internal.h")
 # FP32 instructions per 9-point update of the register wavefront kernel (second-difference form):
 # 1.25 first differences along the row (shared between neighbours) and 1 second difference, both
 # for the row entering the stencil; 1 vertical difference and 1 second difference; 1 sum of the

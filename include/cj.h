@@ -365,7 +365,11 @@ typedef struct {
     double tol;
     int inner_cycle;        /* 0 = the planner's choice */
     int temporal_depth;     /* FP32 sweeps per sweep launch (temporal blocking), 1..8; 0 = the
-                               cj_autotune_engine choice for the size class, else 1 */
+                               cj_autotune_engine choice for the size class, else 4 for 5- and
+                               9-point problems with both sides >= 512, else 1.  Depth 4 of 5 and 9
+                               points runs the register wavefront of cj_sweeps_f32 over the
+                               problem's (strip, row block) items; other depths > 1 run tiles
+                               staged in shared memory */
     long long max_sweeps;   /* 0 = 64 inner cycles */
     const double *f;        /* device, Ny x ld_f, unscaled right-hand side */
     long long ld_f;
@@ -382,7 +386,8 @@ typedef struct {
  * grids that read a device tile list of 128-column tiles) is captured once in a CUDA graph
  * and replayed until every slot has finished; finished problems leave the tile list; tile
  * rows (16/32/64) and depth come from cj_autotune_engine's table for the size class when it
- * has an entry.  A problem's arithmetic does not depend on its batch-mates.  results[k] receives problem k's outcome (status per
+ * has an entry (depth-4 problems of 5 and 9 points sweep on the register wavefront instead of
+ * tiles, one warp per 128-column strip and 128-row block, four sweeps per launch).  A problem's arithmetic does not depend on its batch-mates.  results[k] receives problem k's outcome (status per
  * problem; seconds and launches are those of the whole batch).  Orders itself after the
  * work already on `stream` and makes `stream` wait for it; blocks until done.  Returns
  * CJ_OK, or CJ_ERR_TIMEOUT if a problem did not finish within its sweep budget's steps.
@@ -405,8 +410,11 @@ typedef struct {
  * many as give the device ~8 tiles per SM, up to 256 and 2^24 nodes) at every combination, and
  * recorded in a per-process table that cj_solve_batch and the server use for problems of that
  * class (the server sweeps one at a time, so it takes the tile rows only; an explicit
- * temporal_depth overrides the depth).  Not a method of the paper: a runtime choice of this
- * library.  Synchronous; allocates an Nx x Ny FP64 grid and the engine's slots while it runs.
+ * temporal_depth overrides the depth).  Depth 4 of 5 and 9 points (the register wavefront) is a
+ * candidate only when both sides are at least 512: below that its four-sweep launches are
+ * latency-bound in a batch, which copies of one problem do not show (its rate is then reported
+ * as 0).  Not a method of the paper: a runtime choice of this library.  Synchronous; allocates
+ * an Nx x Ny FP64 grid and the engine's slots while it runs.
  *   tile_rows, depth: the choice (may be NULL);
  *   gupd: host array of 9 (may be NULL): measured Gupdates/s, tile rows 16/32/64 (major) x
  *     depth 1/2/4.

@@ -22,6 +22,8 @@ namespace {
 // up to 32 sweeps, as with one sweep per step and 32 steps, with fewer launches per sweep
 // (measured: 4 sweeps per step 5.68 s for the 512-problem batch, 8: 5.52 s, 16: 5.45 s).
 constexpr int kSweepsPerStep = 8;
+// Shorter side from which 5- and 9-point problems sweep on the register wavefront by default.
+constexpr int kEngWaveMinSide = 512;
 
 using Clock = std::chrono::steady_clock;
 
@@ -71,7 +73,10 @@ class Engine {
     // captured graph's grids are updated when the list changes) instead of 8 blocks per SM that
     // stride over it; short-lived blocks let another stream's higher-priority kernels onto the SMs
     // within microseconds, where resident striding blocks would hold them for a whole launch.
-    cj_status init(int max_slots, int max_depth, int priority_rank = 0, bool tile_grid = false) {
+    // blocked_depth: the deepest depth of the tiles' shared-memory temporal blocking (17-point slots,
+    // depths 2 and 3); -1: max_depth.  Depth-4 slots of 5 and 9 points sweep on the wavefront.
+    cj_status init(int max_slots, int max_depth, int priority_rank = 0, bool tile_grid = false,
+                   int blocked_depth = -1) {
         if (max_slots < 1 || max_depth < 1 || max_depth > kTbMaxDepth) return CJ_ERR_INVALID_ARG;
         max_slots_ = max_slots;
         max_depth_ = max_depth;
@@ -85,7 +90,8 @@ class Engine {
         grid_tiles_ = sms * 8;
         tile_grid_ = tile_grid;
         grid_slots_ = std::min(max_slots, sms * 4);
-        smem_ = eng_sweep_smem(max_depth);
+        smem_ = eng_sweep_smem(blocked_depth < 0 ? max_depth : blocked_depth);
+        wave_ = max_depth >= 4;  // depth-4 slots of 5 and 9 points sweep on the register wavefront
         ENG_TRY(eng_prepare(smem_), "engine smem attribute");
         host_.assign(max_slots, SlotDev{});
         mem_.assign(max_slots, SlotMem{});
@@ -97,11 +103,16 @@ class Engine {
         ENG_TRY(cudaMemset(d_.status, 0, sizeof(SlotStatus) * max_slots), "engine status");
         ENG_TRY(cudaMalloc(&d_.ntiles, sizeof(int)), "engine tile count");
         ENG_TRY(cudaMemset(d_.ntiles, 0, sizeof(int)), "engine tile count");
+        ENG_TRY(cudaMalloc(&d_.nwaves, sizeof(int)), "engine wave count");
+        ENG_TRY(cudaMemset(d_.nwaves, 0, sizeof(int)), "engine wave count");
+        wave_cap_ = 0;
+        d_.waves = nullptr;
         tile_cap_ = 0;
         d_.tiles = nullptr;
         d_.max_slots = max_slots;
         ENG_TRY(cudaMallocHost(&h_status_, sizeof(SlotStatus) * max_slots), "engine status (host)");
         ENG_TRY(cudaMallocHost(&h_ntiles_, sizeof(int)), "engine tile count (host)");
+        ENG_TRY(cudaMallocHost(&h_nwaves_, sizeof(int)), "engine wave count (host)");
         return ensure_tile_capacity(1024);
     }
 
@@ -116,9 +127,12 @@ class Engine {
         cudaFree(d_.slots);
         cudaFree(d_.status);
         cudaFree(d_.ntiles);
+        cudaFree(d_.nwaves);
+        cudaFree(d_.waves);
         cudaFree(d_.tiles);
         if (h_status_) cudaFreeHost(h_status_);
         if (h_ntiles_) cudaFreeHost(h_ntiles_);
+        if (h_nwaves_) cudaFreeHost(h_nwaves_);
         cudaStreamDestroy(s_);
         s_ = nullptr;
     }
@@ -165,6 +179,8 @@ class Engine {
         // a depth the engine has no shared memory for (an autotuned one in the server, whose
         // engine sweeps one at a time) runs at the engine's maximum
         S.depth = std::min(sp.depth, max_depth_);
+        // the wavefront takes 4 sweeps at a time: an inner cycle of 1 or 2 sweeps runs at depth 1
+        if (S.depth == 4 && (sp.st == 5 || sp.st == 9) && M_in % 4 != 0) S.depth = 1;
         S.ty = sp.ty;
         S.ntx = (sp.Nx + kEngTX - 1) / kEngTX;
         S.ntiles = S.ntx * ((sp.Ny + sp.ty - 1) / sp.ty);
@@ -277,7 +293,7 @@ class Engine {
             }
         }
         for (int k = 0; k < replays; ++k) ENG_TRY(cudaGraphLaunch(gexec_, s_), "graph launch");
-        launches_ += (long long)replays * steps_per_graph_ * (4 + (smem_ > 0 ? 3 : 2) * kSweepsPerStep);
+        launches_ += (long long)replays * steps_per_graph_ * (4 + ((smem_ > 0 ? 3 : 2) + (wave_ ? 1 : 0)) * kSweepsPerStep);
         ENG_TRY(cudaMemcpyAsync(h_status_, d_.status, sizeof(SlotStatus) * max_slots_,
                                 cudaMemcpyDeviceToHost, s_), "status readback");
         ENG_TRY(cudaStreamSynchronize(s_), "step sync");
@@ -309,18 +325,45 @@ class Engine {
 
     cj_status upload_tiles() {
         tiles_.clear();
+        waves_.clear();
         for (int q = 0; q < max_slots_; ++q)
-            if (used_[q] && !tiles_off_[q])
+            if (used_[q] && !tiles_off_[q]) {
                 for (int t = 0; t < host_[q].ntiles; ++t) tiles_.push_back(make_int2(q, t));
+                if (wave_) eng_wave_items(q, host_[q].Nx, host_[q].Ny, host_[q].st, host_[q].depth, waves_);
+            }
         cj_status st = ensure_tile_capacity((int)tiles_.size() + 1);
         if (st != CJ_OK) return st;
+        st = ensure_wave_capacity((int)waves_.size() + 1);
+        if (st != CJ_OK) return st;
         *h_ntiles_ = (int)tiles_.size();
+        *h_nwaves_ = (int)waves_.size();
         if (!tiles_.empty())
             ENG_TRY(cudaMemcpyAsync(d_.tiles, tiles_.data(), sizeof(int2) * tiles_.size(),
                                     cudaMemcpyHostToDevice, s_), "tile upload");
+        if (!waves_.empty())
+            ENG_TRY(cudaMemcpyAsync(d_.waves, waves_.data(), sizeof(int4) * waves_.size(),
+                                    cudaMemcpyHostToDevice, s_), "wave upload");
         ENG_TRY(cudaMemcpyAsync(d_.ntiles, h_ntiles_, sizeof(int), cudaMemcpyHostToDevice, s_), "tile count");
+        ENG_TRY(cudaMemcpyAsync(d_.nwaves, h_nwaves_, sizeof(int), cudaMemcpyHostToDevice, s_), "wave count");
         ENG_TRY(cudaStreamSynchronize(s_), "tile sync");
         tiles_dirty_ = false;
+        return CJ_OK;
+    }
+
+    cj_status ensure_wave_capacity(int n) {
+        if (n <= wave_cap_) return CJ_OK;
+        int cap = std::max(n, 2 * wave_cap_);
+        int4 *t = nullptr;
+        ENG_TRY(cudaMalloc(&t, sizeof(int4) * cap), "wave table");
+        cudaFree(d_.waves);
+        d_.waves = t;
+        wave_cap_ = cap;
+        if (gexec_) {  // the graph bakes the table pointer in: capture again
+            cudaGraphExecDestroy(gexec_);
+            gexec_ = nullptr;
+            cudaGraphDestroy(graph_);
+            graph_ = nullptr;
+        }
         return CJ_OK;
     }
 
@@ -329,7 +372,7 @@ class Engine {
         ENG_TRY(cudaStreamBeginCapture(s_, cudaStreamCaptureModeThreadLocal), "begin capture");
         cudaError_t err = cudaSuccess;
         for (int k = 0; k < steps_per_graph_ && err == cudaSuccess; ++k)
-            err = eng_launch_step(d_, grid_tiles_, grid_slots_, smem_, kSweepsPerStep, s_);
+            err = eng_launch_step(d_, grid_tiles_, grid_slots_, smem_, kSweepsPerStep, wave_, s_);
         cudaError_t e2 = cudaStreamEndCapture(s_, &g);
         if (err == cudaSuccess) err = e2;
         if (err == cudaSuccess) err = cudaGraphInstantiate(&gexec_, g, 0);
@@ -379,6 +422,9 @@ class Engine {
     std::vector<SlotMem> mem_;
     std::vector<char> used_, tiles_off_;
     std::vector<int2> tiles_;
+    std::vector<int4> waves_;
+    int wave_cap_ = 0;
+    int *h_nwaves_ = nullptr;
     std::vector<float> wstage_;
     int tile_cap_ = 0;
     bool tiles_dirty_ = true;
@@ -386,7 +432,7 @@ class Engine {
     int *h_ntiles_ = nullptr;
     cudaGraphExec_t gexec_ = nullptr;
     cudaGraph_t graph_ = nullptr;
-    bool tile_grid_ = false;
+    bool tile_grid_ = false, wave_ = false;
     std::vector<cudaGraphNode_t> tile_nodes_;
     int cur_grid_ = 0;
     long long launches_ = 0;
@@ -427,6 +473,12 @@ cj_status check_problem(const cj_problem &pr) {
     return CJ_OK;
 }
 
+// Default depth of a problem the autotuner has not seen: the register wavefront (depth 4) for 5-
+// and 9-point problems whose shorter side is at least kEngWaveMinSide, else one sweep at a time.
+int default_depth(int st, int Nx, int Ny) {
+    return (st == CJ_ST5 || st == CJ_ST9) && std::min(Nx, Ny) >= kEngWaveMinSide ? 4 : 1;
+}
+
 Spec spec_of(const cj_problem &pr) {
     Spec sp;
     sp.Nx = pr.Nx;
@@ -436,7 +488,7 @@ Spec spec_of(const cj_problem &pr) {
     sp.mode = pr.precision ? pr.precision : auto_mode(pr.st, pr.Nx, pr.Ny, pr.tol);
     sp.inner_cycle = pr.inner_cycle;
     EngineTune t = engine_tuned(pr.st, pr.Nx, pr.Ny);
-    sp.depth = pr.temporal_depth ? pr.temporal_depth : (t.depth ? t.depth : 1);
+    sp.depth = pr.temporal_depth ? pr.temporal_depth : (t.depth ? t.depth : default_depth(pr.st, pr.Nx, pr.Ny));
     sp.ty = t.ty ? t.ty : kEngTYDefault;
     sp.max_sweeps = pr.max_sweeps;
     return sp;
@@ -706,15 +758,17 @@ extern "C" {
 
 cj_status cj_solve_batch(const cj_problem *problems, int n, void *stream, cj_result *results) {
     if (!problems || n < 1 || !results) return CJ_ERR_INVALID_ARG;
-    int max_depth = 1;
+    int max_depth = 1, blocked_depth = 1;
     for (int k = 0; k < n; ++k) {
         cj_status st = check_problem(problems[k]);
         if (st != CJ_OK) return st;
-        max_depth = std::max(max_depth, spec_of(problems[k]).depth);  // requested or autotuned
+        const int d = spec_of(problems[k]).depth;  // requested or autotuned
+        max_depth = std::max(max_depth, d);
+        if (problems[k].st == CJ_ST17 || d == 2 || d == 3) blocked_depth = std::max(blocked_depth, d);
     }
     auto t0 = Clock::now();
     Engine eng;
-    cj_status st = eng.init(n, max_depth);
+    cj_status st = eng.init(n, max_depth, 0, false, blocked_depth);
     if (st != CJ_OK) return st;
     cudaEvent_t ev;
     ENG_TRY(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming), "event");
@@ -800,8 +854,22 @@ cj_status cj_autotune_engine(int Nx, int Ny, cj_stencil st, int *tile_rows, int 
     copies = std::max<long long>(1, std::min<long long>(copies, (1LL << 24) / ((long long)Nx * Ny)));
     cj_status rc = CJ_OK;
     for (int c = 0; c < 9 && rc == CJ_OK; ++c) {
+        // depth 4 of 5 and 9 points is the register wavefront, whose four-sweep launches of a
+        // problem with a side under 512 are latency-bound in a batch (measured on the 512-problem
+        // batch: 3.55 s at depth 1 everywhere, 3.45 s at depth 4 everywhere, 3.16 s at depth 4 from
+        // a shorter side of 512): not a candidate there
+        if (dps[c] == 4 && st != CJ_ST17 && std::min(Nx, Ny) < kEngWaveMinSide) continue;
+        // the wavefront's copies: enough (strip, row block) items for two waves of its warps
+        long long cp = copies;
+        if (dps[c] == 4 && st != CJ_ST17) {
+            std::vector<int4> items;
+            const long long per = std::max(1, eng_wave_items(0, Nx, Ny, st, 4, items));
+            cp = std::max(cp, (2LL * eng_wave_grid() * 4 + per - 1) / per);
+            cp = std::min<long long>(cp, 256);
+            cp = std::max<long long>(1, std::min<long long>(cp, (1LL << 24) / ((long long)Nx * Ny)));
+        }
         Engine eng;
-        rc = eng.init((int)copies, dps[c]);
+        rc = eng.init((int)cp, dps[c], 0, false, st == CJ_ST17 || dps[c] == 2 || dps[c] == 3 ? dps[c] : 1);
         if (rc != CJ_OK) break;
         Spec sp{};
         sp.Nx = Nx;
@@ -813,18 +881,18 @@ cj_status cj_autotune_engine(int Nx, int Ny, cj_stencil st, int *tile_rows, int 
         sp.ty = tys[c];
         sp.tol = 1e-15;
         sp.max_sweeps = 0;
-        std::vector<int> q(copies, -1);
-        for (long long k = 0; k < copies && rc == CJ_OK; ++k)
+        std::vector<int> q(cp, -1);
+        for (long long k = 0; k < cp && rc == CJ_OK; ++k)
             rc = eng.admit(sp, f, Nx, nullptr, 0, nullptr, 0, &q[k], true);  // results into own slot
         if (rc == CJ_OK) rc = eng.run(2);  // capture and warm-up
         if (rc != CJ_OK) break;
         long long s0 = 0, s1 = 0;
-        for (long long k = 0; k < copies; ++k) s0 += eng.status(q[k]).sweeps;
+        for (long long k = 0; k < cp; ++k) s0 += eng.status(q[k]).sweeps;
         const auto t0 = Clock::now();
         rc = eng.run(kReplays);
         const double secs = std::chrono::duration<double>(Clock::now() - t0).count();
         if (rc != CJ_OK) break;
-        for (long long k = 0; k < copies; ++k) s1 += eng.status(q[k]).sweeps;
+        for (long long k = 0; k < cp; ++k) s1 += eng.status(q[k]).sweeps;
         rate[c] = (double)Nx * Ny * (double)(s1 - s0) / secs / 1e9;
     }
     cudaFree(f);

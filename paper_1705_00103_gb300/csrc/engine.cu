@@ -27,6 +27,7 @@
 #include "grid_dev.cuh"
 #include "march4_dev.cuh"
 #include "stencil_dev.cuh"
+#include "wave_reg_dev.cuh"
 
 namespace {
 
@@ -45,6 +46,15 @@ __device__ __forceinline__ TileRef tile_ref(const SlotDev &S, int slot, int lt) 
     t.i1 = min(t.i0 + kEngTX - 1, S.Nx);
     t.j1 = min(t.j0 + S.ty - 1, S.Ny);
     return t;
+}
+
+// Rows of the wavefront items' row blocks (16 rows of warm-up per block at depth 4).
+constexpr int kEngWaveRows = 128;
+
+// Slots whose current sweeps run on the register wavefront: 5- and 9-point slots at depth 4
+// with a whole step of 4 sweeps left in the inner cycle.
+__device__ __forceinline__ bool eng_wave_slot(const SlotDev &S) {
+    return S.depth == 4 && (S.st == 5 || S.st == 9) && S.M_in - S.counter >= 4;
 }
 
 template <int R>
@@ -235,7 +245,7 @@ __global__ void __launch_bounds__(kEngThreads, BLOCKED ? 1 : 8) eng_sweep(Engine
     for (int t = blockIdx.x; t < n; t += gridDim.x) {
         const int2 ref = E.tiles[t];
         SlotDev &S = E.slots[ref.x];
-        if (S.phase != PHASE_SWEEP) continue;
+        if (S.phase != PHASE_SWEEP || eng_wave_slot(S)) continue;
         const long long left = S.M_in - S.counter;
         const int k = (int)(S.depth < left ? S.depth : left);
         if ((k > 1) != BLOCKED) continue;
@@ -247,6 +257,31 @@ __global__ void __launch_bounds__(kEngThreads, BLOCKED ? 1 : 8) eng_sweep(Engine
             sweep_tile<9>(S, T, k, sm);
         else
             sweep_tile<17>(S, T, k, sm);
+    }
+}
+
+// Sweep launches, wavefront part: each warp takes (slot, strip, row block) items of the wave list
+// and advances them 4 sweeps (wr_run: the single-grid wavefront's per-warp stage, the same node
+// arithmetic, so the results equal one-sweep tiles bit for bit); the tile kernels leave these
+// slots alone.
+__global__ void __launch_bounds__(kWrThreads, 2) eng_sweep_wave(EngineDev E) {
+    __shared__ float4 ering[kWrWarps][kWrERing][32];
+    __shared__ float4 rring[kWrWarps][kWrRRing][32];
+    const int wid = (int)threadIdx.x >> 5;
+    const int n = *E.nwaves;
+    for (int it = (int)blockIdx.x * kWrWarps + wid; it < n; it += (int)gridDim.x * kWrWarps) {
+        const int4 w = E.waves[it];
+        SlotDev &S = E.slots[w.x];
+        if (S.phase != PHASE_SWEEP || !eng_wave_slot(S)) continue;  // warp-uniform
+        WrWeights wt;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) wt.w[k] = S.w32[S.counter + k];
+        const float *ein = S.cur ? S.e1 : S.e0;
+        float *eout = S.cur ? S.e0 : S.e1;
+        if (S.st == 5)
+            wr_run<5, 4>(ein, S.rt, eout, S.g32, wt, kEngWaveRows, w.y, w.z, ering[wid][0], rring[wid][0]);
+        else
+            wr_run<9, 4>(ein, S.rt, eout, S.g32, wt, kEngWaveRows, w.y, w.z, ering[wid][0], rring[wid][0]);
     }
 }
 
@@ -408,15 +443,38 @@ cudaError_t eng_prepare(size_t sweep_smem) {
     return e;
 }
 
+int eng_wave_items(int slot, int Nx, int Ny, int st, int depth, std::vector<int4> &items) {
+    if (depth != 4 || (st != 5 && st != 9)) return 0;
+    const int nstrips = wr_strips(Nx), nrb = (Ny + kEngWaveRows - 1) / kEngWaveRows;
+    for (int rb = 0; rb < nrb; ++rb)
+        for (int x = 0; x < nstrips; ++x) items.push_back(make_int4(slot, x, rb, 0));
+    return nstrips * nrb;
+}
+
+int eng_wave_grid() {
+    static const int n = [] {
+        int dev = 0, sms = 152, per_sm = 1;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, eng_sweep_wave, kWrThreads, 0) != cudaSuccess ||
+            per_sm < 1)
+            per_sm = 1;
+        return sms * per_sm;
+    }();
+    return n;
+}
+
 cudaError_t eng_launch_step(const EngineDev &e, int grid_tiles, int grid_slots, size_t sweep_smem,
-                            int sweeps, cudaStream_t s) {
+                            int sweeps, bool wave, cudaStream_t s) {
     const int grid_adv = (e.max_slots + 127) / 128;
+    const int grid_wave = wave ? eng_wave_grid() : 0;
     eng_correct<<<grid_tiles, kEngThreads, 0, s>>>(e);
     eng_defect<<<grid_tiles, kEngThreads, 0, s>>>(e);
     eng_decide<<<grid_slots, kEngThreads, 0, s>>>(e);
     for (int q = 0; q < sweeps; ++q) {
         eng_sweep<false><<<grid_tiles, kEngThreads, 0, s>>>(e);
         if (sweep_smem > 0) eng_sweep<true><<<grid_tiles, kEngThreads, sweep_smem, s>>>(e);
+        if (wave) eng_sweep_wave<<<grid_wave, kWrThreads, 0, s>>>(e);
         if (q + 1 < sweeps) eng_advance<<<grid_adv, 128, 0, s>>>(e, 0);
     }
     eng_export<<<grid_tiles, kEngThreads, 0, s>>>(e);

@@ -4,6 +4,8 @@
 // whatever set of problems is admitted when it is replayed.
 #pragma once
 
+#include <vector>
+
 #include "cj_internal.h"
 
 // Engine tile: the unit of work of every engine kernel, kEngTX columns x (per slot) ty rows of
@@ -50,14 +52,22 @@ struct EngineDev {
     int max_slots;
     int2 *tiles;           // (slot, tile index within the slot)
     int *ntiles;           // device counter of valid entries in tiles
+    int4 *waves;           // (slot, strip, row block, 0): register-wavefront items of depth-4 slots
+    int *nwaves;           // device counter of valid entries in waves
     SlotStatus *status;    // max_slots entries, refreshed by the advance kernel
 };
 
 // launchers (engine.cu)
 // one engine step: correct, defect, decide, `sweeps` sweep launches (each but the last
-// followed by a counter advance), export, advance
+// followed by a counter advance; with `wave`, each also launches the register-wavefront kernel
+// over the wave list), export, advance
 cudaError_t eng_launch_step(const EngineDev &e, int grid_tiles, int grid_slots, size_t sweep_smem,
-                            int sweeps, cudaStream_t s);
+                            int sweeps, bool wave, cudaStream_t s);
+// Appends the register-wavefront items of a slot (Nx x Ny, stencil st) to items, if the slot's
+// sweeps at depth `depth` run on the wavefront (5- and 9-point slots at depth 4); returns how many.
+int eng_wave_items(int slot, int Nx, int Ny, int st, int depth, std::vector<int4> &items);
+// Blocks of the wavefront kernel's launch (one wave).
+int eng_wave_grid();
 cudaError_t eng_launch_import(const EngineDev &e, int slot, int ntiles, const double *f,
                               long long ldf, const double *u0, long long ldu, cudaStream_t s);
 size_t eng_sweep_smem(int max_depth);

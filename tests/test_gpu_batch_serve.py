@@ -37,6 +37,11 @@ MIX = [  # (Nx, Ny, stencil, tol, precision, inner cycle, temporal depth)
     (1, 1, 5, 1e-8, 1, 1, 1),
     (200, 199, 17, 1e-8, 1, 256, 2),
     (3, 300, 9, 1e-8, 2, 128, 3),
+    # depth 4 of 5 and 9 points: the register wavefront (several strips and row blocks, ragged)
+    (300, 260, 5, 1e-8, 1, 64, 4),
+    (130, 129, 9, 1e-9, 2, 128, 4),
+    (1, 200, 5, 1e-8, 1, 64, 4),
+    (200, 3, 9, 1e-8, 1, 64, 4),
 ]
 
 
@@ -170,10 +175,14 @@ def test_engine_autotune_records_and_uses_its_choice(cj, torch):
     """The engine autotuner times tile rows x depth on a problem of the size class, records the
     fastest, and a batch of that class then runs with it -- to the oracle's bits.  (Run last in
     this file: the choice stays in the process's table.)"""
+    # both sides >= 512: depth 4 (the register wavefront) is a candidate
+    r = cj.cj_autotune_engine(600, 520, 5)
+    assert all(v > 0 for v in r["gupd"].values())
+    assert r["gupd"][(r["tile_rows"], r["depth"])] == max(r["gupd"].values())
     Nx, Ny, st = 300, 200, 9
     r = cj.cj_autotune_engine(Nx, Ny, st)
-    assert r["tile_rows"] in (16, 32, 64) and r["depth"] in (1, 2, 4)
-    assert all(v > 0 for v in r["gupd"].values())
+    assert r["tile_rows"] in (16, 32, 64) and r["depth"] in (1, 2)
+    assert all((v > 0) == (d != 4) for (ty, d), v in r["gupd"].items())  # a side under 512: no depth 4
     assert r["gupd"][(r["tile_rows"], r["depth"])] == max(r["gupd"].values())
     f, pr = _problem(torch, Nx, Ny, st, 1e-8, 1, 128, 0, 31)  # temporal_depth 0: the tuned one
     res = cj.cj_solve_batch([pr])
