@@ -431,7 +431,10 @@ cj_status cj_autotune_engine(int Nx, int Ny, cj_stencil st, int *tile_rows, int 
  * in hbm_budget_bytes (one budget shared by the lanes); admitted problems join the lane's running
  * engine between graph replays and leave it as each one finishes, so requests arriving while
  * others run overlap with them on the device, and a small request's replays sweep only small
- * grids: its latency follows its own work, not that of the largest grids being solved.
+ * grids: its latency follows its own work, not that of the largest grids being solved.  The
+ * two smaller lanes sweep one sweep per launch; the largest lane sweeps 5- and 9-point requests
+ * with both sides of at least 512 on the register wavefront (four sweeps per launch), launched
+ * with half a wave of blocks so that the smaller lanes' blocks still find room on every SM.
  */
 cj_status cj_server_create(size_t hbm_budget_bytes, int max_slots, cj_server **out);
 

@@ -75,8 +75,10 @@ class Engine {
     // within microseconds, where resident striding blocks would hold them for a whole launch.
     // blocked_depth: the deepest depth of the tiles' shared-memory temporal blocking (17-point slots,
     // depths 2 and 3); -1: max_depth.  Depth-4 slots of 5 and 9 points sweep on the wavefront.
+    // wave_share: the share of the SMs' wavefront blocks the wavefront kernel launches (1 = a whole
+    // wave; the server's larger lanes leave room for the smaller lanes' blocks).
     cj_status init(int max_slots, int max_depth, int priority_rank = 0, bool tile_grid = false,
-                   int blocked_depth = -1) {
+                   int blocked_depth = -1, double wave_share = 1.0) {
         if (max_slots < 1 || max_depth < 1 || max_depth > kTbMaxDepth) return CJ_ERR_INVALID_ARG;
         max_slots_ = max_slots;
         max_depth_ = max_depth;
@@ -92,6 +94,7 @@ class Engine {
         grid_slots_ = std::min(max_slots, sms * 4);
         smem_ = eng_sweep_smem(blocked_depth < 0 ? max_depth : blocked_depth);
         wave_ = max_depth >= 4;  // depth-4 slots of 5 and 9 points sweep on the register wavefront
+        wave_grid_ = wave_ ? std::max(1, (int)(wave_share * eng_wave_grid())) : 0;
         ENG_TRY(eng_prepare(smem_), "engine smem attribute");
         host_.assign(max_slots, SlotDev{});
         mem_.assign(max_slots, SlotMem{});
@@ -372,7 +375,7 @@ class Engine {
         ENG_TRY(cudaStreamBeginCapture(s_, cudaStreamCaptureModeThreadLocal), "begin capture");
         cudaError_t err = cudaSuccess;
         for (int k = 0; k < steps_per_graph_ && err == cudaSuccess; ++k)
-            err = eng_launch_step(d_, grid_tiles_, grid_slots_, smem_, kSweepsPerStep, wave_, s_);
+            err = eng_launch_step(d_, grid_tiles_, grid_slots_, smem_, kSweepsPerStep, wave_grid_, s_);
         cudaError_t e2 = cudaStreamEndCapture(s_, &g);
         if (err == cudaSuccess) err = e2;
         if (err == cudaSuccess) err = cudaGraphInstantiate(&gexec_, g, 0);
@@ -433,6 +436,7 @@ class Engine {
     cudaGraphExec_t gexec_ = nullptr;
     cudaGraph_t graph_ = nullptr;
     bool tile_grid_ = false, wave_ = false;
+    int wave_grid_ = 0;
     std::vector<cudaGraphNode_t> tile_nodes_;
     int cur_grid_ = 0;
     long long launches_ = 0;
@@ -514,6 +518,8 @@ void fill_result(const SlotStatus &st, cj_result *r) {
 // priority.  Admission stays by footprint against the one shared budget, in arrival order
 // within a lane.
 constexpr int kLanes = 3;
+// Share of a wave of wavefront blocks the larger lanes launch (one block per SM of the two that fit).
+constexpr double kServerWaveShare = 0.5;
 constexpr long long kLaneNodes[kLanes] = {1LL << 20, 1LL << 23, 1LL << 62};
 // Every lane launches its tile kernels with one block per tile (Engine::init's tile_grid): with
 // blocks that live a few microseconds, the block scheduler puts the smaller lanes' higher-priority
@@ -922,7 +928,9 @@ cj_status cj_server_create(size_t hbm_budget_bytes, int max_slots, cj_server **o
     sv->max_slots = max_slots;
     cudaGetDevice(&sv->device);
     for (int k = 0; k < kLanes; ++k) {
-        cj_status st = sv->lanes[k].eng.init(max_slots, 1, kLanes - 1 - k, true);
+        // the two larger lanes sweep 5- and 9-point requests with a side of at least 512 on the
+        // register wavefront (depth 4); the smallest sweeps one at a time
+        cj_status st = sv->lanes[k].eng.init(max_slots, k == kLanes - 1 ? 4 : 1, kLanes - 1 - k, true, 1, kServerWaveShare);
         if (st == CJ_OK && cudaMallocHost((void **)&sv->lanes[k].stage, cj_server::kStageBytes) != cudaSuccess)
             st = CJ_ERR_NOMEM;
         if (st != CJ_OK) {

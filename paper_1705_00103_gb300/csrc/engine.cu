@@ -465,16 +465,15 @@ int eng_wave_grid() {
 }
 
 cudaError_t eng_launch_step(const EngineDev &e, int grid_tiles, int grid_slots, size_t sweep_smem,
-                            int sweeps, bool wave, cudaStream_t s) {
+                            int sweeps, int wave_grid, cudaStream_t s) {
     const int grid_adv = (e.max_slots + 127) / 128;
-    const int grid_wave = wave ? eng_wave_grid() : 0;
     eng_correct<<<grid_tiles, kEngThreads, 0, s>>>(e);
     eng_defect<<<grid_tiles, kEngThreads, 0, s>>>(e);
     eng_decide<<<grid_slots, kEngThreads, 0, s>>>(e);
     for (int q = 0; q < sweeps; ++q) {
         eng_sweep<false><<<grid_tiles, kEngThreads, 0, s>>>(e);
         if (sweep_smem > 0) eng_sweep<true><<<grid_tiles, kEngThreads, sweep_smem, s>>>(e);
-        if (wave) eng_sweep_wave<<<grid_wave, kWrThreads, 0, s>>>(e);
+        if (wave_grid > 0) eng_sweep_wave<<<wave_grid, kWrThreads, 0, s>>>(e);
         if (q + 1 < sweeps) eng_advance<<<grid_adv, 128, 0, s>>>(e, 0);
     }
     eng_export<<<grid_tiles, kEngThreads, 0, s>>>(e);

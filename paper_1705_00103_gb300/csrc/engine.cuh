@@ -59,14 +59,14 @@ struct EngineDev {
 
 // launchers (engine.cu)
 // one engine step: correct, defect, decide, `sweeps` sweep launches (each but the last
-// followed by a counter advance; with `wave`, each also launches the register-wavefront kernel
-// over the wave list), export, advance
+// followed by a counter advance; with wave_grid > 0, each also launches the register-wavefront
+// kernel over the wave list with that many blocks), export, advance
 cudaError_t eng_launch_step(const EngineDev &e, int grid_tiles, int grid_slots, size_t sweep_smem,
-                            int sweeps, bool wave, cudaStream_t s);
+                            int sweeps, int wave_grid, cudaStream_t s);
 // Appends the register-wavefront items of a slot (Nx x Ny, stencil st) to items, if the slot's
 // sweeps at depth `depth` run on the wavefront (5- and 9-point slots at depth 4); returns how many.
 int eng_wave_items(int slot, int Nx, int Ny, int st, int depth, std::vector<int4> &items);
-// Blocks of the wavefront kernel's launch (one wave).
+// Blocks of the wavefront kernel resident on the device at once (one wave).
 int eng_wave_grid();
 cudaError_t eng_launch_import(const EngineDev &e, int slot, int ntiles, const double *f,
                               long long ldf, const double *u0, long long ldu, cudaStream_t s);
