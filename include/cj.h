@@ -382,7 +382,7 @@ typedef struct {
  * with the mixed-precision CJM: FP32 inner cycles inside FP64 or double-FP64 defect
  * correction, every problem's residual test and stop rule evaluated on the device.  The
  * problems run as slots of one engine whose step (correct, defect, decide, eight sweep
- * launches each followed by a counter advance, export, advance: launches over persistent
+ * launches, export, advance: launches over persistent
  * grids that read a device tile list of 128-column tiles) is captured once in a CUDA graph
  * and replayed until every slot has finished; finished problems leave the tile list; tile
  * rows (16/32/64) and depth come from cj_autotune_engine's table for the size class when it

@@ -8,13 +8,14 @@
 //               per-tile partial norms, and zero the inner iterate;
 //   decide   -- per slot: reduce the partials in a fixed order, apply the stop rule on the
 //               device, start the next inner cycle or finish the slot;
-//   sweep    -- every slot in an inner cycle advances min(depth, M_in - counter) FP32
-//               sweeps over all of its tiles (one-sweep march4, or temporal blocking); a step
-//               runs several sweep launches, each followed by a counter advance, so the
-//               per-step launches are spread over more sweeps;
+//   sweep    -- every slot in an inner cycle advances min(depth, left) FP32 sweeps over all
+//               of its tiles (one-sweep march4, or temporal blocking; depth-4 slots of 5 and
+//               9 points on the register wavefront); a step runs several sweep launches, the
+//               q-th reading where the slot stands from the step's starting counter and q,
+//               so the per-step launches are spread over more sweeps;
 //   export   -- finished slots copy u into the caller's buffer;
-//   advance  -- per slot: move the cycle counter, flip the ping-pong, retire exported slots,
-//               publish a compact status record for the host.
+//   advance  -- per slot: move the cycle counter and the ping-pong by the step's sweeps,
+//               retire exported slots, publish a compact status record for the host.
 // The launches read the tile list and the slots' phases from device memory, so a CUDA graph
 // of many steps is captured once and replayed unchanged while problems come and go.  No
 // kernel waits on another block: every dependency is a kernel boundary.
@@ -51,10 +52,32 @@ __device__ __forceinline__ TileRef tile_ref(const SlotDev &S, int slot, int lt) 
 // Rows of the wavefront items' row blocks (16 rows of warm-up per block at depth 4).
 constexpr int kEngWaveRows = 128;
 
-// Slots whose current sweeps run on the register wavefront: 5- and 9-point slots at depth 4
-// with a whole step of 4 sweeps left in the inner cycle.
+// Slots whose sweeps run on the register wavefront: 5- and 9-point slots at depth 4 (their inner
+// cycles are a multiple of 4 sweeps long: admission runs shorter ones at depth 1).
 __device__ __forceinline__ bool eng_wave_slot(const SlotDev &S) {
-    return S.depth == 4 && (S.st == 5 || S.st == 9) && S.M_in - S.counter >= 4;
+    return S.depth == 4 && (S.st == 5 || S.st == 9);
+}
+
+// Where sweep launch q of a step (0-based) stands for a slot in its inner cycle: the slot's counter
+// and ping-pong are those of the step's start (the step's last kernel advances them), launch q
+// sweeps k = min(depth, left) sweeps from counter + what the earlier launches swept, and every
+// earlier launch that swept flipped the ping-pong once.
+struct StepPos {
+    long long counter;  // weight index of launch q's first sweep
+    int cur;            // its input buffer
+    int k;              // sweeps of launch q (0: the cycle is already done)
+};
+
+__device__ __forceinline__ StepPos eng_pos(const SlotDev &S, int q) {
+    const long long left = S.M_in - S.counter, d = S.depth;
+    const long long done = (long long)q * d < left ? (long long)q * d : left;
+    const long long busy = (left + d - 1) / d;  // launches with sweeps in this cycle
+    const long long lw = q < busy ? q : busy;
+    StepPos P;
+    P.counter = S.counter + done;
+    P.cur = S.cur ^ (int)(lw & 1);
+    P.k = (int)(left - done < d ? left - done : d);
+    return P;
 }
 
 template <int R>
@@ -213,9 +236,10 @@ __global__ void __launch_bounds__(kEngThreads) eng_decide(EngineDev E) {
 
 // sweep: one-sweep march for depth 1, temporal blocking otherwise
 template <int ST>
-__device__ __forceinline__ void sweep_tile(SlotDev &S, const TileRef &T, int k, float *sm) {
-    const float *ein = S.cur ? S.e1 : S.e0;
-    float *eout = S.cur ? S.e0 : S.e1;
+__device__ __forceinline__ void sweep_tile(SlotDev &S, const TileRef &T, const StepPos &P, float *sm) {
+    const int k = P.k;
+    const float *ein = P.cur ? S.e1 : S.e0;
+    float *eout = P.cur ? S.e0 : S.e1;
     if (k == 1) {
         // four warps split the tile's rows; each lane takes four adjacent columns (march4)
         const int rows_per_warp = (S.ty + kEngThreads / 32 - 1) / (kEngThreads / 32);
@@ -224,11 +248,11 @@ __device__ __forceinline__ void sweep_tile(SlotDev &S, const TileRef &T, int k, 
         const int js = T.j0 + warp * rows_per_warp;
         const int je = min(js + rows_per_warp - 1, T.j1);
         if (c0 > T.i1 || js > je) return;
-        M4Store<ST> op{eout, &S.g32, c0, S.w32[S.counter]};
+        M4Store<ST> op{eout, &S.g32, c0, S.w32[P.counter]};
         march4<ST>(ein, S.rt, S.g32, c0, js, je, op);
     } else {
         float w[kTbMaxDepth];
-        for (int s = 0; s < k; ++s) w[s] = S.w32[S.counter + s];
+        for (int s = 0; s < k; ++s) w[s] = S.w32[P.counter + s];
         tb_tile<ST>(ein, S.rt, eout, S.g32, k, w, T.i0, T.j0, kEngTX, S.ty, sm);
     }
 }
@@ -239,24 +263,23 @@ __device__ __forceinline__ void sweep_tile(SlotDev &S, const TileRef &T, int k, 
 // (64 registers for the one-sweep tiles: 8 blocks per SM stay resident, which measured 1.4x faster on
 // the 512-problem batch than the 95-register, 5-blocks-per-SM build)
 template <bool BLOCKED>
-__global__ void __launch_bounds__(kEngThreads, BLOCKED ? 1 : 8) eng_sweep(EngineDev E) {
+__global__ void __launch_bounds__(kEngThreads, BLOCKED ? 1 : 8) eng_sweep(EngineDev E, int q) {
     extern __shared__ float sm[];
     const int n = *E.ntiles;
     for (int t = blockIdx.x; t < n; t += gridDim.x) {
         const int2 ref = E.tiles[t];
         SlotDev &S = E.slots[ref.x];
         if (S.phase != PHASE_SWEEP || eng_wave_slot(S)) continue;
-        const long long left = S.M_in - S.counter;
-        const int k = (int)(S.depth < left ? S.depth : left);
-        if ((k > 1) != BLOCKED) continue;
+        const StepPos P = eng_pos(S, q);
+        if (P.k == 0 || (P.k > 1) != BLOCKED) continue;
         const TileRef T = tile_ref(S, ref.x, ref.y);
         if (BLOCKED) __syncthreads();  // the previous tile's shared-memory stage is finished
         if (S.st == 5)
-            sweep_tile<5>(S, T, k, sm);
+            sweep_tile<5>(S, T, P, sm);
         else if (S.st == 9)
-            sweep_tile<9>(S, T, k, sm);
+            sweep_tile<9>(S, T, P, sm);
         else
-            sweep_tile<17>(S, T, k, sm);
+            sweep_tile<17>(S, T, P, sm);
     }
 }
 
@@ -264,7 +287,7 @@ __global__ void __launch_bounds__(kEngThreads, BLOCKED ? 1 : 8) eng_sweep(Engine
 // and advances them 4 sweeps (wr_run: the single-grid wavefront's per-warp stage, the same node
 // arithmetic, so the results equal one-sweep tiles bit for bit); the tile kernels leave these
 // slots alone.
-__global__ void __launch_bounds__(kWrThreads, 2) eng_sweep_wave(EngineDev E) {
+__global__ void __launch_bounds__(kWrThreads, 2) eng_sweep_wave(EngineDev E, int q) {
     __shared__ float4 ering[kWrWarps][kWrERing][32];
     __shared__ float4 rring[kWrWarps][kWrRRing][32];
     const int wid = (int)threadIdx.x >> 5;
@@ -273,11 +296,13 @@ __global__ void __launch_bounds__(kWrThreads, 2) eng_sweep_wave(EngineDev E) {
         const int4 w = E.waves[it];
         SlotDev &S = E.slots[w.x];
         if (S.phase != PHASE_SWEEP || !eng_wave_slot(S)) continue;  // warp-uniform
+        const StepPos P = eng_pos(S, q);
+        if (P.k != 4) continue;
         WrWeights wt;
 #pragma unroll
-        for (int k = 0; k < 4; ++k) wt.w[k] = S.w32[S.counter + k];
-        const float *ein = S.cur ? S.e1 : S.e0;
-        float *eout = S.cur ? S.e0 : S.e1;
+        for (int k = 0; k < 4; ++k) wt.w[k] = S.w32[P.counter + k];
+        const float *ein = P.cur ? S.e1 : S.e0;
+        float *eout = P.cur ? S.e0 : S.e1;
         if (S.st == 5)
             wr_run<5, 4>(ein, S.rt, eout, S.g32, wt, kEngWaveRows, w.y, w.z, ering[wid][0], rring[wid][0]);
         else
@@ -299,18 +324,17 @@ __global__ void __launch_bounds__(kEngThreads) eng_export(EngineDev E) {
     }
 }
 
-// Per slot after a sweep launch: counters, ping-pong, end of the inner cycle.  `final` (the
-// last launch of a step) also retires exported slots and publishes the status records.
-__global__ void eng_advance(EngineDev E, int final) {
+// Per slot at the end of a step: the step's `launches` sweep launches move the cycle counter and
+// the ping-pong (eng_pos), an inner cycle that ended becomes an outer step, exported slots retire,
+// and the status records are published.
+__global__ void eng_advance(EngineDev E, int launches) {
     for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < E.max_slots; q += gridDim.x * blockDim.x) {
         SlotDev &S = E.slots[q];
-        if (!final && S.phase != PHASE_SWEEP) continue;
         if (S.phase == PHASE_SWEEP) {
-            const long long left = S.M_in - S.counter;
-            const long long k = S.depth < left ? S.depth : left;
-            S.counter += k;
-            S.sweeps += k;
-            S.cur ^= 1;
+            const StepPos P = eng_pos(S, launches);  // where a launch after the last would start
+            S.sweeps += P.counter - S.counter;
+            S.counter = P.counter;
+            S.cur = P.cur;
             if (S.counter >= S.M_in) {
                 S.phase = PHASE_OUTER;
                 S.outer += 1;
@@ -471,13 +495,12 @@ cudaError_t eng_launch_step(const EngineDev &e, int grid_tiles, int grid_slots, 
     eng_defect<<<grid_tiles, kEngThreads, 0, s>>>(e);
     eng_decide<<<grid_slots, kEngThreads, 0, s>>>(e);
     for (int q = 0; q < sweeps; ++q) {
-        eng_sweep<false><<<grid_tiles, kEngThreads, 0, s>>>(e);
-        if (sweep_smem > 0) eng_sweep<true><<<grid_tiles, kEngThreads, sweep_smem, s>>>(e);
-        if (wave_grid > 0) eng_sweep_wave<<<wave_grid, kWrThreads, 0, s>>>(e);
-        if (q + 1 < sweeps) eng_advance<<<grid_adv, 128, 0, s>>>(e, 0);
+        eng_sweep<false><<<grid_tiles, kEngThreads, 0, s>>>(e, q);
+        if (sweep_smem > 0) eng_sweep<true><<<grid_tiles, kEngThreads, sweep_smem, s>>>(e, q);
+        if (wave_grid > 0) eng_sweep_wave<<<wave_grid, kWrThreads, 0, s>>>(e, q);
     }
     eng_export<<<grid_tiles, kEngThreads, 0, s>>>(e);
-    eng_advance<<<grid_adv, 128, 0, s>>>(e, 1);
+    eng_advance<<<grid_adv, 128, 0, s>>>(e, sweeps);
     return cudaGetLastError();
 }
 

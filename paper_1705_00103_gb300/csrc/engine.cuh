@@ -58,9 +58,9 @@ struct EngineDev {
 };
 
 // launchers (engine.cu)
-// one engine step: correct, defect, decide, `sweeps` sweep launches (each but the last
-// followed by a counter advance; with wave_grid > 0, each also launches the register-wavefront
-// kernel over the wave list with that many blocks), export, advance
+// one engine step: correct, defect, decide, `sweeps` sweep launches (with wave_grid > 0, each
+// also launches the register-wavefront kernel over the wave list with that many blocks), export,
+// advance (the step's sweeps applied to the counters at once)
 cudaError_t eng_launch_step(const EngineDev &e, int grid_tiles, int grid_slots, size_t sweep_smem,
                             int sweeps, int wave_grid, cudaStream_t s);
 // Appends the register-wavefront items of a slot (Nx x Ny, stencil st) to items, if the slot's
