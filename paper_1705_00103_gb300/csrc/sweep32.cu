@@ -16,9 +16,10 @@
 namespace {
 
 // The 17-point kernel is held to 85 registers (6 blocks per SM): measured 422 Gupd/s on 8192^2
-// against 365 at its unconstrained 119 registers (4 blocks) and 407 at 5 blocks.
+// against 365 at its unconstrained 119 registers (4 blocks) and 407 at 5 blocks.  (Minimum blocks
+// 0 leaves the 5- and 9-point kernels to the compiler's own register choice.)
 template <int ST>
-__global__ void __launch_bounds__(kBX, ST == 17 ? 6 : 1) sweep32_vec_kernel(const float *__restrict__ e, const float *__restrict__ r,
+__global__ void __launch_bounds__(kBX, ST == 17 ? 6 : 0) sweep32_vec_kernel(const float *__restrict__ e, const float *__restrict__ r,
                                                           float *__restrict__ out, Grid g, int ty, float w) {
     const int c0 = ((int)blockIdx.x * kBX + (int)threadIdx.x) * 4 + 1;  // first of this thread's columns
     const int j0 = (int)blockIdx.y * ty + 1;
