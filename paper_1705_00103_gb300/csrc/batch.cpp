@@ -296,7 +296,7 @@ class Engine {
             }
         }
         for (int k = 0; k < replays; ++k) ENG_TRY(cudaGraphLaunch(gexec_, s_), "graph launch");
-        launches_ += (long long)replays * steps_per_graph_ * (5 + ((smem_ > 0 ? 2 : 1) + (wave_ ? 1 : 0)) * kSweepsPerStep);
+        launches_ += (long long)replays * steps_per_graph_ * (5 + ((smem_ > 0 ? 2 : 1) + (wave_ ? 2 : 0)) * kSweepsPerStep);
         ENG_TRY(cudaMemcpyAsync(h_status_, d_.status, sizeof(SlotStatus) * max_slots_,
                                 cudaMemcpyDeviceToHost, s_), "status readback");
         ENG_TRY(cudaStreamSynchronize(s_), "step sync");

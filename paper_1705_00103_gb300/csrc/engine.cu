@@ -287,6 +287,8 @@ __global__ void __launch_bounds__(kEngThreads, BLOCKED ? 1 : 8) eng_sweep(Engine
 // and advances them 4 sweeps (wr_run: the single-grid wavefront's per-warp stage, the same node
 // arithmetic, so the results equal one-sweep tiles bit for bit); the tile kernels leave these
 // slots alone.
+// (one kernel per stencil: both stage bodies in one kernel overflow the instruction cache)
+template <int ST>
 __global__ void __launch_bounds__(kWrThreads, 2) eng_sweep_wave(EngineDev E, int q) {
     __shared__ float4 ering[kWrWarps][kWrERing][32];
     __shared__ float4 rring[kWrWarps][kWrRRing][32];
@@ -295,7 +297,7 @@ __global__ void __launch_bounds__(kWrThreads, 2) eng_sweep_wave(EngineDev E, int
     for (int it = (int)blockIdx.x * kWrWarps + wid; it < n; it += (int)gridDim.x * kWrWarps) {
         const int4 w = E.waves[it];
         SlotDev &S = E.slots[w.x];
-        if (S.phase != PHASE_SWEEP || !eng_wave_slot(S)) continue;  // warp-uniform
+        if (S.st != ST || S.phase != PHASE_SWEEP || !eng_wave_slot(S)) continue;  // warp-uniform
         const StepPos P = eng_pos(S, q);
         if (P.k != 4) continue;
         WrWeights wt;
@@ -303,10 +305,7 @@ __global__ void __launch_bounds__(kWrThreads, 2) eng_sweep_wave(EngineDev E, int
         for (int k = 0; k < 4; ++k) wt.w[k] = S.w32[P.counter + k];
         const float *ein = P.cur ? S.e1 : S.e0;
         float *eout = P.cur ? S.e0 : S.e1;
-        if (S.st == 5)
-            wr_run<5, 4>(ein, S.rt, eout, S.g32, wt, kEngWaveRows, w.y, w.z, ering[wid][0], rring[wid][0]);
-        else
-            wr_run<9, 4>(ein, S.rt, eout, S.g32, wt, kEngWaveRows, w.y, w.z, ering[wid][0], rring[wid][0]);
+        wr_run<ST, 4>(ein, S.rt, eout, S.g32, wt, kEngWaveRows, w.y, w.z, ering[wid][0], rring[wid][0]);
     }
 }
 
@@ -480,7 +479,7 @@ int eng_wave_grid() {
         int dev = 0, sms = 152, per_sm = 1;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, eng_sweep_wave, kWrThreads, 0) != cudaSuccess ||
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, eng_sweep_wave<9>, kWrThreads, 0) != cudaSuccess ||
             per_sm < 1)
             per_sm = 1;
         return sms * per_sm;
@@ -497,7 +496,10 @@ cudaError_t eng_launch_step(const EngineDev &e, int grid_tiles, int grid_slots, 
     for (int q = 0; q < sweeps; ++q) {
         eng_sweep<false><<<grid_tiles, kEngThreads, 0, s>>>(e, q);
         if (sweep_smem > 0) eng_sweep<true><<<grid_tiles, kEngThreads, sweep_smem, s>>>(e, q);
-        if (wave_grid > 0) eng_sweep_wave<<<wave_grid, kWrThreads, 0, s>>>(e, q);
+        if (wave_grid > 0) {
+            eng_sweep_wave<5><<<wave_grid, kWrThreads, 0, s>>>(e, q);
+            eng_sweep_wave<9><<<wave_grid, kWrThreads, 0, s>>>(e, q);
+        }
     }
     eng_export<<<grid_tiles, kEngThreads, 0, s>>>(e);
     eng_advance<<<grid_adv, 128, 0, s>>>(e, sweeps);
