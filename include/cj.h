@@ -294,7 +294,7 @@ cj_status cj_sweeps(cj_plan *plan, const double *f, long long ld_f, double *u, l
  * added and multiplied by error-free transformations (Knuth's TwoSum, the fused-multiply-add
  * TwoProduct), in the FP64 sweep's evaluation order.  Not bit-equal to cj_sweeps: each sweep
  * agrees with the FP64 sweep of the same input to a few units of 2^-47 of the terms it adds (within
- * 1e-12 x max(1, w_n S) x max |u|); it moves the same bytes with FP32 instructions, where the FP64
+ * 1e-12 x (max|u| + |w_n| (9 max|u| + max|b|))); it moves the same bytes with FP32 instructions, where the FP64
  * sweep is bound by GB300's FP64 rate.  Values must lie in the float range.  Plain FP64 plans of the
  * paper's stencils with the homogeneous boundary (CJ_BC_DIRICHLET0) only, else CJ_ERR_INVALID_ARG.
  * Arguments and layout as cj_sweeps; asynchronous on `stream`.

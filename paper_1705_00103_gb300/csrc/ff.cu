@@ -5,20 +5,19 @@
 // of the HBM bandwidth.  Here the iterate and b are held as unevaluated pairs of floats, hi + lo
 // with |lo| <= ulp(hi)/2 (48 significant bits against FP64's 53), and the sweep
 // u' = u + w (L u - b) of Sec. 2.1 is evaluated with the error-free transformations of Knuth
-// (TwoSum: s + e = a + b exactly) and Dekker/Kahan (TwoProduct by a fused multiply-add:
-// p + e = a b exactly), in the evaluation order of the FP64 sweep (the y-march of stencil_dev.cuh
-// with float-float in place of double).  The pair occupies the same 8 bytes as a double, so the
-// sweep moves the FP64 sweep's bytes with FP32 instructions only.  The result is not the FP64
-// sweep's bits: it agrees with it to a few units of 2^-47 of the terms it adds, well inside the
-// per-sweep tolerance of 1e-12 x max(1, w S) x ||u|| the sweeps are held to.
+// (TwoSum: s + e = a + b exactly) and Dekker (TwoProduct, here in its fused-multiply-add form:
+// p + e = a b exactly), in the evaluation order of the FP64 sweep (a y-march of its own for 5
+// and 9 points, with the next row's loads issued ahead, and the shared y-march of stencil_dev.cuh
+// for 17, with float-float in place of double).  The pair occupies the same 8 bytes as a double,
+// so the sweep moves the FP64 sweep's bytes with FP32 instructions only.  The result is not the
+// FP64 sweep's bits: it agrees with it to a few units of 2^-47 of the terms it adds, well inside
+// the per-sweep tolerance of 1e-12 x (max|u| + |w| (9 max|u| + max|b|)) the sweeps are held to.
 //
 // Conversions: the plan's padded FP64 buffers are converted in place to float-float before the
 // sweeps (hi = fl32(d), lo = fl32(d - hi)) and back after them (fl64(hi + lo)); values must lie in
 // the float range (|d| < 3.4e38); below 2^-126 their low part is lost (relative error 2^-24 of a
 // value that small).  Homogeneous-Dirichlet plans only: their ghost ring is 0 or the reflection of
 // the interior, which the sweeps rewrite, so no boundary data passes through the conversions.
-#include <cstdio>
-
 #include "cj_internal.h"
 #include "grid_dev.cuh"
 #include "stencil_dev.cuh"
