@@ -435,6 +435,10 @@ cj_status cj_autotune_engine(int Nx, int Ny, cj_stencil st, int *tile_rows, int 
  * two smaller lanes sweep one sweep per launch; the largest lane sweeps 5- and 9-point requests
  * with both sides of at least 512 on the register wavefront (four sweeps per launch), launched
  * with half a wave of blocks so that the smaller lanes' blocks still find room on every SM.
+ * While the smallest lane has requests on the device, the two larger lanes hold their next
+ * graph replay (32 sweeps of their slots), within an allowance of 1 s that refills at 0.5 s per
+ * second, so a larger lane still runs at least half the time under a sustained stream of small
+ * requests.  Results do not depend on the lanes' timing.
  */
 cj_status cj_server_create(size_t hbm_budget_bytes, int max_slots, cj_server **out);
 

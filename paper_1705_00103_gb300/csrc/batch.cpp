@@ -525,6 +525,17 @@ constexpr long long kLaneNodes[kLanes] = {1LL << 20, 1LL << 23, 1LL << 62};
 // blocks that live a few microseconds, the block scheduler puts the smaller lanes' higher-priority
 // blocks on the SMs as soon as any block retires, while each lane still fills the device when it
 // runs alone.
+// The two larger lanes also hold their next graph replay while the smallest lane has requests on
+// the device, so its short-lived kernels find the SMs free instead of sharing them with the larger
+// lanes' blocks; a replay is 32 sweeps of a lane's slots, so at most one replay of each larger
+// lane is in flight when a small request arrives.  (Holding the largest lane for the middle one
+// as well raised the p99 latency and lowered the throughput more, for no lower p50.)  The hold is
+// paid from an allowance per lane: it starts at kYieldCapS seconds, refills at kYieldRate seconds
+// per second and never exceeds kYieldCapS, so under a sustained stream of small requests a larger
+// lane still runs at least 1 - kYieldRate of the time.  Only the order in which the lanes'
+// replays reach the GPU changes: every request's arithmetic is the same.
+constexpr double kYieldCapS = 1.0;
+constexpr double kYieldRate = 0.5;
 
 int lane_of(const Spec &sp) {
     const long long n = (long long)sp.Nx * sp.Ny;
@@ -558,6 +569,8 @@ struct cj_server {
         std::map<int, uint64_t> by_slot;
         std::thread worker;
         char *stage = nullptr;
+        double allowance = kYieldCapS;  // seconds this lane may still hold for smaller lanes
+        Clock::time_point refilled{};
         ~Lane() {
             if (stage) cudaFreeHost(stage);
         }
@@ -586,6 +599,24 @@ struct cj_server {
         long long n = 0;
         for (const Lane &L : lanes) n += (long long)L.queue.size();
         return n;
+    }
+
+    bool small_lane_busy() const { return !lanes[0].by_slot.empty(); }
+
+    // Before a replay of a larger lane: waits while the smallest lane has requests on the device,
+    // as long as the lane's allowance lasts (the caller holds mu through lk).
+    void hold_for_small_lane(int lane, std::unique_lock<std::mutex> &lk) {
+        Lane &L = lanes[lane];
+        const Clock::time_point now = Clock::now();
+        if (L.refilled == Clock::time_point{}) L.refilled = now;
+        L.allowance = std::min(kYieldCapS,
+                               L.allowance + kYieldRate * std::chrono::duration<double>(now - L.refilled).count());
+        L.refilled = now;
+        if (L.allowance <= 0.0 || !small_lane_busy()) return;
+        const auto until = now + std::chrono::duration_cast<Clock::duration>(std::chrono::duration<double>(L.allowance));
+        cv.wait_until(lk, until, [&] { return stop || !small_lane_busy(); });
+        const double waited = std::chrono::duration<double>(Clock::now() - now).count();
+        L.allowance -= waited;
     }
 
     // Marks every running request of lane L failed (after a CUDA error of its engine).
@@ -661,7 +692,9 @@ struct cj_server {
             }
             bool active;
             {
-                std::lock_guard<std::mutex> lk(mu);
+                std::unique_lock<std::mutex> lk(mu);
+                if (lane > 0 && !L.by_slot.empty()) hold_for_small_lane(lane, lk);
+                if (stop) return;
                 active = !L.by_slot.empty();
             }
             if (!active) continue;
