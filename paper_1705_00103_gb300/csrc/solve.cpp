@@ -175,17 +175,18 @@ cudaError_t import64(const cj_plan *p, const double *f, long long ldf, const dou
 }
 
 // A whole plain FP64 solve in one cluster launch (small grids): the stop test runs on the
-// device, so the host reads the outcome once.
-cj_status run_fp64_cluster(cj_plan *p, cudaStream_t s, double **cur_out, cj_result *res) {
+// device, so its outcome is read back behind the solution's export, and the host synchronises
+// once per solve.
+cj_status solve_fp64_cluster(cj_plan *p, double *u, long long ldu, cudaStream_t s, cj_result *res) {
     CJ_TRY(cudaEventRecord(p->ev0, s), "event");
     CJ_TRY(launch_cluster_solve(p, p->red, s), "cluster solve");
     CJ_TRY(cudaEventRecord(p->ev1, s), "event");
-    res->launches += 1;
     CJ_TRY(cudaMemcpyAsync(p->h_red, p->red, 6 * sizeof(double), cudaMemcpyDeviceToHost, s), "cluster readback");
-    CJ_TRY(cudaStreamSynchronize(s), "cluster sync");
+    CJ_TRY(launch_export(p, p->u0, u, ldu, s), "export");
+    res->launches += 2;
+    CJ_TRY(cudaStreamSynchronize(s), "solve sync");
     const double *r = p->h_red;
     res->sweep_seconds = 1e-3 * elapsed_ms(p);
-    *cur_out = p->u0;
     res->status = (int)r[0];
     res->sweeps = (long long)r[1];
     res->cycles = (int)r[2];
@@ -197,7 +198,6 @@ cj_status run_fp64_cluster(cj_plan *p, cudaStream_t s, double **cur_out, cj_resu
 
 // The solve proper, once f and u have been imported into the plan's padded buffers.
 cj_status run_fp64(cj_plan *p, cudaStream_t s, double **cur_out, cj_result *res, History *h) {
-    if (p->cluster_C > 0 && h->cap == 0) return run_fp64_cluster(p, s, cur_out, res);
     double *cur = p->u0, *nxt = p->u1;
     long long sweeps = 0, cycles = 0;
     double prev = 0.0, sweep_ms = 0.0;
@@ -561,6 +561,13 @@ cj_status solve_core(cj_plan *p, const double *f, long long ldf, double *u, long
     cj_result r{};
     CJ_TRY(import64(p, f, ldf, u, ldu, s), "import");
     r.launches = 2;
+    if (p->precision == CJ_FP64 && p->cluster_C > 0 && h->cap == 0) {
+        cj_status st = solve_fp64_cluster(p, u, ldu, s, &r);
+        if (st == CJ_ERR_CUDA) return st;
+        r.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+        if (res) *res = r;
+        return st;
+    }
     double *cur = nullptr;
     cj_status st = p->precision == CJ_FP32_INNER      ? run_mixed(p, s, &cur, &r, h)
                    : p->precision == CJ_FP32_INNER_DD ? run_mixed_dd(p, s, &cur, &r, h)
