@@ -6,12 +6,19 @@
 // with |lo| <= ulp(hi)/2 (48 significant bits against FP64's 53), and the sweep
 // u' = u + w (L u - b) of Sec. 2.1 is evaluated with the error-free transformations of Knuth
 // (TwoSum: s + e = a + b exactly) and Dekker (TwoProduct, here in its fused-multiply-add form:
-// p + e = a b exactly), in the evaluation order of the FP64 sweep (a y-march of its own for 5
-// and 9 points, with the next row's loads issued ahead, and the shared y-march of stencil_dev.cuh
-// for 17, with float-float in place of double).  The pair occupies the same 8 bytes as a double,
+// p + e = a b exactly).  17 points: in the evaluation order of the FP64 sweep (the shared y-march
+// of stencil_dev.cuh, with float-float in place of double).  5 and 9 points: a y-march of its own,
+// with the next row's loads issued ahead, in the algebraically equal scaled form
+//   u' = (1 - c w / D) u + (w / D) (S - D b),
+// S the neighbour sum of D L u + c u with coefficients 1 and 4 (D = 1, c = 4 for 5 points; D = 6,
+// c = 20 for 9 points, Eq. 1 times 6): S needs float-float adds and one exact scaling by 4, D b is
+// formed once when b is converted, and w / D and 1 - c w / D are rounded once per sweep on the host
+// -- 69 and 93 FP32 operations per update against 80 and 116 for the three float-float
+// multiply-adds of the FP64 sweep's form.  The pair occupies the same 8 bytes as a double,
 // so the sweep moves the FP64 sweep's bytes with FP32 instructions only.  The result is not the
-// FP64 sweep's bits: it agrees with it to a few units of 2^-47 of the terms it adds, well inside
-// the per-sweep tolerance of 1e-12 x (max|u| + |w| (9 max|u| + max|b|)) the sweeps are held to.
+// FP64 sweep's bits: it agrees with it to a few units of 2^-47 of the terms it adds (in the scaled
+// form, |c1 u| and |w / D| |S - D b|, each at most about 3.4 |w| max|u| + |w| max|b| for 9 points), well
+// inside the per-sweep tolerance of 1e-12 x (max|u| + |w| (9 max|u| + max|b|)) the sweeps are held to.
 //
 // Conversions: the plan's padded FP64 buffers are converted in place to float-float before the
 // sweeps (hi = fl32(d), lo = fl32(d - hi)) and back after them (fl64(hi + lo)); values must lie in
@@ -61,6 +68,12 @@ __device__ __forceinline__ ff ff_mul(ff a, ff b) {
     return fast_two_sum_f(p, e);
 }
 
+// a - b
+__device__ __forceinline__ ff ff_sub(ff a, ff b) { return ff_add(a, -b); }
+
+// a times a power of two (exact: both parts scale without rounding)
+__device__ __forceinline__ ff ff_scale2(ff a, float two_k) { return ff{a.hi * two_k, a.lo * two_k}; }
+
 // float-float of a double, rounded once per part (host and device)
 __host__ __device__ __forceinline__ ff ff_of(double d) {
     const float hi = (float)d;
@@ -97,14 +110,27 @@ __device__ __forceinline__ ff ld<ff>(const ff *p) {
     return ff{v.x, v.y};
 }
 
+// The weights of one sweep.  17 points: w, for u' = u + w (L u - b) in the FP64 sweep's order.
+// 5 and 9 points, in the scaled form D L u = sum of the neighbours with small integer
+// coefficients - c u (D = 1, c = 4; D = 6, c = 20), with b stored as D b:
+//   u' = c1 u + wD (D L u + c u - D b),   wD = w / D,   c1 = 1 - c wD,
+// so the neighbour sum needs no multiplication (its coefficients 1 and 4 are powers of two).
+struct FFWeights {
+    ff w, wD, c1;
+};
+
 template <int ST>
 struct SweepOpFF {
     ff *out;
     const Grid *g;
     int i;
-    ff w;
+    FFWeights w;
     __device__ __forceinline__ void operator()(int j, ff r, ff uc) {
-        store_node<(ST == 17 ? 2 : 1), ff>(out, *g, i, j, Ar<ff>::fm(w, r, uc));
+        store_node<(ST == 17 ? 2 : 1), ff>(out, *g, i, j, Ar<ff>::fm(w.w, r, uc));
+    }
+    // t = D L u + c u - D b at (i, j): the new value c1 u + wD t
+    __device__ __forceinline__ void scaled(int j, ff t, ff uc) {
+        store_node<1, ff>(out, *g, i, j, ff_add(ff_mul(w.c1, uc), ff_mul(w.wD, t)));
     }
 };
 
@@ -138,8 +164,7 @@ __device__ __forceinline__ void march_ff(const ff *__restrict__ u, const ff *__r
             const ff p0 = ff_add(l, r_);
             const ff v1 = ff_add(um, up);
             const ff a = ff_add(p0, v1);
-            const ff r = ff_add(a, Ar<ff>::fm(Co<ff>::c5(), uc, -bk));
-            op(j, r, uc);
+            op.scaled(j, ff_sub(a, bk), uc);
             um = uc;
             uc = up;
         }
@@ -164,9 +189,7 @@ __device__ __forceinline__ void march_ff(const ff *__restrict__ u, const ff *__r
             const ff v1 = ff_add(um, up);
             const ff a = ff_add(pc, v1);
             const ff d = ff_add(pm, pp);
-            const ff r = Ar<ff>::fm(Co<ff>::ax9(), a,
-                                    Ar<ff>::fm(Co<ff>::dg9(), d, Ar<ff>::fm(Co<ff>::cc9(), uc, -bk)));
-            op(j, r, uc);
+            op.scaled(j, ff_sub(ff_add(ff_scale2(a, 4.0f), d), bk), uc);
             um = uc;
             uc = up;
             pm = pc;
@@ -181,7 +204,7 @@ template <int ST>
 __global__ void __launch_bounds__(kBX, ff_blocks_per_sm(ST)) sweep_ff_kernel(const ff *__restrict__ u,
                                                                         const ff *__restrict__ b,
                                                                         ff *__restrict__ out, Grid g, int ty,
-                                                                        ff w) {
+                                                                        FFWeights w) {
     const int i = blockIdx.x * kBX + threadIdx.x + 1;
     const int j0 = blockIdx.y * ty + 1;
     const int j1 = min(j0 + ty - 1, g.Ny);
@@ -210,29 +233,36 @@ dim3 ff_grid(const Grid &g, int st, int *ty) {
     return dim3(nbx, (g.Ny + t - 1) / t);
 }
 
-// In place: doubles -> float-float pairs, and back.
-__global__ void __launch_bounds__(256) to_ff_kernel(double *a, long long n) {
+// In place: doubles -> float-float pairs of D times them (D = 1 for u; the scale of the sweep's
+// form for b), and back (times 1 / D, exact for D = 1; b is imported again by every call that
+// uses it, so its value after the sweeps is not read).
+__global__ void __launch_bounds__(256) to_ff_kernel(double *a, long long n, double D) {
     for (long long k = blockIdx.x * 256LL + threadIdx.x; k < n; k += (long long)gridDim.x * 256) {
-        const ff v = ff_of(a[k]);
+        const ff v = ff_of(D * a[k]);
         reinterpret_cast<ff *>(a)[k] = v;
     }
 }
 
-__global__ void __launch_bounds__(256) from_ff_kernel(double *a, long long n) {
+__global__ void __launch_bounds__(256) from_ff_kernel(double *a, long long n, double inv_D) {
     for (long long k = blockIdx.x * 256LL + threadIdx.x; k < n; k += (long long)gridDim.x * 256) {
         const ff v = reinterpret_cast<const ff *>(a)[k];
-        a[k] = (double)v.hi + (double)v.lo;
+        a[k] = ((double)v.hi + (double)v.lo) * inv_D;
     }
 }
 
-cudaError_t convert(double *a, long long n, bool to_ff, cudaStream_t s) {
+cudaError_t convert(double *a, long long n, bool to_ff, cudaStream_t s, double D = 1.0) {
     const long long blocks = (n + 255) / 256 < 4096 ? (n + 255) / 256 : 4096;
     if (to_ff)
-        to_ff_kernel<<<(int)blocks, 256, 0, s>>>(a, n);
+        to_ff_kernel<<<(int)blocks, 256, 0, s>>>(a, n, D);
     else
-        from_ff_kernel<<<(int)blocks, 256, 0, s>>>(a, n);
+        from_ff_kernel<<<(int)blocks, 256, 0, s>>>(a, n, 1.0 / D);
     return cudaGetLastError();
 }
+
+// D and c of the scaled form of the 5- and 9-point sweeps (1 for 17 points, which keeps the
+// FP64 sweep's form).
+double ff_scale(int st) { return st == 9 ? 6.0 : 1.0; }
+double ff_centre(int st) { return st == 9 ? 20.0 : 4.0; }
 
 }  // namespace
 
@@ -247,13 +277,15 @@ cudaError_t launch_sweeps_ff(const cj_plan *p, const double *const *bufs, long l
     const long long n = p->g64.elems();
     double *u[2] = {const_cast<double *>(bufs[0]), const_cast<double *>(bufs[1])};
     double *b = const_cast<double *>(bufs[2]);
-    cudaError_t e = convert(b, n, true, s);
+    const double D = ff_scale(p->st);
+    cudaError_t e = convert(b, n, true, s, D);
     if (e == cudaSuccess) e = convert(u[0], n, true, s);
     if (e == cudaSuccess) e = convert(u[1], n, true, s);
     int cur = 0, ty = 1;
     const dim3 grid = ff_grid(p->g64, p->st, &ty);
     for (long long k = 0; k < count && e == cudaSuccess; ++k) {
-        const ff w = ff_of(p->w[(first + k) % p->M]);
+        const double wk = p->w[(first + k) % p->M], wD = wk / D;
+        const FFWeights w{ff_of(wk), ff_of(wD), ff_of(1.0 - ff_centre(p->st) * wD)};
         const ff *ui = reinterpret_cast<const ff *>(u[cur]);
         ff *uo = reinterpret_cast<ff *>(u[cur ^ 1]);
         const ff *bb = reinterpret_cast<const ff *>(b);
@@ -267,7 +299,7 @@ cudaError_t launch_sweeps_ff(const cj_plan *p, const double *const *bufs, long l
     }
     if (e == cudaSuccess) e = convert(u[0], n, false, s);
     if (e == cudaSuccess) e = convert(u[1], n, false, s);
-    if (e == cudaSuccess) e = convert(b, n, false, s);
+    if (e == cudaSuccess) e = convert(b, n, false, s, D);
     *cur_out = cur;
     return e;
 }

@@ -1,7 +1,8 @@
 """GPU accuracy of the float-float sweeps (cj_sweeps_ff) against the FP64 oracle, through the C ABI.
 
-The float-float sweep evaluates the FP64 sweep's expression (Sec. 2.1) in the same order with
-48-bit pairs of floats, so it is not bit-equal to the FP64 sweep; each sweep is held to
+The float-float sweep evaluates the sweep of Sec. 2.1 with 48-bit pairs of floats (17 points in the
+FP64 sweep's order, 5 and 9 points in an algebraically equal scaled form), so it is not bit-equal
+to the FP64 sweep; each sweep is held to
 
     |got - ref| <= 1e-12 x (max|u| + |w| (S max|u| + max|b|))
 
